@@ -1,0 +1,387 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 string sample sorter.
+
+One step is one pass of the whole hot path over the URL-like workload
+(n = 10,000,000 strings, seed 2): the set is cut into K = 4 index-contiguous
+runs, ss_sort_batch sorts the runs together (key gathers, splitter trees,
+classification, histograms, prefix sums, scatter, recursion, base case,
+LCP output), then ss_merge LCP-merges the runs into the final permutation
+and LCP array.  The result is identical to one ss_sort of the whole set.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the CPU oracle (plain qsort + naive LCP, one thread)
+on a bounded sample of the same workload instead.
+
+With N > 1 (torchrun) every rank sorts its own replica of the workload:
+the sort does not shard, there is no collective on the data path; the
+barrier and the max over ranks only frame the timing.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "strings/s and D-GB/s vs HBM roofline (bit-exact); batched p50/p99 vs plain"
+
+# Algorithmic bytes per unit of each kernel (unit = string, counter or record);
+# the minimal traffic the step needs, independent of cache behaviour.
+BYTES_PER_UNIT = {
+    "init": 8 + 8 + 4 + 8,           # offset read, key gather, index + key write
+    "classify": 8 + 2,               # key read, bucket write
+    "scatter": 2 + 4 + 8 + 4 + 8,    # bucket + index read, next-key gather, index + key write
+    "small_warp": 4 + 8 + 4 + 4,     # index + key read, perm + lcp write
+    "small_cta512": 4 + 8 + 4 + 4,
+    "small_cta4096": 4 + 8 + 4 + 4,
+    "boundary": 4 + 4 + 8 + 8 + 4,   # two perm reads, two key gathers, lcp write
+    "merge_round": 4 + 4 + 4 + 4,    # perm + lcp read, perm + lcp write
+    "copy_run": 16,
+    "scan_reduce": 4,
+    "scan_down": 8,
+    "buckets": 8,
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--runs", type=int, default=4)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def workload(n):
+    import workloads as W
+    return W.url_like(n, seed=2)
+
+
+def workload_name(n, runs):
+    return (f"url_like: n={n:,} strings 'http://' + host (2,000 hosts, Zipf s=1.1) + 1-6 path segments, "
+            f"5% duplicates, seed 2; sorted as {runs} runs + {runs}-way LCP merge")
+
+
+def d_and_balg(lcp: np.ndarray):
+    """D (Section 2) and the algorithmic bytes of a whole sort from the output LCP array."""
+    l = lcp.astype(np.int64)
+    nxt = np.concatenate([l[1:], [0]])
+    prv = l.copy()
+    prv[0] = 0
+    dist = np.maximum(prv, nxt) + 1
+    D = int(dist.sum())
+    n = l.shape[0]
+    balg = 8 * n + int((8 * ((dist + 7) // 8)).sum()) + 8 * n
+    return D, balg
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        self.index = index
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}",
+                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(ss, seconds):
+    """The oracle (one thread) on the first m strings of the workload, m sized for ~`seconds`."""
+    import oracle
+    import workloads as W
+    m = min(ss.n, 200_000)
+    t0 = time.perf_counter()
+    oracle.sort(W.subset(ss, np.arange(m)))
+    dt = time.perf_counter() - t0
+    if m < ss.n and dt < seconds:
+        m2 = min(ss.n, int(m * seconds / max(dt, 1e-3) / 1.1))
+        if m2 > m:
+            m = m2
+            t0 = time.perf_counter()
+            oracle.sort(W.subset(ss, np.arange(m)))
+            dt = time.perf_counter() - t0
+    return {"value": m / dt, "unit": "strings/s", "cores": 1, "kind": "oracle",
+            "sample": f"first {m:,} strings of the workload, one qsort + naive LCP pass ({dt:.1f} s)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    import workloads as W
+    oracle.build()
+    ss = workload(args.n)
+    m = min(ss.n, 1_000_000)
+    sub = W.subset(ss, np.arange(m))
+    for _ in range(max(0, args.warmup)):
+        oracle.sort(W.subset(ss, np.arange(min(m, 100_000))))
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.sort(sub)
+    dt = time.perf_counter() - t0
+    value = m * args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": workload_name(args.n, args.runs), "sample": m},
+            "cpu_baseline": {"value": value, "unit": "strings/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first {m:,} strings of the workload per step"},
+            "e2e": {"value": value, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import torch
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1403_2056_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    ss = workload(args.n)
+    n, K = ss.n, args.runs
+    chars = torch.from_numpy(ss.chars).to(dev)
+    offsets = torch.from_numpy(ss.offsets.view(np.int64)).to(dev)
+    rb = np.array([n * k // K for k in range(K + 1)], np.uint32)
+    rperm = torch.empty(n, dtype=torch.int32, device=dev)
+    rlcp = torch.empty(n, dtype=torch.int32, device=dev)
+    perm = torch.empty(n, dtype=torch.int32, device=dev)
+    lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    reqs = [dict(chars=chars, offsets=offsets[int(rb[k]):int(rb[k + 1])], lengths=None, fixed_len=0,
+                 n=int(rb[k + 1] - rb[k]), perm_out=rperm[int(rb[k]):int(rb[k + 1])],
+                 lcp_out=rlcp[int(rb[k]):int(rb[k + 1])]) for k in range(K)]
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        P.ss_sort_batch(reqs, stream=stream)
+        P.ss_merge(chars, offsets, None, 0, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], stream=stream)
+
+    def sort_only():
+        P.ss_sort(chars, offsets, n, perm, lcp, stream=stream)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+
+    # timed region: K steps, kernel events on the launch stream, clocks sampled
+    clocks = Clocks(local)
+    P.profile_reset()
+    P.profile_enable(True)
+    barrier()
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    launches0 = P.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    launches = P.launch_count() - launches0
+    ck = clocks.stop()
+    P.profile_enable(False)
+    prof = P.profile_read()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    if dist is not None:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    lcp_h = lcp.cpu().numpy().view(np.uint32)
+    D, balg = d_and_balg(lcp_h)
+    value = n * world / (ms / 1e3)
+
+    # sort only (rows a1-a9, one request) for context
+    for _ in range(2):
+        sort_only()
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    reps = max(3, args.steps // 2)
+    e0.record(stream)
+    for _ in range(reps):
+        sort_only()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    ms_sort = e0.elapsed_time(e1) / reps
+
+    # dominant kernel and its roofline
+    peak, peak_kind = load_peaks()
+    kernels = {}
+    for name, (nl, tms, units) in prof.items():
+        bpu = BYTES_PER_UNIT.get(name)
+        gbs = (units * bpu / (tms / 1e3) / 1e9) if (bpu and tms > 0) else None
+        kernels[name] = {"launches": nl, "ms_per_step": tms / args.steps, "share": None,
+                         "units_per_launch": units / max(nl, 1), "bytes_per_unit": bpu,
+                         "achieved_gbs": gbs}
+    tot = sum(v["ms_per_step"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms_per_step"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if dom and os.path.exists(tp):
+        try:
+            with open(tp) as f:
+                tj = json.load(f)
+            if tj.get("kernel") == dom and tj.get("source_hash") == _source_hash():
+                traffic = tj.get("bytes_per_launch")
+        except Exception:
+            traffic = None
+    roofline = None
+    if dom:
+        kd = kernels[dom]
+        ach = kd["achieved_gbs"] or 0.0
+        roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "traffic": traffic, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_launch": kd["units_per_launch"] * (kd["bytes_per_unit"] or 0)}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": world, "steps": args.steps,
+        "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": {"workload": workload_name(n, K), "n": n, "N_bytes": int(ss.chars.nbytes),
+                   "mean_len": ss.meta.get("mean_len"), "runs": K, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (chars 0.5 GB + offsets 80 MB per step)"},
+        "d_gb_per_s": D * world / (ms / 1e3) / 1e9, "D": D,
+        "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
+                                "frac": balg / (ms / 1e3) / 1e9 / peak},
+        "sort_only": {"ms": ms_sort, "value": n / (ms_sort / 1e3), "unit": "strings/s",
+                      "what": "one ss_sort of the whole set (no runs, no merge)"},
+        "roofline": roofline,
+        "gpu_launches": int(launches),
+        "clocks": ck,
+        "kernels": kernels,
+    }
+
+    # end to end through the host-buffer API: H2D, sort runs + merge, D2H
+    if not args.no_e2e:
+        hc = torch.from_numpy(ss.chars).pin_memory()
+        ho = torch.from_numpy(ss.offsets.view(np.int64)).pin_memory()
+        hp = torch.empty(n, dtype=torch.int32).pin_memory()
+        hl = torch.empty(n, dtype=torch.int32).pin_memory()
+        for _ in range(2):
+            P.ss_sort_host(hc, ho, None, 0, hp, hl, runs=K, stream=stream)
+        barrier()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        reps = max(3, args.steps // 2)
+        for _ in range(reps):
+            P.ss_sort_host(hc, ho, None, 0, hp, hl, runs=K, stream=stream)
+        torch.cuda.synchronize(dev)
+        e2e_ms = (time.perf_counter() - t0) / reps * 1e3
+        if dist is not None:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        line["e2e"] = {"value": n * world / (e2e_ms / 1e3), "unit": "strings/s",
+                       "h2d_bytes_per_step": int(ss.chars.nbytes + 8 * n), "d2h_bytes_per_step": int(8 * n),
+                       "ms_per_step": e2e_ms}
+        same = np.array_equal(hp.numpy(), perm.cpu().numpy()) and np.array_equal(hl.numpy(), lcp.cpu().numpy())
+        line["e2e"]["equals_device_result"] = bool(same)
+
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        line["cpu_baseline"] = cpu_baseline(ss, args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def _source_hash():
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1403_2056_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,213 @@
+/*
+ * ss.h -- C ABI of the GB300 string sample sorter (libss_gb300.so).
+ *
+ * Sorts n byte strings lexicographically and returns the sorted permutation
+ * and the LCP array, following the problem statement of Section 2 of
+ * Bingmann, Eberle, Sanders, "Engineering Parallel String Sorting": strings
+ * over the alphabet {1..255} (unsigned bytes, no 0 byte inside a string),
+ * ordered character by character with the end of a string below every
+ * character.  The method is super scalar string sample sort (Section 3.3,
+ * Algorithm 1) with LCP saving (Section 4.4) and LCP-aware merging of sorted
+ * runs (Section 4.1-4.3, Algorithms 2-4), run on one GPU.
+ *
+ * Conventions for every entry point:
+ *   - Pointers named *_dev are DEVICE pointers owned by the caller; the
+ *     library never frees or retains them past the call.  Pointers named
+ *     *_host are host pointers.
+ *   - `stream` is a cudaStream_t (may be NULL for the legacy default stream).
+ *     Work is ordered on that stream.  The sort entry points read small
+ *     counters back between recursion levels, so they return only after the
+ *     sort has finished on `stream`; outputs are then complete.
+ *   - Scratch memory comes from a stream-ordered pool owned by the library
+ *     (one per device, kept between calls); it is returned to the pool at the
+ *     end of each call.
+ *   - Output conventions (the reading taken where the paper is silent):
+ *     perm_out[i] = input index of the i-th smallest string; equal strings
+ *     appear in ascending input index; lcp_out[0] = 0 and lcp_out[i] =
+ *     lcp(s_{perm[i-1]}, s_{perm[i]}) for i >= 1, the LCP stopping at the end
+ *     of the shorter string.
+ *   - Return value: SS_OK, or a negative ss_status.  On error
+ *     ss_last_error_detail() gives a message for the calling thread.  Outputs
+ *     are unspecified after an error.
+ *   - Reads of string bytes are aligned 8-byte words that hold at least one
+ *     byte of the string being read (or of its terminator), so no read
+ *     touches a page the strings do not touch.
+ */
+#ifndef SS_GB300_H
+#define SS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+typedef struct CUstream_st *ss_stream_t; /* identical to cudaStream_t */
+
+typedef enum {
+    SS_OK = 0,
+    SS_ERR_INVALID = -1,       /* bad argument (NULL pointer with n > 0, bad K, ...) */
+    SS_ERR_OOM = -2,           /* scratch allocation failed */
+    SS_ERR_CUDA = -3,          /* a CUDA call or launch failed */
+    SS_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
+    SS_ERR_TOO_LARGE = -5,     /* n or a total beyond 2^32 - 2 */
+    SS_ERR_UNIMPLEMENTED = -6, /* feature not available in this build */
+    SS_ERR_INTERNAL = -7       /* a device-side consistency check failed */
+} ss_status;
+
+/*
+ * ss_sort -- sort n NUL-terminated strings (Section 2; Algorithm 1 applied
+ * recursively, Section 3.5; LCP saving, Section 4.4).
+ *   chars_dev   : string bytes; string i starts at chars_dev[offsets_dev[i]]
+ *                 and ends at the first 0 byte (the terminator).
+ *   offsets_dev : uint64[n], byte offset of each string.
+ *   n           : number of strings, 0 <= n <= 2^32 - 2; n = 0 is a no-op.
+ *   perm_out_dev: uint32[n] output, sorted permutation.
+ *   lcp_out_dev : uint32[n] output, LCP array.
+ * Strings must be shorter than 2^32 - 16 bytes.
+ */
+int ss_sort(const uint8_t *chars_dev, const uint64_t *offsets_dev, uint32_t n,
+            uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
+
+/*
+ * ss_sort_ex -- as ss_sort for strings delimited by length instead of a
+ * terminator (for example overlapping windows of one text).
+ *   lengths_dev : uint32[n] string lengths, or NULL;
+ *   fixed_len   : when lengths_dev is NULL and fixed_len > 0, every string
+ *                 has exactly fixed_len bytes; when both are 0/NULL the
+ *                 strings are NUL-terminated as in ss_sort.
+ * Strings must not contain the byte 0 (the paper's alphabet is {1..sigma}).
+ */
+int ss_sort_ex(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32_t *lengths_dev,
+               uint32_t fixed_len, uint32_t n, uint32_t *perm_out_dev, uint32_t *lcp_out_dev,
+               ss_stream_t stream);
+
+/*
+ * ss_sort_host -- ss_sort_ex for HOST buffers: copies the strings to the
+ * device, sorts, copies perm and lcp back, and returns when they are in the
+ * host arrays.  chars_len_host is the number of bytes of chars_host to copy
+ * (every string and terminator must lie inside it).  Host buffers may be
+ * pageable or pinned; pinned buffers copy faster.
+ *   runs : 0 or 1 sorts the set in one piece.  runs = K > 1 sorts K
+ *          index-contiguous runs together (as one ss_sort_batch) and merges
+ *          them with ss_merge, the paper's "independent sorters, then LCP
+ *          merge" structure (Section 4); the result is the same.
+ */
+int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len_host, const uint64_t *offsets_host,
+                 const uint32_t *lengths_host, uint32_t fixed_len, uint32_t n, uint32_t runs,
+                 uint32_t *perm_out_host, uint32_t *lcp_out_host, ss_stream_t stream);
+
+/*
+ * One independent sort request of a batch.  Fields as in ss_sort_ex; all
+ * pointers are device pointers.  status_out_dev may be NULL; otherwise the
+ * library writes the request's ss_status (int32) there when it is done.
+ */
+typedef struct {
+    const uint8_t *chars;
+    const uint64_t *offsets;
+    const uint32_t *lengths;
+    uint32_t fixed_len;
+    uint32_t n;
+    uint32_t *perm_out;
+    uint32_t *lcp_out;
+    int32_t *status_out;
+} ss_request;
+
+/*
+ * ss_sort_batch -- sort `count` independent requests together (host array
+ * reqs_host).  All requests advance through the same recursion levels in
+ * the same kernel launches (the paper's job queue of independent
+ * subproblems, Section 3.5, moved onto the device).  The sum of all n must
+ * not exceed 2^32 - 2.  Results equal those of one ss_sort_ex per request.
+ */
+int ss_sort_batch(const ss_request *reqs_host, uint32_t count, ss_stream_t stream);
+
+/*
+ * ss_merge -- LCP-aware merge of K sorted runs of one string set
+ * (Sections 4.1-4.3: LCP-Compare, Algorithm 2; binary LCP-merge,
+ * Algorithm 3; the K-way merge is done as ceil(log2 K) rounds of pairwise
+ * merges partitioned by merge path).
+ *   chars_dev/offsets_dev/lengths_dev/fixed_len : the string set, as ss_sort_ex.
+ *   run_perm_dev : uint32[total]; run k is positions
+ *                  [run_begin_host[k], run_begin_host[k+1]), sorted.  Its
+ *                  entries plus run_base_host[k] are string indices of the set.
+ *   run_lcp_dev  : uint32[total] LCP array of each run (entry at a run's
+ *                  first position is ignored).
+ *   run_begin_host : uint32[K+1] on the host, non-decreasing, [0] = 0.
+ *   run_base_host  : uint32[K] on the host, or NULL for all zero (for runs
+ *                  sorted by ss_sort_batch with request-local indices: the
+ *                  index of each run's first string).
+ *   K            : number of runs, 1 <= K.
+ *   perm_out_dev/lcp_out_dev : uint32[total] merged order (string indices of
+ *                  the set) and its LCP array; must not overlap the inputs.
+ * Equal strings from different runs are ordered by run number.  The input
+ * arrays are not modified.
+ */
+int ss_merge(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32_t *lengths_dev,
+             uint32_t fixed_len, const uint32_t *run_perm_dev, const uint32_t *run_lcp_dev,
+             const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
+             uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
+
+/*
+ * ss_gather_keys -- chars_h (Section 3.4): for each string i, the 8 bytes at
+ * depth depth_dev[i] as a big-endian uint64 (first character in the most
+ * significant byte), bytes past the end of the string zero.
+ *   depth_dev : uint32[n] depths (each at most the string's length).
+ *   keys_out_dev : uint64[n].
+ */
+int ss_gather_keys(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32_t *lengths_dev,
+                   uint32_t fixed_len, uint32_t n, const uint32_t *depth_dev, uint64_t *keys_out_dev,
+                   ss_stream_t stream);
+
+/*
+ * ss_splitters -- splitter selection of Section 3.4 on the device: sort the
+ * sample (a keys) and pick v = 2^d - 1 in-order splitters with the recursive
+ * scheme that skips samples equal to the chosen middle splitter.
+ *   sample_dev : uint64[a], 1 <= a <= 2047; d in [1, 10].
+ *   x_out_dev  : uint64[2^d - 1], sorted splitters.
+ */
+int ss_splitters(const uint64_t *sample_dev, uint32_t a, uint32_t d, uint64_t *x_out_dev,
+                 ss_stream_t stream);
+
+/*
+ * ss_classify -- one S5 step over n 8-byte keys with given splitters
+ * (Algorithm 1: tree descent, equality test, bucket counts, prefix sum,
+ * stable redistribution), run by the same kernels the sort uses.
+ *   keys_dev     : uint64[n].
+ *   x_dev        : uint64[2^d - 1] in-order splitters, non-decreasing; d in [1, 10].
+ *   bucket_out_dev : uint16[n]; bucket 2r + [x_r == c] where r = #{j: x_j < c}.
+ *   bucket_begin_out_dev : uint32[2^(d+1)] start of each bucket, last = n.
+ *   order_out_dev  : uint32[n]; order_out[p] = input position placed at p
+ *                    (stable: input order inside a bucket).
+ */
+int ss_classify(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, uint32_t d,
+                uint16_t *bucket_out_dev, uint32_t *bucket_begin_out_dev, uint32_t *order_out_dev,
+                ss_stream_t stream);
+
+/* Kernel timing: when enabled, the library records CUDA events around each of
+ * its kernel launches (on the launch stream) and accumulates per-kernel time.
+ * ss_profile_read fills up to `cap` entries: name (NUL-terminated, 48 bytes
+ * each), launches, total milliseconds and units (strings or records the
+ * launches processed); returns the number of kernels.  Any output pointer
+ * may be NULL. */
+int ss_profile_enable(int on);
+int ss_profile_reset(void);
+int ss_profile_read(char *names48, uint64_t *launches, double *total_ms, uint64_t *units, int cap);
+
+/* Number of kernel launches issued by the library since the last reset. */
+uint64_t ss_launch_count(void);
+
+/* Copies the calling thread's last error message into buf (NUL-terminated);
+ * returns its full length. */
+int ss_last_error_detail(char *buf, size_t len);
+
+/* ABI version (major * 100 + minor). */
+int ss_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SS_GB300_H */

@@ -1,0 +1,222 @@
+"""Python binding of libss_gb300.so, the GB300 string sample sorter.
+
+Argument marshalling only: every function forwards torch tensors (device
+memory, contiguous) or host numpy arrays to the C ABI declared in
+include/ss.h and raises :class:`SortError` on a non-zero status.  There is no
+CPU fallback: importing this module on a machine without the built library
+raises immediately.
+
+Names follow the C ABI: ss_sort, ss_sort_ex, ss_sort_host, ss_sort_batch,
+ss_merge, ss_gather_keys, ss_splitters, ss_classify.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "SortError", "lib", "library_path",
+    "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge",
+    "ss_gather_keys", "ss_splitters", "ss_classify",
+    "profile_enable", "profile_reset", "profile_read", "launch_count",
+    "STATUS",
+]
+
+STATUS = {0: "SS_OK", -1: "SS_ERR_INVALID", -2: "SS_ERR_OOM", -3: "SS_ERR_CUDA", -4: "SS_ERR_TIMEOUT",
+          -5: "SS_ERR_TOO_LARGE", -6: "SS_ERR_UNIMPLEMENTED", -7: "SS_ERR_INTERNAL"}
+
+
+class SortError(RuntimeError):
+    def __init__(self, status: int, detail: str):
+        super().__init__(f"{STATUS.get(status, status)}: {detail}")
+        self.status = status
+        self.detail = detail
+
+
+def library_path() -> str:
+    return _build.SO
+
+
+_lib = None
+
+
+def lib():
+    """Load libss_gb300.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = library_path()
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: run `python -m paper_1403_2056_gb300.build` "
+                          "(or __graft_entry__.build()) first; there is no CPU fallback")
+    L = C.CDLL(path)
+    vp, u32, u64, i32 = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+    L.ss_sort.argtypes = [vp, vp, u32, vp, vp, vp]
+    L.ss_sort_ex.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp]
+    L.ss_sort_host.argtypes = [vp, u64, vp, vp, u32, u32, u32, vp, vp, vp]
+    L.ss_sort_batch.argtypes = [vp, u32, vp]
+    L.ss_merge.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, u32, vp, vp, vp]
+    L.ss_gather_keys.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp]
+    L.ss_splitters.argtypes = [vp, u32, u32, vp, vp]
+    L.ss_classify.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp]
+    L.ss_profile_enable.argtypes = [i32]
+    L.ss_profile_read.argtypes = [vp, vp, vp, vp, i32]
+    L.ss_launch_count.restype = u64
+    L.ss_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
+    L.ss_version.restype = i32
+    for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_gather_keys",
+                 "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read"):
+        getattr(L, name).restype = i32
+    _lib = L
+    return L
+
+
+class Request(C.Structure):
+    """ss_request of the C ABI."""
+    _fields_ = [("chars", C.c_void_p), ("offsets", C.c_void_p), ("lengths", C.c_void_p),
+                ("fixed_len", C.c_uint32), ("n", C.c_uint32), ("perm_out", C.c_void_p),
+                ("lcp_out", C.c_void_p), ("status_out", C.c_void_p)]
+
+
+def _detail() -> str:
+    buf = C.create_string_buffer(512)
+    lib().ss_last_error_detail(buf, 512)
+    return buf.value.decode(errors="replace")
+
+
+def _check(rc: int):
+    if rc != 0:
+        raise SortError(rc, _detail())
+
+
+def _ptr(t):
+    """Device/host address of a torch tensor, numpy array or int (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be contiguous")
+        return t.ctypes.data
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _dev(t, dtype_name, what):
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    if not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+    if str(t.dtype) != f"torch.{dtype_name}":
+        raise TypeError(f"{what} must be torch.{dtype_name}, got {t.dtype}")
+    return _ptr(t)
+
+
+def _stream(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def ss_sort(chars, offsets, n, perm_out, lcp_out, stream=None):
+    _check(lib().ss_sort(_dev(chars, "uint8", "chars"), _off(offsets), int(n), _dev(perm_out, "int32", "perm_out"),
+                         _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+
+
+def ss_sort_ex(chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, stream=None):
+    _check(lib().ss_sort_ex(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
+                            int(fixed_len), int(n), _dev(perm_out, "int32", "perm_out"),
+                            _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+
+
+def _off(offsets):
+    if offsets is None or isinstance(offsets, int):
+        return offsets
+    if str(offsets.dtype) not in ("torch.int64", "torch.uint64"):
+        raise TypeError("offsets must be a 64-bit integer tensor")
+    if not offsets.is_cuda:
+        raise ValueError("offsets must be a CUDA tensor")
+    return _ptr(offsets)
+
+
+def ss_sort_host(chars, offsets, lengths, fixed_len, perm_out, lcp_out, runs=1, stream=None):
+    """Host arrays (numpy, or pinned CPU tensors) in and out; the copies happen inside the call."""
+    n = int(offsets.shape[0])
+    nbytes = int(chars.nbytes) if isinstance(chars, np.ndarray) else int(chars.numel() * chars.element_size())
+    _check(lib().ss_sort_host(_ptr(chars), nbytes, _ptr(offsets), _ptr(lengths), int(fixed_len), n, int(runs),
+                              _ptr(perm_out), _ptr(lcp_out), _stream(stream)))
+
+
+def ss_sort_batch(requests, stream=None):
+    """requests: list of dicts with keys chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, status_out."""
+    arr = (Request * max(1, len(requests)))()
+    for k, q in enumerate(requests):
+        arr[k] = Request(_dev(q["chars"], "uint8", "chars"), _off(q["offsets"]),
+                         _dev(q.get("lengths"), "int32", "lengths"), int(q.get("fixed_len", 0)), int(q["n"]),
+                         _dev(q["perm_out"], "int32", "perm_out"), _dev(q["lcp_out"], "int32", "lcp_out"),
+                         _dev(q.get("status_out"), "int32", "status_out"))
+    _check(lib().ss_sort_batch(C.cast(arr, C.c_void_p), len(requests), _stream(stream)))
+
+
+def ss_merge(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+             run_base=None, stream=None):
+    rb = np.ascontiguousarray(np.asarray(run_begin, dtype=np.uint32))
+    K = rb.shape[0] - 1
+    base = None if run_base is None else np.ascontiguousarray(np.asarray(run_base, dtype=np.uint32))
+    _check(lib().ss_merge(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
+                          int(fixed_len), _dev(run_perm, "int32", "run_perm"), _dev(run_lcp, "int32", "run_lcp"),
+                          rb.ctypes.data, None if base is None else base.ctypes.data, K,
+                          _dev(perm_out, "int32", "perm_out"), _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+
+
+def ss_gather_keys(chars, offsets, lengths, fixed_len, n, depth, keys_out, stream=None):
+    _check(lib().ss_gather_keys(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
+                                int(fixed_len), int(n), _dev(depth, "int32", "depth"), _off(keys_out),
+                                _stream(stream)))
+
+
+def ss_splitters(sample, a, d, x_out, stream=None):
+    _check(lib().ss_splitters(_off(sample), int(a), int(d), _off(x_out), _stream(stream)))
+
+
+def ss_classify(keys, n, x, d, bucket_out, bucket_begin_out, order_out, stream=None):
+    _check(lib().ss_classify(_off(keys), int(n), _off(x), int(d), _dev(bucket_out, "int16", "bucket_out"),
+                             _dev(bucket_begin_out, "int32", "bucket_begin_out"),
+                             _dev(order_out, "int32", "order_out"), _stream(stream)))
+
+
+def profile_enable(on: bool = True):
+    _check(lib().ss_profile_enable(1 if on else 0))
+
+
+def profile_reset():
+    _check(lib().ss_profile_reset())
+
+
+def profile_read(cap: int = 64):
+    """{kernel name: (launches, total ms, units)} of the library's own launches since the last reset."""
+    names = C.create_string_buffer(48 * cap)
+    launches = (C.c_uint64 * cap)()
+    ms = (C.c_double * cap)()
+    units = (C.c_uint64 * cap)()
+    k = lib().ss_profile_read(names, launches, ms, units, cap)
+    out = {}
+    for i in range(min(k, cap)):
+        nm = names.raw[48 * i: 48 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(ms[i]), int(units[i]))
+    return out
+
+
+def launch_count() -> int:
+    return int(lib().ss_launch_count())

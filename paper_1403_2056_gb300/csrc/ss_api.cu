@@ -1,0 +1,403 @@
+// C ABI of the string sorter: argument checks, scratch pool, error detail,
+// optional per-kernel timing.  Every entry point forwards to the kernels in
+// ss_engine.cu / ss_merge.cu; nothing here computes on the host.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+static thread_local std::string t_detail;
+
+void set_error_detail(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    t_detail = buf;
+}
+
+int cuda_fail(cudaError_t e, const char *what) {
+    set_error_detail("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return SS_ERR_CUDA;
+}
+
+// ---------------------------------------------------------- scratch pool
+// One memory pool per device, owned by the library, keeping freed blocks
+// for reuse (release threshold = unlimited).
+
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t pool_for_current() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    std::lock_guard<std::mutex> lk(g_pool_mu);
+    auto it = g_pools.find(dev);
+    if (it != g_pools.end()) return it->second;
+    cudaMemPoolProps props;
+    memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    uint64_t thr = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    g_pools[dev] = pool;
+    return pool;
+}
+
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    cudaMemPool_t pool = pool_for_current();
+    if (!pool) return cudaErrorMemoryAllocation;
+    return cudaMallocFromPoolAsync(p, bytes ? bytes : 256, pool, s);
+}
+
+cudaError_t scratch_free(void *p, cudaStream_t s) {
+    if (!p) return cudaSuccess;
+    return cudaFreeAsync(p, s);
+}
+
+// ------------------------------------------------------ host staging
+struct Staging {
+    void *p = nullptr;
+    size_t cap = 0;
+    ~Staging() {
+        if (p) cudaFreeHost(p);
+    }
+};
+static thread_local Staging t_staging;
+
+void *host_staging(size_t bytes) {
+    if (t_staging.cap < bytes) {
+        if (t_staging.p) cudaFreeHost(t_staging.p);
+        t_staging.p = nullptr;
+        size_t cap = bytes < 4096 ? 4096 : bytes;
+        if (cudaMallocHost(&t_staging.p, cap) != cudaSuccess) {
+            cudaGetLastError();
+            t_staging.p = malloc(cap);   // pageable fallback for the counter readback only
+        }
+        t_staging.cap = cap;
+    }
+    return t_staging.p;
+}
+
+// ------------------------------------------------------------ profiling
+static std::atomic<int> g_prof_on{0};
+static std::atomic<uint64_t> g_launches{0};
+struct ProfRec {
+    uint64_t launches = 0;
+    uint64_t units = 0;
+    double ms = 0;
+};
+static std::mutex g_prof_mu;
+static std::vector<std::pair<std::string, ProfRec>> g_prof;
+struct PendingEv {
+    std::string name;
+    cudaEvent_t a, b;
+    uint64_t units;
+};
+static thread_local std::vector<PendingEv> t_pending;
+static thread_local cudaEvent_t t_open = nullptr;
+
+static void prof_flush() {
+    for (auto &pe : t_pending) {
+        float ms = 0;
+        cudaEventSynchronize(pe.b);
+        cudaEventElapsedTime(&ms, pe.a, pe.b);
+        cudaEventDestroy(pe.a);
+        cudaEventDestroy(pe.b);
+        std::lock_guard<std::mutex> lk(g_prof_mu);
+        bool found = false;
+        for (auto &r : g_prof)
+            if (r.first == pe.name) { r.second.launches++; r.second.ms += ms; r.second.units += pe.units; found = true; break; }
+        if (!found) {
+            ProfRec r;
+            r.launches = 1;
+            r.ms = ms;
+            r.units = pe.units;
+            g_prof.emplace_back(pe.name, r);
+        }
+    }
+    t_pending.clear();
+}
+
+void prof_begin(const char *name, cudaStream_t s) {
+    (void)name;
+    g_launches++;
+    if (!g_prof_on.load()) return;
+    cudaEventCreate(&t_open);
+    cudaEventRecord(t_open, s);
+}
+
+void prof_end(const char *name, cudaStream_t s, uint64_t units) {
+    if (!g_prof_on.load() || !t_open) return;
+    cudaEvent_t b;
+    cudaEventCreate(&b);
+    cudaEventRecord(b, s);
+    t_pending.push_back(PendingEv{name, t_open, b, units});
+    t_open = nullptr;
+    if (t_pending.size() > 4096) prof_flush();
+}
+
+}  // namespace ss
+
+using namespace ss;
+
+static cudaStream_t as_stream(ss_stream_t s) { return reinterpret_cast<cudaStream_t>(s); }
+
+static ReqDesc make_req(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
+                        uint32_t n, uint32_t *perm, uint32_t *lcp, int32_t *status) {
+    ReqDesc r;
+    memset(&r, 0, sizeof(r));
+    r.chars = chars;
+    r.offsets = offsets;
+    r.lengths = lengths;
+    r.fixed_len = lengths ? 0 : fixed_len;
+    r.n = n;
+    r.perm_out = perm;
+    r.lcp_out = lcp;
+    r.status_out = status;
+    return r;
+}
+
+static int check_req(const ReqDesc &r, const char *who) {
+    if (r.n == 0) return SS_OK;
+    if (!r.chars || !r.offsets || !r.perm_out || !r.lcp_out) {
+        set_error_detail("%s: NULL pointer with n = %u", who, r.n);
+        return SS_ERR_INVALID;
+    }
+    if (r.n == 0xFFFFFFFFu) {
+        set_error_detail("%s: n = 2^32 - 1 is beyond the limit 2^32 - 2", who);
+        return SS_ERR_TOO_LARGE;
+    }
+    return SS_OK;
+}
+
+extern "C" {
+
+int ss_version(void) { return 100; }
+
+int ss_last_error_detail(char *buf, size_t len) {
+    const std::string &d = t_detail;
+    if (buf && len) {
+        size_t k = d.size() < len - 1 ? d.size() : len - 1;
+        memcpy(buf, d.data(), k);
+        buf[k] = 0;
+    }
+    return (int)d.size();
+}
+
+int ss_sort_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len, uint32_t n,
+               uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
+    t_detail.clear();
+    ReqDesc r = make_req(chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, nullptr);
+    int rc = check_req(r, "ss_sort_ex");
+    if (rc != SS_OK || n == 0) return rc;
+    return engine_sort(&r, 1, as_stream(stream));
+}
+
+int ss_sort(const uint8_t *chars, const uint64_t *offsets, uint32_t n, uint32_t *perm_out, uint32_t *lcp_out,
+            ss_stream_t stream) {
+    return ss_sort_ex(chars, offsets, nullptr, 0, n, perm_out, lcp_out, stream);
+}
+
+int ss_sort_batch(const ss_request *reqs, uint32_t count, ss_stream_t stream) {
+    t_detail.clear();
+    if (count == 0) return SS_OK;
+    if (!reqs) {
+        set_error_detail("ss_sort_batch: NULL request array");
+        return SS_ERR_INVALID;
+    }
+    std::vector<ReqDesc> v(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const ss_request &q = reqs[i];
+        v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
+        int rc = check_req(v[i], "ss_sort_batch");
+        if (rc != SS_OK) return rc;
+    }
+    return engine_sort(v.data(), count, as_stream(stream));
+}
+
+int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host,
+                 const uint32_t *lengths_host, uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host,
+                 uint32_t *lcp_host, ss_stream_t stream) {
+    t_detail.clear();
+    if (n == 0) return SS_OK;
+    if (!chars_host || !offsets_host || !perm_host || !lcp_host || chars_len == 0) {
+        set_error_detail("ss_sort_host: NULL pointer or empty chars with n = %u", n);
+        return SS_ERR_INVALID;
+    }
+    if (n == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
+    if (runs == 0) runs = 1;
+    if (runs > n) runs = n;
+    cudaStream_t st = as_stream(stream);
+    const size_t A = 255;
+    size_t cbytes = (chars_len + 15) & ~(size_t)15;   // aligned words past the end stay inside
+    size_t nb4 = (4ull * n + A) & ~A, nb8 = (8ull * n + A) & ~A;
+    size_t bytes = ((cbytes + A) & ~A) + nb8 + (lengths_host ? nb4 : 0) + 2 * nb4 + (runs > 1 ? 2 * nb4 : 0) + 1024;
+    void *block = nullptr;
+    cudaError_t e = scratch_alloc(&block, bytes, st);
+    if (e) {
+        cudaGetLastError();
+        set_error_detail("ss_sort_host: device allocation of %zu bytes failed", bytes);
+        return SS_ERR_OOM;
+    }
+    char *p = (char *)block;
+    uint8_t *d_chars = (uint8_t *)p;
+    p += (cbytes + A) & ~A;
+    uint64_t *d_off = (uint64_t *)p;
+    p += nb8;
+    uint32_t *d_len = nullptr;
+    if (lengths_host) {
+        d_len = (uint32_t *)p;
+        p += nb4;
+    }
+    uint32_t *d_perm = (uint32_t *)p;
+    p += nb4;
+    uint32_t *d_lcp = (uint32_t *)p;
+    p += nb4;
+    uint32_t *d_rperm = runs > 1 ? (uint32_t *)p : nullptr;
+    uint32_t *d_rlcp = runs > 1 ? (uint32_t *)(p + nb4) : nullptr;
+    int rc = SS_OK;
+    do {
+        if (cbytes > chars_len && (e = cudaMemsetAsync(d_chars + chars_len, 0, cbytes - chars_len, st))) break;
+        if ((e = cudaMemcpyAsync(d_chars, chars_host, chars_len, cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(d_off, offsets_host, 8ull * n, cudaMemcpyHostToDevice, st))) break;
+        if (lengths_host && (e = cudaMemcpyAsync(d_len, lengths_host, 4ull * n, cudaMemcpyHostToDevice, st))) break;
+        if (runs <= 1) {
+            ReqDesc r = make_req(d_chars, d_off, d_len, fixed_len, n, d_perm, d_lcp, nullptr);
+            rc = engine_sort(&r, 1, st);
+        } else {
+            // index-contiguous runs sorted together, then merged (Section 4)
+            std::vector<ReqDesc> rq(runs);
+            std::vector<uint32_t> rb(runs + 1);
+            for (uint32_t k = 0; k <= runs; k++) rb[k] = (uint32_t)((uint64_t)n * k / runs);
+            for (uint32_t k = 0; k < runs; k++)
+                rq[k] = make_req(d_chars, d_off + rb[k], d_len ? d_len + rb[k] : nullptr, fixed_len, rb[k + 1] - rb[k],
+                                 d_rperm + rb[k], d_rlcp + rb[k], nullptr);
+            rc = engine_sort(rq.data(), runs, st);
+            if (rc == SS_OK) {
+                ReqDesc set = make_req(d_chars, d_off, d_len, fixed_len, 0, nullptr, nullptr, nullptr);
+                rc = merge_runs(set, d_rperm, d_rlcp, rb.data(), rb.data(), runs, d_perm, d_lcp, st);
+            }
+        }
+        if (rc != SS_OK) break;
+        if ((e = cudaMemcpyAsync(perm_host, d_perm, 4ull * n, cudaMemcpyDeviceToHost, st))) break;
+        if ((e = cudaMemcpyAsync(lcp_host, d_lcp, 4ull * n, cudaMemcpyDeviceToHost, st))) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    if (e && rc == SS_OK) rc = cuda_fail(e, "ss_sort_host");
+    scratch_free(block, st);
+    return rc;
+}
+
+int ss_merge(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
+             const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
+             const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
+    t_detail.clear();
+    if (K == 0 || !run_begin_host) {
+        set_error_detail("ss_merge: K must be >= 1 with run_begin_host[K+1]");
+        return SS_ERR_INVALID;
+    }
+    if (run_begin_host[0] != 0) {
+        set_error_detail("ss_merge: run_begin_host[0] must be 0");
+        return SS_ERR_INVALID;
+    }
+    for (uint32_t k = 0; k < K; k++)
+        if (run_begin_host[k + 1] < run_begin_host[k]) {
+            set_error_detail("ss_merge: run_begin_host must be non-decreasing");
+            return SS_ERR_INVALID;
+        }
+    uint32_t total = run_begin_host[K];
+    if (total == 0) return SS_OK;
+    if (total == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
+    if (!chars || !offsets || !run_perm || !run_lcp || !perm_out || !lcp_out) {
+        set_error_detail("ss_merge: NULL pointer");
+        return SS_ERR_INVALID;
+    }
+    ReqDesc set = make_req(chars, offsets, lengths, fixed_len, 0, nullptr, nullptr, nullptr);
+    return merge_runs(set, run_perm, run_lcp, run_begin_host, run_base_host, K, perm_out, lcp_out, as_stream(stream));
+}
+
+int ss_gather_keys(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
+                   uint32_t n, const uint32_t *depth, uint64_t *keys_out, ss_stream_t stream) {
+    t_detail.clear();
+    if (n == 0) return SS_OK;
+    if (!chars || !offsets || !depth || !keys_out) {
+        set_error_detail("ss_gather_keys: NULL pointer");
+        return SS_ERR_INVALID;
+    }
+    ReqDesc r = make_req(chars, offsets, lengths, fixed_len, n, nullptr, nullptr, nullptr);
+    return engine_gather(r, depth, keys_out, as_stream(stream));
+}
+
+int ss_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, ss_stream_t stream) {
+    t_detail.clear();
+    if (!sample || !x_out || a == 0 || a > 2047 || d < 1 || d > (uint32_t)kMaxD) {
+        set_error_detail("ss_splitters: need 1 <= a <= 2047, 1 <= d <= %d and non-NULL pointers", kMaxD);
+        return SS_ERR_INVALID;
+    }
+    return engine_splitters(sample, a, d, x_out, as_stream(stream));
+}
+
+int ss_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
+                uint32_t *bucket_begin_out, uint32_t *order_out, ss_stream_t stream) {
+    t_detail.clear();
+    if (d < 1 || d > (uint32_t)kMaxD || !x || !bucket_begin_out || (n && (!keys || !bucket_out || !order_out))) {
+        set_error_detail("ss_classify: need 1 <= d <= %d and non-NULL pointers", kMaxD);
+        return SS_ERR_INVALID;
+    }
+    if (n == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
+    return engine_classify(keys, n, x, d, bucket_out, bucket_begin_out, order_out, as_stream(stream));
+}
+
+int ss_profile_enable(int on) {
+    g_prof_on.store(on ? 1 : 0);
+    return SS_OK;
+}
+
+int ss_profile_reset(void) {
+    prof_flush();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_prof.clear();
+    g_launches.store(0);
+    return SS_OK;
+}
+
+int ss_profile_read(char *names48, uint64_t *launches, double *total_ms, uint64_t *units, int cap) {
+    prof_flush();
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    int k = 0;
+    for (auto &r : g_prof) {
+        if (k >= cap) break;
+        if (names48) {
+            memset(names48 + 48 * k, 0, 48);
+            strncpy(names48 + 48 * k, r.first.c_str(), 47);
+        }
+        if (launches) launches[k] = r.second.launches;
+        if (total_ms) total_ms[k] = r.second.ms;
+        if (units) units[k] = r.second.units;
+        k++;
+    }
+    return (int)g_prof.size();
+}
+
+uint64_t ss_launch_count(void) { return g_launches.load(); }
+
+}  // extern "C"

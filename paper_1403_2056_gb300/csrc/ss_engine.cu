@@ -1,0 +1,1205 @@
+// Super scalar string sample sort (S5) on one GB300, level-synchronous.
+//
+// Every recursion level of the paper's S5 (Algorithm 1, applied recursively
+// as in Section 3.5) runs as a handful of kernels over ALL segments that are
+// still larger than the base-case threshold, whatever request they belong to:
+//
+//   k_build_trees  sample (alpha = 2), sort, pick splitters with the
+//                  skip-equal-samples recursion (Section 3.4)      one CTA / segment
+//   k_classify     tree descent + equality test per 8-byte key,
+//                  bucket buffer, per-tile histogram (Alg. 1 loops)  one CTA / tile
+//   k_scan_*       exclusive prefix sum over the bucket-major
+//                  (segment, bucket, tile) counters (Theorem 1)
+//   k_scatter      stable out-of-place redistribution of (index, next key),
+//                  final placement of singletons and all-equal buckets
+//   k_buckets      child segments: big ones to the next level, small ones to
+//                  the base case; bucket boundaries recorded for LCPs
+//
+// Segments of at most kSmallMax strings are sorted completely by the base
+// case (k_small_warp / k_small_cta), which also emits their LCPs
+// (the role of LCP insertion sort, Algorithm 5).  The LCP between the last
+// string of one bucket and the first of the next is depth + lcp of their keys
+// at that depth (Section 4.4, "LCPs for free"), computed in k_boundary once all
+// strings are placed.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+// --------------------------------------------------------------- helpers
+
+__host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size) {
+    // v + 1 = 2^d about size / 1024 (children near 512 strings), d in [2, 10]
+    uint32_t q = (size + 1023) / 1024;
+    uint32_t d = 0;
+    while ((1u << d) < q) d++;
+    if (d < 2) d = 2;
+    if (d > (uint32_t)kMaxD) d = kMaxD;
+    return d;
+}
+
+__host__ __device__ __forceinline__ uint32_t tiles_of(uint32_t size) { return (size + kTile - 1) / kTile; }
+__host__ __device__ __forceinline__ uint32_t buckets_of(uint32_t d) { return (2u << d) - 1u; }
+
+__device__ __forceinline__ uint32_t find_req(const ReqDesc *reqs, uint32_t nreq, uint32_t g) {
+    uint32_t lo = 0, hi = nreq;   // last request with base <= g
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (reqs[mid].base <= g) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// last segment whose field (prefix) <= t
+template <typename F>
+__device__ __forceinline__ uint32_t find_seg(const BigSeg *segs, uint32_t nseg, uint32_t t, F field) {
+    uint32_t lo = 0, hi = nseg;
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (field(segs[mid]) <= t) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+    uint32_t m;
+    asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+    return m;
+}
+
+// ------------------------------------------------------------ k_init
+
+__global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t *idx0, uint64_t *key0) {
+    for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
+        uint32_t r = find_req(reqs, nreq, g);
+        const ReqDesc &R = reqs[r];
+        uint32_t i = g - R.base;
+        idx0[g] = i;
+        key0[g] = load_key(R, i, 0);
+        if (i == 0) {
+            R.lcp_out[0] = 0;
+            if (R.n == 1) R.perm_out[0] = 0;
+        }
+    }
+}
+
+// ------------------------------------------------------ k_setup_big
+// Exclusive prefix sums over the big list: tile_base, cnt_base, bkt_base, scan_base.
+
+__global__ void __launch_bounds__(1024) k_setup_big(BigSeg *segs, uint32_t nseg) {
+    __shared__ uint32_t wsum[4][32];
+    __shared__ uint32_t carry[4];
+    if (threadIdx.x < 4) carry[threadIdx.x] = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = 0; base < nseg; base += 1024) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t v[4] = {0, 0, 0, 0};
+        if (i < nseg) {
+            BigSeg s = segs[i];
+            uint32_t d = choose_d(s.size);
+            uint32_t t = tiles_of(s.size);
+            uint32_t B = buckets_of(d);
+            v[0] = t;
+            v[1] = B * t;
+            v[2] = B;
+            v[3] = s.size;
+        }
+        uint32_t incl[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            uint32_t x = v[k];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= (uint32_t)o) x += y;
+            }
+            incl[k] = x;
+            if (lane == 31) wsum[k][warp] = x;
+        }
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                uint32_t x = wsum[k][lane];
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                    if (lane >= (uint32_t)o) x += y;
+                }
+                wsum[k][lane] = x;   // inclusive over warps
+            }
+        }
+        __syncthreads();
+        uint32_t excl[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) excl[k] = carry[k] + (warp ? wsum[k][warp - 1] : 0) + incl[k] - v[k];
+        if (i < nseg) {
+            BigSeg s = segs[i];
+            s.d = choose_d(s.size);
+            s.tiles = v[0];
+            s.tile_base = excl[0];
+            s.cnt_base = excl[1];
+            s.bkt_base = excl[2];
+            s.scan_base = excl[3];
+            segs[i] = s;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+#pragma unroll
+            for (int k = 0; k < 4; k++) carry[k] += wsum[k][31];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------ k_build_trees
+
+// bitonic sort of n (power of two) u64 keys in shared memory
+__device__ void bitonic_u64(uint64_t *s, uint32_t n) {
+    for (uint32_t k = 2; k <= n; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+            for (uint32_t t = threadIdx.x; t < n / 2; t += blockDim.x) {
+                uint32_t i = 2 * t - (t & (j - 1));   // lower index of the pair
+                uint32_t l = i + j;
+                bool up = (i & k) == 0;
+                uint64_t a = s[i], b = s[l];
+                if ((a > b) == up) { s[i] = b; s[l] = a; }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+// Splitter pick of Section 3.4 on a sorted sample s[0..a): breadth-first over
+// the implicit tree; node state (lo, hi, has_right, right, left).
+struct PickNode {
+    uint32_t lo, hi, has_right, pad;
+    uint64_t right, left;
+};
+
+__device__ void pick_splitters(const uint64_t *s, uint32_t a, uint32_t d, uint64_t *x, PickNode *cur, PickNode *nxt) {
+    if (threadIdx.x == 0) cur[0] = PickNode{0, a, 0, 0, 0ull, 0ull};
+    __syncthreads();
+    for (uint32_t l = 0; l < d; l++) {
+        uint32_t nodes = 1u << l;
+        uint32_t span = 1u << (d - l);   // slots covered: span - 1
+        for (uint32_t j = threadIdx.x; j < nodes; j += blockDim.x) {
+            PickNode nd = cur[j];
+            uint32_t xm = j * span + span / 2 - 1;
+            PickNode L, R;
+            if (nd.lo >= nd.hi) {
+                uint64_t val = nd.has_right ? nd.right : nd.left;
+                x[xm] = val;
+                L = PickNode{0, 0, 1, 0, val, nd.left};
+                R = PickNode{0, 0, nd.has_right, 0, nd.right, val};
+            } else {
+                uint32_t m = nd.lo + (nd.hi - nd.lo) / 2;
+                uint64_t sv = s[m];
+                uint32_t lo = nd.lo, hi = m;   // first index in [lo, m] equal to sv
+                while (lo < hi) {
+                    uint32_t mid = (lo + hi) / 2;
+                    if (s[mid] < sv) lo = mid + 1; else hi = mid;
+                }
+                uint32_t b = lo;
+                lo = m; hi = nd.hi;             // first index in [m, hi) greater than sv
+                while (lo < hi) {
+                    uint32_t mid = (lo + hi) / 2;
+                    if (s[mid] <= sv) lo = mid + 1; else hi = mid;
+                }
+                uint32_t ap = lo;
+                x[xm] = sv;
+                L = PickNode{nd.lo, b, 1, 0, sv, nd.left};
+                R = PickNode{ap, nd.hi, nd.has_right, 0, nd.right, sv};
+            }
+            if (l + 1 < d) {
+                nxt[2 * j] = L;
+                nxt[2 * j + 1] = R;
+            }
+        }
+        __syncthreads();
+        PickNode *t = cur; cur = nxt; nxt = t;
+    }
+}
+
+struct TreeSmem {
+    uint64_t s[2 * (kMaxV + 1)];
+    PickNode n0[(kMaxV + 1) / 2], n1[(kMaxV + 1) / 2];
+};
+
+__global__ void __launch_bounds__(kThreads) k_build_trees(const BigSeg *segs, const uint64_t *key, uint64_t *splitters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TreeSmem &S = *reinterpret_cast<TreeSmem *>(smem_raw);
+    BigSeg sg = segs[blockIdx.x];
+    uint32_t d = sg.d;
+    uint32_t v = (1u << d) - 1;
+    uint32_t a = 2 * v + 1;            // alpha * v + alpha - 1 with alpha = 2
+    uint32_t P = a + 1;
+    uint64_t seed = ((uint64_t)sg.begin << 32) ^ (uint64_t)sg.depth * 0x9E3779B97F4A7C15ULL;
+    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) {
+        if (j < a) {
+            uint32_t pos = (uint32_t)(mix64(seed + j) % sg.size);
+            S.s[j] = key[sg.begin + pos];
+        } else {
+            S.s[j] = ~0ull;
+        }
+    }
+    __syncthreads();
+    bitonic_u64(S.s, P);
+    uint64_t *x = splitters + (size_t)blockIdx.x * kMaxV;
+    pick_splitters(S.s, a, d, x, S.n0, S.n1);
+}
+
+// stand-alone splitter pick (ss_splitters): sample given, a <= 2047
+__global__ void __launch_bounds__(kThreads) k_pick_only(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TreeSmem &S = *reinterpret_cast<TreeSmem *>(smem_raw);
+    uint32_t P = 1;
+    while (P < a) P <<= 1;
+    for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) S.s[j] = j < a ? sample[j] : ~0ull;
+    __syncthreads();
+    bitonic_u64(S.s, P);
+    pick_splitters(S.s, a, d, x, S.n0, S.n1);
+}
+
+// ------------------------------------------------------------ k_classify
+
+struct ClassifySmem {
+    uint64_t t[kMaxV + 1];   // level order, one-based (t[0] unused)
+    uint64_t x[kMaxV + 1];   // in order, x[v] unused
+    uint32_t cnt[kMaxB + 1];
+};
+
+// load the in-order splitters and build the level-order tree (Figure 1):
+// node i at level l, position j = i - 2^l holds x[(2j + 1) 2^(d-l-1) - 1]
+__device__ __forceinline__ void load_tree(const uint64_t *xs, uint32_t d, uint64_t *t, uint64_t *x) {
+    uint32_t v = (1u << d) - 1;
+    for (uint32_t k = threadIdx.x; k < v; k += blockDim.x) x[k] = xs[k];
+    __syncthreads();
+    for (uint32_t i = threadIdx.x + 1; i <= v; i += blockDim.x) {
+        uint32_t l = 31 - __clz(i);
+        uint32_t j = i - (1u << l);
+        t[i] = x[((2 * j + 1) << (d - l - 1)) - 1];
+    }
+}
+
+// bucket of key c: descend with i := 2i + [c > t_i], then one equality test
+__device__ __forceinline__ uint32_t classify_one(uint64_t c, const uint64_t *t, const uint64_t *x, uint32_t d, uint32_t v) {
+    uint32_t i = 1;
+    for (uint32_t l = 0; l < d; l++) i = 2 * i + (c > t[i] ? 1u : 0u);
+    uint32_t r = i - (v + 1);
+    return 2 * r + ((r < v && x[r] == c) ? 1u : 0u);
+}
+
+__global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *segs, uint32_t nseg, const uint64_t *key,
+                                                       const uint64_t *splitters, uint16_t *obuf, uint32_t *counts) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ClassifySmem &S = *reinterpret_cast<ClassifySmem *>(smem_raw);
+    const uint32_t tile = blockIdx.x;
+    const uint32_t si = find_seg(segs, nseg, tile, [](const BigSeg &s) { return s.tile_base; });
+    const BigSeg sg = segs[si];
+    const uint32_t tl = tile - sg.tile_base;
+    const uint32_t d = sg.d, v = (1u << d) - 1, B = 2 * v + 1;
+    load_tree(splitters + (size_t)si * kMaxV, d, S.t, S.x);
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) S.cnt[b] = 0;
+    __syncthreads();
+
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t seg_end = sg.begin + sg.size;
+    const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
+    // four interleaved descents per thread (Section 3.3: unrolled, interleaved loops)
+    for (uint32_t it = 0; it < (uint32_t)kItems; it += 4) {
+        uint64_t c[4];
+        uint32_t p[4], node[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            p[u] = wbeg + (it + u) * 32 + lane;
+            ok[u] = p[u] < seg_end;
+            c[u] = ok[u] ? key[p[u]] : 0ull;
+            node[u] = 1;
+        }
+        for (uint32_t l = 0; l < d; l++) {
+#pragma unroll
+            for (int u = 0; u < 4; u++) node[u] = 2 * node[u] + (c[u] > S.t[node[u]] ? 1u : 0u);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            uint32_t r = node[u] - (v + 1);
+            uint32_t b = 2 * r + ((r < v && S.x[r] == c[u]) ? 1u : 0u);
+            if (ok[u]) obuf[p[u]] = (uint16_t)b;
+            uint32_t key_b = ok[u] ? b : 0xFFFFu;
+            uint32_t peers = __match_any_sync(0xffffffffu, key_b);
+            if (ok[u] && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&S.cnt[b], (uint32_t)__popc(peers));
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) counts[sg.cnt_base + b * sg.tiles + tl] = S.cnt[b];
+}
+
+// ------------------------------------------------------------ scan
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kThreads * kScanItems;   // 4096
+
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, uint32_t *total) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < kWarps ? wsum[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= (uint32_t)o) w += y;
+        }
+        if (lane < kWarps) wsum[lane] = w;
+    }
+    __syncthreads();
+    uint32_t r = (warp ? wsum[warp - 1] : 0) + incl - x;
+    if (total) *total = wsum[kWarps - 1];
+    __syncthreads();
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t *a, uint32_t n, uint32_t *partial) {
+    __shared__ uint32_t wsum[32];
+    uint32_t base = blockIdx.x * kScanChunk;
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        uint32_t i = base + k * kThreads + threadIdx.x;
+        if (i < n) s += a[i];
+    }
+    uint32_t total;
+    block_excl_scan(s, wsum, &total);
+    if (threadIdx.x == 0) partial[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partial, uint32_t np) {
+    __shared__ uint32_t wsum[32];
+    __shared__ uint32_t carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (uint32_t base = 0; base < np; base += 1024) {
+        uint32_t i = base + threadIdx.x;
+        uint32_t x = i < np ? partial[i] : 0;
+        uint32_t incl = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            uint32_t w = wsum[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= (uint32_t)o) w += y;
+            }
+            wsum[lane] = w;
+        }
+        __syncthreads();
+        uint32_t ex = carry + (warp ? wsum[warp - 1] : 0) + incl - x;
+        if (i < np) partial[i] = ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += wsum[31];
+        __syncthreads();
+    }
+}
+
+// in-place exclusive scan of a chunk plus its partial offset
+__global__ void __launch_bounds__(kThreads) k_scan_down(uint32_t *a, uint32_t n, const uint32_t *partial) {
+    __shared__ uint32_t wsum[32];
+    uint32_t base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;   // thread-contiguous
+    uint32_t v[kScanItems];
+    uint32_t s = 0;
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        uint32_t i = base + k;
+        v[k] = i < n ? a[i] : 0;
+        s += v[k];
+    }
+    uint32_t off = block_excl_scan(s, wsum, nullptr) + partial[blockIdx.x];
+#pragma unroll
+    for (int k = 0; k < kScanItems; k++) {
+        uint32_t i = base + k;
+        if (i < n) a[i] = off;
+        off += v[k];
+    }
+}
+
+// ------------------------------------------------------------ k_scatter
+
+struct ScatterSmem {
+    uint32_t wpos[kWarps][kMaxB + 1];   // per warp: count, then running output position
+    uint32_t bstart[kMaxB + 1];         // global start of each bucket
+    uint32_t binfo[kMaxB + 1];          // delta | final << 4 | done << 5 | nulpos << 8
+};
+
+enum { MODE_SORT = 0, MODE_CLASSIFY = 1 };
+
+// position of (bucket b, tile tl) from the scanned counters
+__device__ __forceinline__ uint32_t tile_pos(const BigSeg &sg, const uint32_t *scan, uint32_t b, uint32_t tl) {
+    return sg.begin + scan[sg.cnt_base + b * sg.tiles + tl] - sg.scan_base;
+}
+
+__device__ __forceinline__ uint32_t bucket_start(const BigSeg &sg, const uint32_t *scan, uint32_t b, uint32_t B) {
+    return b < B ? tile_pos(sg, scan, b, 0) : sg.begin + sg.size;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32_t nseg, const ReqDesc *reqs,
+                                                      const uint32_t *idx_in, const uint64_t *key_in,
+                                                      const uint16_t *obuf, const uint32_t *scan,
+                                                      const uint64_t *splitters, uint32_t *idx_out,
+                                                      uint64_t *key_out, uint32_t *counters) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    const uint32_t tile = blockIdx.x;
+    const uint32_t si = find_seg(segs, nseg, tile, [](const BigSeg &s) { return s.tile_base; });
+    const BigSeg sg = segs[si];
+    const uint32_t tl = tile - sg.tile_base;
+    const uint32_t d = sg.d, v = (1u << d) - 1, B = 2 * v + 1;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t seg_end = sg.begin + sg.size;
+    const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
+    const uint64_t *xs = splitters + (size_t)si * kMaxV;
+
+    for (uint32_t k = threadIdx.x; k < kWarps * (kMaxB + 1); k += blockDim.x) (&S.wpos[0][0])[k] = 0;
+    __syncthreads();
+    // phase A: per-warp bucket counts of its contiguous span
+    for (uint32_t it = 0; it < (uint32_t)kItems; it++) {
+        uint32_t p = wbeg + it * 32 + lane;
+        bool ok = p < seg_end;
+        uint32_t b = ok ? obuf[p] : 0xFFFFu;
+        uint32_t peers = __match_any_sync(0xffffffffu, b);
+        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][b] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // phase B: running positions per (warp, bucket); bucket facts
+    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
+        uint32_t pos = tile_pos(sg, scan, b, tl);
+#pragma unroll
+        for (int w = 0; w < kWarps; w++) {
+            uint32_t c = S.wpos[w][b];
+            S.wpos[w][b] = pos;
+            pos += c;
+        }
+        if (MODE == MODE_SORT) {
+            uint32_t st = bucket_start(sg, scan, b, B);
+            uint32_t en = bucket_start(sg, scan, b + 1, B);
+            uint32_t r = b >> 1;
+            uint32_t delta, done = 0, np = 0;
+            if (b & 1) {
+                uint64_t xr = xs[r];
+                np = nulpos(xr);
+                done = np < 8;   // equal keys that hold the end of the string: all equal
+                delta = 8;
+            } else {
+                delta = (r == 0 || r == v) ? 0u : lcp8(xs[r - 1], xs[r]);
+            }
+            uint32_t fin = (en - st == 1) || done;
+            S.bstart[b] = st;
+            S.binfo[b] = delta | (fin << 4) | (done << 5) | (np << 8);
+        }
+    }
+    __syncthreads();
+    // phase C: stable placement; lanes in order inside the warp, warps in order inside the tile
+    for (uint32_t it = 0; it < (uint32_t)kItems; it += 4) {
+        uint32_t pos[4], id[4], bk[4];
+        bool ok[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            uint32_t p = wbeg + (it + u) * 32 + lane;
+            ok[u] = p < seg_end;
+            bk[u] = ok[u] ? obuf[p] : 0xFFFFu;
+            id[u] = ok[u] ? (MODE == MODE_SORT ? idx_in[p] : p - sg.begin) : 0u;
+            uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
+            uint32_t rank = __popc(peers & lanemask_lt());
+            uint32_t basep = ok[u] ? S.wpos[warp][bk[u]] : 0u;
+            pos[u] = basep + rank;
+            __syncwarp();
+            if (ok[u] && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][bk[u]] = basep + __popc(peers);
+            __syncwarp();
+        }
+        if (MODE == MODE_CLASSIFY) {
+#pragma unroll
+            for (int u = 0; u < 4; u++)
+                if (ok[u]) idx_out[pos[u] - sg.begin] = id[u];
+            continue;
+        }
+        const ReqDesc &R = reqs[sg.req];
+        uint64_t nk[4];
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            nk[u] = 0;
+            if (!ok[u]) continue;
+            uint32_t info = S.binfo[bk[u]];
+            if (info & 16u) continue;   // final: no next key
+            uint32_t delta = info & 15u;
+            uint32_t p = wbeg + (it + u) * 32 + lane;
+            nk[u] = delta == 0 ? key_in[p] : load_key(R, id[u], sg.depth + delta);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; u++) {
+            if (!ok[u]) continue;
+            uint32_t info = S.binfo[bk[u]];
+            uint32_t q = pos[u];
+            if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
+            if (info & 16u) {
+                uint32_t local = q - R.base;
+                R.perm_out[local] = id[u];
+                if ((info & 32u) && q > S.bstart[bk[u]]) R.lcp_out[local] = sg.depth + (info >> 8);
+            } else {
+                idx_out[q] = id[u];
+                key_out[q] = nk[u];
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------ k_buckets
+
+__device__ __forceinline__ void push_small(SmallTask *tiny, SmallTask *mid, SmallTask *large, const Caps &caps,
+                                           uint32_t *counters, SmallTask t) {
+    if (t.size <= kTinyMax) {
+        uint32_t k = atomicAdd(counters + C_NTINY, 1u);
+        atomicAdd(counters + C_E_TINY, t.size);
+        if (k < caps.small_tiny) tiny[k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
+    } else if (t.size <= kMidMax) {
+        uint32_t k = atomicAdd(counters + C_NMID, 1u);
+        atomicAdd(counters + C_E_MID, t.size);
+        if (k < caps.small_mid) mid[k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
+    } else {
+        uint32_t k = atomicAdd(counters + C_NLARGE, 1u);
+        atomicAdd(counters + C_E_LARGE, t.size);
+        if (k < caps.small_large) large[k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32_t nseg, uint32_t npairs,
+                                                      const uint32_t *scan, const uint64_t *splitters,
+                                                      uint32_t next_parity, BigSeg *next_big, SmallTask *tiny,
+                                                      SmallTask *mid, SmallTask *large, Boundary *bounds,
+                                                      Caps caps, uint32_t *counters) {
+    uint32_t pr = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pr >= npairs) return;
+    uint32_t si = find_seg(segs, nseg, pr, [](const BigSeg &s) { return s.bkt_base; });
+    BigSeg sg = segs[si];
+    uint32_t b = pr - sg.bkt_base;
+    uint32_t v = (1u << sg.d) - 1, B = 2 * v + 1;
+    if (b >= B) return;
+    uint32_t st = bucket_start(sg, scan, b, B);
+    uint32_t en = bucket_start(sg, scan, b + 1, B);
+    if (en <= st) return;
+    if (st > sg.begin) {
+        uint32_t k = atomicAdd(counters + C_NBOUND, 1u);
+        if (k < caps.bound) bounds[k] = Boundary{st, sg.depth, sg.req};
+        else set_error(counters, E_BOUND_OVERFLOW, k);
+    }
+    uint32_t size = en - st;
+    if (size == 1) return;
+    const uint64_t *xs = splitters + (size_t)si * kMaxV;
+    uint32_t r = b >> 1, delta;
+    if (b & 1) {
+        if (has_zero(xs[r])) return;   // all equal and complete: placed by k_scatter
+        delta = 8;
+    } else {
+        delta = (r == 0 || r == v) ? 0u : lcp8(xs[r - 1], xs[r]);
+    }
+    uint32_t depth = sg.depth + delta;
+    if (size > kSmallMax) {
+        uint32_t k = atomicAdd(counters + C_NBIG, 1u);
+        if (k < caps.big) {
+            BigSeg c{};
+            c.begin = st; c.size = size; c.depth = depth; c.req = sg.req;
+            next_big[k] = c;
+            uint32_t d = choose_d(size), t = tiles_of(size), Bc = buckets_of(d);
+            atomicAdd(counters + C_TILES, t);
+            atomicAdd(counters + C_COUNTS, Bc * t);
+            atomicAdd(counters + C_PAIRS, Bc);
+            atomicAdd(counters + C_ELEMS, size);
+        } else {
+            set_error(counters, E_BIG_OVERFLOW, k);
+        }
+    } else {
+        push_small(tiny, mid, large, caps, counters, SmallTask{st, size, depth, sg.req, next_parity});
+    }
+}
+
+// ------------------------------------------------------- base case sorters
+// A base-case segment shares its first `depth` characters.  Repeat: sort by
+// (group, key, index); neighbours of one group with different keys are split
+// (LCP = depth + lcp of keys); equal keys that hold the string end are equal
+// strings (LCP = depth + their length past depth); groups of equal keys
+// without the end continue 8 characters deeper.  Groups are contiguous and
+// carry their first position as id, so sorting by it keeps them in place,
+// and positions already split never move.  The LCP belongs to the position
+// (every member of a group shares the key that fixed it).
+
+struct Elem {
+    uint32_t g;   // group id: first position of the group (0xFFFFFFFF: padding)
+    uint32_t i;   // string index
+    uint64_t k;   // key at the current depth
+};
+
+__device__ __forceinline__ bool elem_less(const Elem &a, const Elem &b) {
+    if (a.g != b.g) return a.g < b.g;
+    if (a.k != b.k) return a.k < b.k;
+    return a.i < b.i;   // inside a segment input order equals index order
+}
+
+__device__ __forceinline__ Elem shfl_xor_elem(const Elem &e, int m) {
+    Elem r;
+    r.g = __shfl_xor_sync(0xffffffffu, e.g, m);
+    r.i = __shfl_xor_sync(0xffffffffu, e.i, m);
+    r.k = __shfl_xor_sync(0xffffffffu, e.k, m);
+    return r;
+}
+
+__global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
+                                                         const uint32_t *idx0, const uint64_t *key0,
+                                                         const uint32_t *idx1, const uint64_t *key1) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t tk = gw; tk < ntask; tk += nw) {
+        SmallTask t = tasks[tk];
+        const uint32_t *idx = t.parity ? idx1 : idx0;
+        const uint64_t *key = t.parity ? key1 : key0;
+        const ReqDesc &R = reqs[t.req];
+        const uint32_t m = t.size;
+        Elem e;
+        if (lane < m) { e.g = 0; e.i = idx[t.begin + lane]; e.k = key[t.begin + lane]; }
+        else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k = ~0ull; }
+        uint32_t lcp = 0;
+        uint32_t depth = t.depth;
+        for (;;) {
+            // bitonic sort across the warp
+            for (int k = 2; k <= 32; k <<= 1) {
+                for (int j = k >> 1; j > 0; j >>= 1) {
+                    Elem o = shfl_xor_elem(e, j);
+                    bool up = (lane & k) == 0;
+                    bool lower = (lane & j) == 0;
+                    bool take_o = lower == up ? elem_less(o, e) : elem_less(e, o);
+                    if (take_o) e = o;
+                }
+            }
+            uint32_t pg = __shfl_up_sync(0xffffffffu, e.g, 1);
+            uint64_t pk = __shfl_up_sync(0xffffffffu, e.k, 1);
+            bool start = true;
+            if (lane > 0 && lane < m && pg == e.g) {
+                if (pk != e.k) lcp = depth + lcp8(pk, e.k);
+                else if (has_zero(e.k)) lcp = depth + nulpos(e.k);
+                else start = false;
+            }
+            if (lane >= m) start = true;
+            uint32_t sg = start ? lane : 0;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                uint32_t y = __shfl_up_sync(0xffffffffu, sg, o);
+                if (lane >= (uint32_t)o) sg = max(sg, y);
+            }
+            bool next_start = __shfl_down_sync(0xffffffffu, start, 1) || lane == 31;
+            bool active = lane < m && !(start && next_start);
+            if (lane < m) e.g = sg;
+            if (!__any_sync(0xffffffffu, active)) break;
+            depth += 8;
+            if (active) e.k = load_key(R, e.i, depth);
+        }
+        if (lane < m) {
+            uint32_t local = t.begin - R.base + lane;
+            R.perm_out[local] = e.i;
+            if (lane > 0) R.lcp_out[local] = lcp;
+        }
+    }
+}
+
+template <uint32_t CAP, int NT>
+struct SmallCtaSmem {
+    Elem e[CAP];
+    uint32_t lcp[CAP];
+    uint32_t flag[CAP];
+    uint32_t wtot[NT / 32];
+    uint32_t any;
+};
+
+// block-wide inclusive max-scan of per-position values v[0..P) held in smem (in place)
+template <uint32_t CAP, int NT>
+__device__ void block_max_scan(uint32_t *v, uint32_t P, uint32_t *wtot) {
+    constexpr uint32_t PER = CAP / NT;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t base = threadIdx.x * PER;
+    uint32_t run = 0;
+    uint32_t loc[PER];
+#pragma unroll
+    for (uint32_t k = 0; k < PER; k++) {
+        uint32_t x = (base + k < P) ? v[base + k] : 0;
+        run = max(run, x);
+        loc[k] = run;
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl = max(incl, y);
+    }
+    if (lane == 31) wtot[warp] = incl;
+    __syncthreads();
+    uint32_t prev = 0;
+    for (uint32_t w = 0; w < warp; w++) prev = max(prev, wtot[w]);
+    uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) ex = 0;
+    ex = max(ex, prev);
+#pragma unroll
+    for (uint32_t k = 0; k < PER; k++)
+        if (base + k < P) v[base + k] = max(loc[k], ex);
+    __syncthreads();
+}
+
+template <uint32_t CAP, int NT>
+__global__ void __launch_bounds__(NT) k_small_cta(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
+                                                  const uint32_t *idx0, const uint64_t *key0,
+                                                  const uint32_t *idx1, const uint64_t *key1) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallCtaSmem<CAP, NT> &S = *reinterpret_cast<SmallCtaSmem<CAP, NT> *>(smem_raw);
+    for (uint32_t tk = blockIdx.x; tk < ntask; tk += gridDim.x) {
+        SmallTask t = tasks[tk];
+        const uint32_t *idx = t.parity ? idx1 : idx0;
+        const uint64_t *key = t.parity ? key1 : key0;
+        const ReqDesc &R = reqs[t.req];
+        const uint32_t m = t.size;
+        uint32_t P = 1;
+        while (P < m) P <<= 1;
+        for (uint32_t i = threadIdx.x; i < P; i += NT) {
+            Elem e;
+            if (i < m) { e.g = 0; e.i = idx[t.begin + i]; e.k = key[t.begin + i]; }
+            else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k = ~0ull; }
+            S.e[i] = e;
+            S.lcp[i] = 0;
+        }
+        uint32_t depth = t.depth;
+        __syncthreads();
+        for (;;) {
+            // bitonic sort of S.e[0..P)
+            for (uint32_t k = 2; k <= P; k <<= 1) {
+                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                    for (uint32_t q = threadIdx.x; q < P / 2; q += NT) {
+                        uint32_t i = 2 * q - (q & (j - 1));
+                        uint32_t l = i + j;
+                        bool up = (i & k) == 0;
+                        Elem a = S.e[i], b = S.e[l];
+                        if (elem_less(b, a) == up) { S.e[i] = b; S.e[l] = a; }
+                    }
+                    __syncthreads();
+                }
+            }
+            // split groups, record LCPs
+            for (uint32_t i = threadIdx.x; i < P; i += NT) {
+                uint32_t start = 1;
+                if (i > 0 && i < m) {
+                    Elem p = S.e[i - 1], c = S.e[i];
+                    if (p.g == c.g) {
+                        if (p.k != c.k) S.lcp[i] = depth + lcp8(p.k, c.k);
+                        else if (has_zero(c.k)) S.lcp[i] = depth + nulpos(c.k);
+                        else start = 0;
+                    }
+                }
+                S.flag[i] = start ? i : 0;
+            }
+            if (threadIdx.x == 0) S.any = 0;
+            __syncthreads();
+            // starts (flag = own position) before the max-scan turns them into group ids
+            bool act_local = false;
+            for (uint32_t i = threadIdx.x; i < m; i += NT) {
+                bool st = (i == 0) || S.flag[i] != 0;
+                bool nst = (i + 1 >= m) || S.flag[i + 1] != 0;
+                if (!(st && nst)) act_local = true;
+            }
+            if (act_local) S.any = 1;
+            __syncthreads();
+            block_max_scan<CAP, NT>(S.flag, P, S.wtot);
+            bool any = S.any != 0;
+            for (uint32_t i = threadIdx.x; i < m; i += NT) S.e[i].g = S.flag[i];
+            __syncthreads();
+            if (!any) break;
+            depth += 8;
+            // reload keys of elements in groups of two or more
+            for (uint32_t i = threadIdx.x; i < m; i += NT) {
+                uint32_t g = S.e[i].g;
+                bool single = (g == i) && (i + 1 >= m || S.e[i + 1].g == i + 1);
+                if (!single) S.e[i].k = load_key(R, S.e[i].i, depth);
+            }
+            __syncthreads();
+        }
+        for (uint32_t i = threadIdx.x; i < m; i += NT) {
+            uint32_t local = t.begin - R.base + i;
+            R.perm_out[local] = S.e[i].i;
+            if (i > 0) R.lcp_out[local] = S.lcp[i];
+        }
+        __syncthreads();
+    }
+}
+
+// ------------------------------------------------------------ k_boundary
+
+__global__ void k_boundary(const Boundary *bounds, uint32_t nb, const ReqDesc *reqs) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
+        Boundary b = bounds[k];
+        const ReqDesc &R = reqs[b.req];
+        uint32_t lp = b.pos - R.base;
+        uint32_t sa = R.perm_out[lp - 1], sb = R.perm_out[lp];
+        uint64_t ka = load_key(R, sa, b.depth), kb = load_key(R, sb, b.depth);
+        R.lcp_out[lp] = b.depth + lcp8(ka, kb);
+    }
+}
+
+__global__ void k_status(const ReqDesc *reqs, uint32_t nreq, int32_t code) {
+    for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nreq; r += gridDim.x * blockDim.x)
+        if (reqs[r].status_out) *reqs[r].status_out = code;
+}
+
+__global__ void k_gather(ReqDesc R, const uint32_t *depth, uint64_t *keys) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < R.n; i += gridDim.x * blockDim.x)
+        keys[i] = load_key(R, i, depth[i]);
+}
+
+__global__ void k_iota(uint32_t *a, uint32_t n) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) a[i] = i;
+}
+
+__global__ void k_bucket_begin(const BigSeg *seg, const uint32_t *scan, uint32_t *out) {
+    uint32_t B = buckets_of(seg->d);
+    for (uint32_t b = threadIdx.x; b <= B; b += blockDim.x) out[b] = bucket_start(*seg, scan, b, B) - seg->begin;
+}
+
+// ------------------------------------------------------------ host side
+
+static int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+static bool g_attrs_done[64];
+
+template <typename K>
+static cudaError_t set_smem(K kernel, size_t bytes) {
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+static cudaError_t ensure_attrs() {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (dev < 64 && g_attrs_done[dev]) return cudaSuccess;
+    cudaError_t e;
+    if ((e = set_smem(k_build_trees, sizeof(TreeSmem)))) return e;
+    if ((e = set_smem(k_pick_only, sizeof(TreeSmem)))) return e;
+    if ((e = set_smem(k_classify, sizeof(ClassifySmem)))) return e;
+    if ((e = set_smem(k_scatter<MODE_SORT>, sizeof(ScatterSmem)))) return e;
+    if ((e = set_smem(k_scatter<MODE_CLASSIFY>, sizeof(ScatterSmem)))) return e;
+    if ((e = set_smem(k_small_cta<kMidMax, 256>, sizeof(SmallCtaSmem<kMidMax, 256>)))) return e;
+    if ((e = set_smem(k_small_cta<kSmallMax, 512>, sizeof(SmallCtaSmem<kSmallMax, 512>)))) return e;
+    if (dev < 64) g_attrs_done[dev] = true;
+    return cudaSuccess;
+}
+
+// bump allocator over one scratch block
+struct Carve {
+    char *base;
+    size_t off;
+    template <typename T>
+    T *take(size_t count) {
+        off = (off + 255) & ~(size_t)255;
+        T *p = reinterpret_cast<T *>(base + off);
+        off += count * sizeof(T);
+        return p;
+    }
+};
+
+static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
+    caps.big = (uint32_t)(N / (kSmallMax + 1) + nreq + 1);
+    caps.small_tiny = (uint32_t)(N / 2 + nreq + 1);
+    caps.small_mid = (uint32_t)(N / (kTinyMax + 1) + nreq + 1);
+    caps.small_large = (uint32_t)(N / (kMidMax + 1) + nreq + 1);
+    caps.bound = (uint32_t)(N + 1);
+    caps.counts = (uint32_t)(N + (size_t)caps.big * 8 + 4096);
+    np = caps.counts / kScanChunk + 2;
+    Carve c{nullptr, 0};
+    c.take<uint32_t>(N); c.take<uint32_t>(N);
+    c.take<uint64_t>(N); c.take<uint64_t>(N);
+    c.take<uint16_t>(N);
+    c.take<uint32_t>(caps.counts);
+    c.take<uint32_t>(np);
+    c.take<uint64_t>((size_t)caps.big * kMaxV);
+    c.take<BigSeg>(caps.big); c.take<BigSeg>(caps.big);
+    c.take<SmallTask>(caps.small_tiny); c.take<SmallTask>(caps.small_mid); c.take<SmallTask>(caps.small_large);
+    c.take<Boundary>(caps.bound);
+    c.take<uint32_t>(C_NUM);
+    c.take<ReqDesc>(nreq);
+    return c.off + 256;
+}
+
+static int check(cudaError_t e, const char *what) { return e == cudaSuccess ? SS_OK : cuda_fail(e, what); }
+
+static int launch_scan(uint32_t *a, uint32_t n, uint32_t *partial, cudaStream_t st) {
+    if (n == 0) return SS_OK;
+    uint32_t nb = (n + kScanChunk - 1) / kScanChunk;
+    SS_LAUNCH_U("scan_reduce", st, n, k_scan_reduce<<<nb, kThreads, 0, st>>>(a, n, partial));
+    SS_LAUNCH_U("scan_partials", st, nb, k_scan_partials<<<1, 1024, 0, st>>>(partial, nb));
+    SS_LAUNCH_U("scan_down", st, n, k_scan_down<<<nb, kThreads, 0, st>>>(a, n, partial));
+    return check(cudaGetLastError(), "scan launch");
+}
+
+int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
+    if (ensure_attrs() != cudaSuccess) return cuda_fail(cudaGetLastError(), "kernel attributes");
+    std::vector<ReqDesc> reqs(reqs_in, reqs_in + nreq);
+    uint64_t N64 = 0;
+    for (auto &r : reqs) {
+        r.base = (uint32_t)N64;
+        N64 += r.n;
+    }
+    if (N64 > 0xFFFFFFFEull) {
+        set_error_detail("total number of strings %llu exceeds 2^32 - 2", (unsigned long long)N64);
+        return SS_ERR_TOO_LARGE;
+    }
+    const uint32_t N = (uint32_t)N64;
+    if (N == 0) {
+        for (auto &r : reqs)
+            if (r.status_out) {
+                int32_t ok = 0;
+                cudaError_t e = cudaMemcpyAsync(r.status_out, &ok, 4, cudaMemcpyHostToDevice, st);
+                if (e) return cuda_fail(e, "status write");
+            }
+        return check(cudaStreamSynchronize(st), "sync");
+    }
+    Caps caps;
+    size_t np;
+    size_t bytes = carve_size(N, nreq, caps, np);
+    void *block = nullptr;
+    cudaError_t e = scratch_alloc(&block, bytes, st);
+    if (e != cudaSuccess) {
+        set_error_detail("scratch allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        cudaGetLastError();
+        return SS_ERR_OOM;
+    }
+    Carve c{(char *)block, 0};
+    uint32_t *idx[2] = {c.take<uint32_t>(N), c.take<uint32_t>(N)};
+    uint64_t *key[2] = {c.take<uint64_t>(N), c.take<uint64_t>(N)};
+    uint16_t *obuf = c.take<uint16_t>(N);
+    uint32_t *counts = c.take<uint32_t>(caps.counts);
+    uint32_t *partial = c.take<uint32_t>(np);
+    uint64_t *splitters = c.take<uint64_t>((size_t)caps.big * kMaxV);
+    BigSeg *big[2] = {c.take<BigSeg>(caps.big), c.take<BigSeg>(caps.big)};
+    SmallTask *tiny = c.take<SmallTask>(caps.small_tiny);
+    SmallTask *mid = c.take<SmallTask>(caps.small_mid);
+    SmallTask *large = c.take<SmallTask>(caps.small_large);
+    Boundary *bounds = c.take<Boundary>(caps.bound);
+    uint32_t *counters = c.take<uint32_t>(C_NUM);
+    ReqDesc *dreqs = c.take<ReqDesc>(nreq);
+
+    int rc = SS_OK;
+    uint32_t *hc = (uint32_t *)host_staging(sizeof(uint32_t) * C_NUM + 64);
+    // initial segments: one per request
+    std::vector<BigSeg> big0;
+    std::vector<SmallTask> s_tiny, s_mid, s_large;
+    uint32_t tiles0 = 0, counts0 = 0, pairs0 = 0;
+    for (uint32_t r = 0; r < nreq; r++) {
+        const ReqDesc &q = reqs[r];
+        if (q.n < 2) continue;
+        if (q.n > kSmallMax) {
+            BigSeg s{};
+            s.begin = q.base; s.size = q.n; s.depth = 0; s.req = r;
+            big0.push_back(s);
+            uint32_t d = choose_d(q.n), t = tiles_of(q.n), B = buckets_of(d);
+            tiles0 += t; counts0 += B * t; pairs0 += B;
+        } else {
+            SmallTask t{q.base, q.n, 0, r, 0};
+            (q.n <= kTinyMax ? s_tiny : q.n <= kMidMax ? s_mid : s_large).push_back(t);
+        }
+    }
+    uint32_t hcnt[C_NUM] = {0};
+    uint32_t elems0 = 0;
+    for (auto &s : big0) elems0 += s.size;
+    hcnt[C_NTINY] = (uint32_t)s_tiny.size();
+    hcnt[C_NMID] = (uint32_t)s_mid.size();
+    hcnt[C_NLARGE] = (uint32_t)s_large.size();
+    for (auto &t : s_tiny) hcnt[C_E_TINY] += t.size;
+    for (auto &t : s_mid) hcnt[C_E_MID] += t.size;
+    for (auto &t : s_large) hcnt[C_E_LARGE] += t.size;
+#define TRY(x, what)                                     \
+    do {                                                 \
+        cudaError_t _e = (x);                            \
+        if (_e != cudaSuccess) { rc = cuda_fail(_e, what); goto done; } \
+    } while (0)
+    TRY(cudaMemcpyAsync(dreqs, reqs.data(), sizeof(ReqDesc) * nreq, cudaMemcpyHostToDevice, st), "copy requests");
+    TRY(cudaMemcpyAsync(counters, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, st), "copy counters");
+    if (!big0.empty()) TRY(cudaMemcpyAsync(big[0], big0.data(), sizeof(BigSeg) * big0.size(), cudaMemcpyHostToDevice, st), "copy big");
+    if (!s_tiny.empty()) TRY(cudaMemcpyAsync(tiny, s_tiny.data(), sizeof(SmallTask) * s_tiny.size(), cudaMemcpyHostToDevice, st), "copy tiny");
+    if (!s_mid.empty()) TRY(cudaMemcpyAsync(mid, s_mid.data(), sizeof(SmallTask) * s_mid.size(), cudaMemcpyHostToDevice, st), "copy mid");
+    if (!s_large.empty()) TRY(cudaMemcpyAsync(large, s_large.data(), sizeof(SmallTask) * s_large.size(), cudaMemcpyHostToDevice, st), "copy large");
+    {
+        uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
+        SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], key[0]));
+        TRY(cudaGetLastError(), "init launch");
+    }
+    {
+        uint32_t nbig = (uint32_t)big0.size(), ntiles = tiles0, ncounts = counts0, npairs = pairs0, nelems = elems0;
+        uint32_t cur = 0;
+        // the host-built first list must be synchronized before its vectors go away
+        TRY(cudaStreamSynchronize(st), "sync after setup");
+        while (nbig > 0) {
+            if (ncounts > caps.counts) {
+                set_error_detail("internal: counters %u exceed capacity %u", ncounts, caps.counts);
+                rc = SS_ERR_INTERNAL;
+                goto done;
+            }
+            uint32_t nxt = cur ^ 1;
+            SS_LAUNCH_U("setup_big", st, nbig, k_setup_big<<<1, 1024, 0, st>>>(big[cur], nbig));
+            SS_LAUNCH_U("build_trees", st, nbig, k_build_trees<<<nbig, kThreads, sizeof(TreeSmem), st>>>(big[cur], key[cur], splitters));
+            SS_LAUNCH_U("classify", st, nelems, k_classify<<<ntiles, kThreads, sizeof(ClassifySmem), st>>>(big[cur], nbig, key[cur], splitters, obuf, counts));
+            TRY(cudaGetLastError(), "classify launch");
+            if ((rc = launch_scan(counts, ncounts, partial, st)) != SS_OK) goto done;
+            SS_LAUNCH_U("scatter", st, nelems, k_scatter<MODE_SORT><<<ntiles, kThreads, sizeof(ScatterSmem), st>>>(
+                big[cur], nbig, dreqs, idx[cur], key[cur], obuf, counts, splitters, idx[nxt], key[nxt], counters));
+            TRY(cudaMemsetAsync(counters + C_NBIG, 0, sizeof(uint32_t), st), "reset");
+            TRY(cudaMemsetAsync(counters + C_TILES, 0, 3 * sizeof(uint32_t), st), "reset");
+            TRY(cudaMemsetAsync(counters + C_ELEMS, 0, sizeof(uint32_t), st), "reset");
+            SS_LAUNCH_U("buckets", st, npairs, k_buckets<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(
+                big[cur], nbig, npairs, counts, splitters, nxt, big[nxt], tiny, mid, large, bounds, caps, counters));
+            TRY(cudaGetLastError(), "level launch");
+            TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
+            TRY(cudaStreamSynchronize(st), "level sync");
+            if (hc[C_ERROR]) break;
+            nbig = hc[C_NBIG];
+            ntiles = hc[C_TILES];
+            ncounts = hc[C_COUNTS];
+            npairs = hc[C_PAIRS];
+            nelems = hc[C_ELEMS];
+            cur = nxt;
+        }
+        if (!hc[C_ERROR] || nbig == 0) {
+            TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
+            TRY(cudaStreamSynchronize(st), "sync");
+        }
+        if (hc[C_ERROR]) {
+            set_error_detail("device-side check failed: code %u info %u", hc[C_ERROR], hc[C_ERRINFO]);
+            rc = SS_ERR_INTERNAL;
+            goto done;
+        }
+        uint32_t ntiny = hc[C_NTINY], nmid = hc[C_NMID], nlarge = hc[C_NLARGE], nb = hc[C_NBOUND];
+        uint32_t sms = (uint32_t)sm_count();
+        if (ntiny) {
+            uint32_t grid = std::min<uint32_t>((ntiny + kWarps - 1) / kWarps, sms * 8);
+            SS_LAUNCH_U("small_warp", st, hc[C_E_TINY], k_small_warp<<<grid, kThreads, 0, st>>>(tiny, ntiny, dreqs, idx[0], key[0], idx[1], key[1]));
+        }
+        if (nmid) {
+            uint32_t grid = std::min<uint32_t>(nmid, sms * 8);
+            SS_LAUNCH_U("small_cta512", st, hc[C_E_MID], (k_small_cta<kMidMax, 256><<<grid, 256, sizeof(SmallCtaSmem<kMidMax, 256>), st>>>(mid, nmid, dreqs, idx[0], key[0], idx[1], key[1])));
+        }
+        if (nlarge) {
+            uint32_t grid = std::min<uint32_t>(nlarge, sms * 2);
+            SS_LAUNCH_U("small_cta4096", st, hc[C_E_LARGE], (k_small_cta<kSmallMax, 512><<<grid, 512, sizeof(SmallCtaSmem<kSmallMax, 512>), st>>>(large, nlarge, dreqs, idx[0], key[0], idx[1], key[1])));
+        }
+        TRY(cudaGetLastError(), "base case launch");
+        if (nb) {
+            uint32_t grid = std::min<uint32_t>((nb + 255) / 256, sms * 8);
+            SS_LAUNCH_U("boundary", st, nb, k_boundary<<<grid, 256, 0, st>>>(bounds, nb, dreqs));
+            TRY(cudaGetLastError(), "boundary launch");
+        }
+        SS_LAUNCH("status", st, k_status<<<(nreq + 255) / 256, 256, 0, st>>>(dreqs, nreq, 0));
+        TRY(cudaGetLastError(), "status launch");
+        TRY(cudaStreamSynchronize(st), "final sync");
+    }
+done:
+#undef TRY
+    scratch_free(block, st);
+    return rc;
+}
+
+// ------------------------------------------------ single-step entry points
+
+int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
+                    uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t st) {
+    if (ensure_attrs() != cudaSuccess) return cuda_fail(cudaGetLastError(), "kernel attributes");
+    uint32_t v = (1u << d) - 1, B = 2 * v + 1;
+    uint32_t tiles = tiles_of(n);
+    uint32_t ncounts = B * tiles;
+    uint32_t np = ncounts / kScanChunk + 2;
+    size_t bytes = 0;
+    Carve c0{nullptr, 0};
+    c0.take<uint32_t>(ncounts); c0.take<uint32_t>(np); c0.take<uint64_t>(kMaxV); c0.take<BigSeg>(1); c0.take<uint32_t>(C_NUM);
+    bytes = c0.off + 256;
+    void *block = nullptr;
+    cudaError_t e = scratch_alloc(&block, bytes, st);
+    if (e) { cudaGetLastError(); set_error_detail("scratch allocation failed"); return SS_ERR_OOM; }
+    Carve c{(char *)block, 0};
+    uint32_t *counts = c.take<uint32_t>(ncounts);
+    uint32_t *partial = c.take<uint32_t>(np);
+    uint64_t *spl = c.take<uint64_t>(kMaxV);
+    BigSeg *seg = c.take<BigSeg>(1);
+    uint32_t *counters = c.take<uint32_t>(C_NUM);
+    BigSeg s{};
+    s.begin = 0; s.size = n; s.depth = 0; s.req = 0; s.d = d; s.tiles = tiles;
+    s.tile_base = 0; s.cnt_base = 0; s.bkt_base = 0; s.scan_base = 0;
+    int rc = SS_OK;
+    do {
+        if ((e = cudaMemcpyAsync(seg, &s, sizeof(s), cudaMemcpyHostToDevice, st))) break;
+        if ((e = cudaMemcpyAsync(spl, x, sizeof(uint64_t) * v, cudaMemcpyDeviceToDevice, st))) break;
+        if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * C_NUM, st))) break;
+        if (n) {
+            SS_LAUNCH("classify", st, k_classify<<<tiles, kThreads, sizeof(ClassifySmem), st>>>(seg, 1, keys, spl, bucket_out, counts));
+            if ((e = cudaGetLastError())) break;
+            if ((rc = launch_scan(counts, ncounts, partial, st)) != SS_OK) break;
+            SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY><<<tiles, kThreads, sizeof(ScatterSmem), st>>>(
+                seg, 1, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, counters));
+            if ((e = cudaGetLastError())) break;
+            SS_LAUNCH("bucket_begin", st, k_bucket_begin<<<1, 256, 0, st>>>(seg, counts, bucket_begin_out));
+        } else {
+            if ((e = cudaMemsetAsync(bucket_begin_out, 0, sizeof(uint32_t) * (B + 1), st))) break;
+        }
+        if ((e = cudaGetLastError())) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    if (e && rc == SS_OK) rc = cuda_fail(e, "classify");
+    scratch_free(block, st);
+    return rc;
+}
+
+int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t st) {
+    if (ensure_attrs() != cudaSuccess) return cuda_fail(cudaGetLastError(), "kernel attributes");
+    SS_LAUNCH("pick_only", st, k_pick_only<<<1, kThreads, sizeof(TreeSmem), st>>>(sample, a, d, x_out));
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaStreamSynchronize(st);
+    return e ? cuda_fail(e, "splitters") : SS_OK;
+}
+
+int engine_gather(const ReqDesc &r, const uint32_t *depth, uint64_t *keys_out, cudaStream_t st) {
+    if (r.n == 0) return SS_OK;
+    uint32_t grid = std::min<uint32_t>((r.n + 255) / 256, (uint32_t)sm_count() * 8);
+    SS_LAUNCH("gather", st, k_gather<<<grid, 256, 0, st>>>(r, depth, keys_out));
+    cudaError_t e = cudaGetLastError();
+    if (!e) e = cudaStreamSynchronize(st);
+    return e ? cuda_fail(e, "gather") : SS_OK;
+}
+
+}  // namespace ss

@@ -1,0 +1,210 @@
+// Internal declarations of the GB300 string sample sorter.
+//
+// Layout in HBM during a sort (N = total strings of all requests):
+//   idx[2][N]  u32  string index (request-local) per global position, double buffered
+//   key[2][N]  u64  the 8 characters at the current depth of the element's segment
+//   obuf[N]    u16  bucket of each element in the current level (the "oracle" array
+//                   of Section 3.4; named bucket buffer here)
+//   counts[]   u32  per (segment, bucket, tile) counters, bucket-major per segment
+//   splitters  u64  in-order splitters of every big segment of the current level
+//   lists      big segments (per level), small tasks and boundary records
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/ss.h"
+
+namespace ss {
+
+// ---------------------------------------------------------------- tunables
+constexpr int kThreads = 256;                  // CTA size of the tile kernels
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 32;                     // elements per thread in a tile
+constexpr int kTile = kThreads * kItems;       // 8192 elements per tile
+constexpr int kWarpSpan = kTile / kWarps;      // 1024 contiguous elements per warp
+constexpr int kMaxD = 10;                      // tree depth: v = 2^d - 1 <= 1023
+constexpr int kMaxV = (1 << kMaxD) - 1;
+constexpr int kMaxB = 2 * kMaxV + 1;           // 2047 buckets
+constexpr uint32_t kSmallMax = 4096;           // segments up to this size are base cases
+constexpr uint32_t kTinyMax = 32;              // base cases handled by one warp
+constexpr uint32_t kMidMax = 512;              // base cases handled by a 512-capacity CTA
+
+// ------------------------------------------------------------ descriptors
+struct ReqDesc {
+    const uint8_t *chars;
+    const uint64_t *offsets;
+    const uint32_t *lengths;   // NULL: fixed_len or NUL-terminated
+    uint32_t fixed_len;
+    uint32_t n;
+    uint32_t base;             // global position of the request's first element
+    uint32_t pad;
+    uint32_t *perm_out;
+    uint32_t *lcp_out;
+    int32_t *status_out;
+};
+
+struct BigSeg {                 // a segment sorted by one multi-CTA S5 step
+    uint32_t begin, size, depth, req;
+    uint32_t d, tiles;
+    uint32_t tile_base, cnt_base, bkt_base, scan_base;
+    uint32_t pad0, pad1;
+};
+
+struct SmallTask {              // a base-case segment
+    uint32_t begin, size, depth, req, parity;
+};
+
+struct Boundary {               // lcp at global position pos is depth + lcp8(keys at depth)
+    uint32_t pos, depth, req;
+};
+
+// device counters (one block of u32 per sort)
+enum Counter : int {
+    C_NBIG = 0,       // big segments emitted for the next level
+    C_NTINY = 1,      // small tasks by class
+    C_NMID = 2,
+    C_NLARGE = 3,
+    C_NBOUND = 4,     // boundary records
+    C_ERROR = 5,      // first device-side error code (0 = none)
+    C_TILES = 6,      // tiles of the next level's big segments
+    C_COUNTS = 7,     // counters of the next level
+    C_PAIRS = 8,      // (segment, bucket) pairs of the next level
+    C_ERRINFO = 9,
+    C_ELEMS = 10,     // strings in the next level's big segments
+    C_E_TINY = 11,    // strings in small tasks by class
+    C_E_MID = 12,
+    C_E_LARGE = 13,
+    C_NUM = 16
+};
+
+enum DevError : uint32_t {
+    E_NONE = 0,
+    E_BIG_OVERFLOW = 1,
+    E_SMALL_OVERFLOW = 2,
+    E_BOUND_OVERFLOW = 3,
+    E_BAD_BUCKET = 4,
+    E_BAD_POS = 5,
+};
+
+struct Caps {                   // capacities of the scratch lists
+    uint32_t big, small_tiny, small_mid, small_large, bound, counts;
+};
+
+// ------------------------------------------------------------ device math
+__device__ __forceinline__ uint64_t bswap64(uint64_t x) {
+    uint32_t lo = (uint32_t)x, hi = (uint32_t)(x >> 32);
+    uint32_t rlo = __byte_perm(lo, 0, 0x0123), rhi = __byte_perm(hi, 0, 0x0123);
+    return ((uint64_t)rlo << 32) | rhi;
+}
+
+// per-byte zero flags (0x80 in each byte that is zero), exact (no carries)
+__device__ __forceinline__ uint64_t zero_bytes(uint64_t x) {
+    const uint64_t m = 0x7F7F7F7F7F7F7F7FULL;
+    uint64_t t = (x & m) + m;
+    return ~(t | x | m);
+}
+
+// number of leading non-zero bytes of a big-endian key (8 if none is zero)
+__device__ __forceinline__ uint32_t nulpos(uint64_t key) {
+    uint64_t z = zero_bytes(key);
+    return z ? (uint32_t)(__clzll(z) >> 3) : 8u;
+}
+
+__device__ __forceinline__ bool has_zero(uint64_t key) { return zero_bytes(key) != 0; }
+
+// common leading bytes of two keys (8 when equal)
+__device__ __forceinline__ uint32_t lcp8(uint64_t a, uint64_t b) {
+    uint64_t x = a ^ b;
+    return x ? (uint32_t)(__clzll(x) >> 3) : 8u;
+}
+
+// chars_h: 8 bytes of string i at depth h, big-endian, zero past the end.
+// Reads the aligned word holding byte h, and the next aligned word only when
+// the string continues into it.
+__device__ __forceinline__ uint64_t load_key(const ReqDesc &R, uint32_t i, uint32_t h) {
+    uint64_t off = __ldg(R.offsets + i);
+    uint64_t rem = ~0ULL;   // bytes of the string left from depth h (terminated: unknown)
+    if (R.lengths) {
+        uint32_t len = __ldg(R.lengths + i);
+        if (h >= len) return 0;
+        rem = len - h;
+    } else if (R.fixed_len) {
+        if (h >= R.fixed_len) return 0;
+        rem = R.fixed_len - h;
+    }
+    const uint8_t *p = R.chars + off + h;
+    uintptr_t a = (uintptr_t)p;
+    const uint64_t *w = (const uint64_t *)(a & ~(uintptr_t)7);
+    uint32_t sh = (uint32_t)(a & 7) * 8;
+    uint64_t w0 = __ldg(w);
+    uint64_t v = w0 >> sh;   // memory bytes p[0 .. 8 - (a&7)) in the low bytes
+    if (sh) {
+        bool need;
+        if (rem == ~0ULL) {
+            // terminated: continue only if no 0 byte among the valid bytes
+            uint64_t valid = v | (~0ULL << (64 - sh));
+            need = !has_zero(valid);
+        } else {
+            need = rem > (uint64_t)(8 - (a & 7));
+        }
+        if (need) v |= __ldg(w + 1) << (64 - sh);
+    }
+    uint64_t key = bswap64(v);
+    if (rem < 8) key &= ~0ULL << (8 * (8 - rem));
+    uint64_t z = zero_bytes(key);
+    if (z) {
+        uint32_t k = (uint32_t)(__clzll(z) >> 3);   // first zero byte
+        key &= k ? (~0ULL << (64 - 8 * k)) : 0ULL;
+    }
+    return key;
+}
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finaliser
+    z += 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ void set_error(uint32_t *counters, uint32_t code, uint32_t info) {
+    if (atomicCAS(counters + C_ERROR, 0u, code) == 0u) counters[C_ERRINFO] = info;
+}
+
+// ------------------------------------------------------- host-side helpers
+void set_error_detail(const char *fmt, ...);
+int cuda_fail(cudaError_t e, const char *what);
+
+// launch bookkeeping (profiling): begin/end around each library kernel launch
+void prof_begin(const char *name, cudaStream_t s);
+void prof_end(const char *name, cudaStream_t s, uint64_t units);
+
+// scratch memory from the library's stream-ordered pool
+cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+cudaError_t scratch_free(void *p, cudaStream_t s);
+
+// pinned host staging buffer of the calling thread (at least `bytes`)
+void *host_staging(size_t bytes);
+
+// engine entry points (ss_engine.cu)
+int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream);
+int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
+                    uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t stream);
+int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t stream);
+int engine_gather(const ReqDesc &r, const uint32_t *depth, uint64_t *keys_out, cudaStream_t stream);
+
+// merge (ss_merge.cu)
+int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
+               const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t stream);
+
+}  // namespace ss
+
+// launch with optional per-kernel timing; `units` = strings (or records)
+// the launch processes, used to turn time into algorithmic bandwidth
+#define SS_LAUNCH_U(name, stream, units, ...)    \
+    do {                                         \
+        ::ss::prof_begin(name, stream);          \
+        __VA_ARGS__;                             \
+        ::ss::prof_end(name, stream, (units));   \
+    } while (0)
+#define SS_LAUNCH(name, stream, ...) SS_LAUNCH_U(name, stream, 0, __VA_ARGS__)

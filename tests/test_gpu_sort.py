@@ -1,0 +1,250 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle,
+element by element (integer outputs: bit-exact)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from gpu_util import gpu_sort, to_device
+
+pytestmark = pytest.mark.gpu
+
+
+def _check(ss):
+    perm, lcp = gpu_sort(ss)
+    want_perm, want_lcp = oracle.sort(ss)
+    if not np.array_equal(perm, want_perm):
+        bad = np.flatnonzero(perm != want_perm)
+        raise AssertionError(f"{ss.name}: perm differs at {bad[:10]} (of {bad.size}); got {perm[bad[:5]]} want {want_perm[bad[:5]]}")
+    if not np.array_equal(lcp, want_lcp):
+        bad = np.flatnonzero(lcp != want_lcp)
+        raise AssertionError(f"{ss.name}: lcp differs at {bad[:10]} (of {bad.size}); got {lcp[bad[:5]]} want {want_lcp[bad[:5]]}")
+    return perm, lcp
+
+
+# ------------------------------------------------------------- workloads
+
+def test_plain_random_lower_200k():
+    """Plain single sort: n = 200,000, length U[8,32] over 'a'..'z', seed 1."""
+    _check(W.random_lower(200_000, seed=1))
+
+
+def test_url_like_small():
+    _check(W.url_like(300_000, seed=2))
+
+
+def test_dna_windows_small():
+    _check(W.dna_windows(n=300_000, text_len=6_000_000, window=100, seed=3))
+
+
+def test_no_lcp_small():
+    _check(W.no_lcp(n=300_000, seed=5))
+
+
+def test_paper_random_with_empty_strings():
+    _check(W.paper_random(200_000, seed=11))
+
+
+def test_sinha_dna_like_duplicates():
+    _check(W.sinha_dna_like(400_000, seed=12))
+
+
+# ------------------------------------------------------------- edge cases
+
+def test_empty_and_single():
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = W.from_bytes_list([b"abc"])
+    perm, lcp = gpu_sort(ss)
+    assert perm.tolist() == [0] and lcp.tolist() == [0]
+    chars, offsets, _ = to_device(W.from_bytes_list([b"x"]))
+    out = torch.zeros(1, dtype=torch.int32, device="cuda:0")
+    P.ss_sort(chars, offsets, 0, out, out)   # n = 0: no-op
+
+
+@pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 511, 512, 513, 4095, 4096, 4097, 8191, 8192, 8193, 20000])
+def test_threshold_sizes(n):
+    _check(W.random_lower(n, seed=n, min_len=0, max_len=12))
+
+
+def test_all_equal_long_strings():
+    """One big equality bucket recursing 8 characters per level."""
+    s = b"q" * 200
+    _check(W.from_bytes_list([s] * 10000 + [s[:-1] + b"r"] * 3 + [s[:150]] * 5))
+
+
+def test_many_duplicates_tiny_alphabet():
+    rng = np.random.default_rng(1)
+    strs = [bytes(rng.integers(1, 3, int(rng.integers(0, 6))).astype(np.uint8)) for _ in range(50000)]
+    _check(W.from_bytes_list(strs))
+
+
+def test_long_common_prefix_last_char_differs():
+    rng = np.random.default_rng(2)
+    pre = b"p" * 997
+    strs = [pre + bytes([int(c)]) + b"z" * int(rng.integers(0, 9)) for c in rng.integers(1, 256, 30000)]
+    _check(W.from_bytes_list(strs))
+
+
+def test_high_bytes_and_unaligned_offsets():
+    rng = np.random.default_rng(3)
+    strs = [bytes(rng.integers(1, 256, int(rng.integers(0, 40))).astype(np.uint8)) for _ in range(70000)]
+    _check(W.from_bytes_list(strs))
+
+
+def test_explicit_lengths():
+    rng = np.random.default_rng(4)
+    strs = [bytes(rng.integers(1, 5, int(rng.integers(0, 30))).astype(np.uint8)) for _ in range(60000)]
+    _check(W.from_bytes_list(strs, terminated=False))
+
+
+def test_fixed_windows_short_text_many_duplicates():
+    _check(W.dna_windows(n=100_000, text_len=20_000, window=100, seed=8))
+
+
+# ---------------------------------------------------------- other entry points
+
+def test_batch_equals_single():
+    import torch
+    import paper_1403_2056_gb300 as P
+    sets = [W.random_lower(5000, seed=1), W.url_like(20000, seed=2), W.dna_windows(30000, 100000, 100, seed=3),
+            W.from_bytes_list([b"a"]), W.from_bytes_list([]), W.random_lower(33, seed=4),
+            W.url_like(100000, seed=6), W.sinha_dna_like(3000, seed=7)]
+    reqs, keep = [], []
+    for ss in sets:
+        chars, offsets, lengths = to_device(ss)
+        n = ss.n
+        perm = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((max(n, 1),), -1, dtype=torch.int32, device="cuda:0")
+        st = torch.full((1,), 99, dtype=torch.int32, device="cuda:0")
+        reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=n,
+                         perm_out=perm, lcp_out=lcp, status_out=st))
+        keep.append((ss, perm, lcp, st))
+    P.ss_sort_batch(reqs)
+    torch.cuda.synchronize()
+    for ss, perm, lcp, st in keep:
+        want_perm, want_lcp = oracle.sort(ss)
+        assert int(st.item()) == 0
+        assert np.array_equal(perm[:ss.n].cpu().numpy().view(np.uint32), want_perm), ss.name
+        assert np.array_equal(lcp[:ss.n].cpu().numpy().view(np.uint32), want_lcp), ss.name
+
+
+@pytest.mark.parametrize("runs", [1, 2, 4, 5])
+def test_sort_host_buffers(runs):
+    import paper_1403_2056_gb300 as P
+    ss = W.url_like(100_000, seed=9)
+    perm = np.empty(ss.n, np.uint32)
+    lcp = np.empty(ss.n, np.uint32)
+    P.ss_sort_host(ss.chars, ss.offsets, None, 0, perm, lcp, runs=runs)
+    want_perm, want_lcp = oracle.sort(ss)
+    assert np.array_equal(perm, want_perm)
+    assert np.array_equal(lcp, want_lcp)
+
+
+def test_gather_keys():
+    import torch
+    import paper_1403_2056_gb300 as P
+    rng = np.random.default_rng(5)
+    strs = [bytes(rng.integers(1, 256, int(rng.integers(0, 30))).astype(np.uint8)) for _ in range(5000)]
+    for ss in (W.from_bytes_list(strs), W.from_bytes_list(strs, terminated=False),
+               W.dna_windows(5000, 50000, 100, seed=1)):
+        lens = ss.all_lengths()
+        depth = (rng.random(ss.n) * (lens.astype(np.float64) + 1)).astype(np.uint32)
+        depth = np.minimum(depth, lens.astype(np.uint32))
+        chars, offsets, lengths = to_device(ss)
+        d = torch.from_numpy(depth.view(np.int32)).cuda()
+        keys = torch.zeros(ss.n, dtype=torch.int64, device="cuda:0")
+        P.ss_gather_keys(chars, offsets, lengths, ss.fixed_len, ss.n, d, keys)
+        got = keys.cpu().numpy().view(np.uint64)
+        want = oracle.chars_h_all(ss, depth.astype(np.uint64))
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("d", [1, 2, 5, 10])
+def test_splitters_match_oracle_pick(d):
+    import torch
+    import paper_1403_2056_gb300 as P
+    rng = np.random.default_rng(d)
+    v = (1 << d) - 1
+    a = 2 * v + 1
+    for hi in (5, 50, 10**12):
+        sample = rng.integers(0, hi, a).astype(np.uint64)
+        s = torch.from_numpy(sample.view(np.int64)).cuda()
+        x = torch.zeros(v, dtype=torch.int64, device="cuda:0")
+        P.ss_splitters(s, a, d, x)
+        got = x.cpu().numpy().view(np.uint64)
+        want = oracle.s5_pick(np.sort(sample), v)
+        assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("d,n", [(1, 1000), (3, 9000), (7, 50000), (10, 300000), (10, 0)])
+def test_classify_step_matches_oracle(d, n):
+    import torch
+    import paper_1403_2056_gb300 as P
+    rng = np.random.default_rng(d + n)
+    v = (1 << d) - 1
+    x = np.sort(rng.integers(0, 8 * v + 16, v).astype(np.uint64))
+    keys = rng.integers(0, 8 * v + 20, n).astype(np.uint64)
+    tk = torch.from_numpy(keys.view(np.int64)).cuda() if n else torch.zeros(1, dtype=torch.int64, device="cuda:0")
+    tx = torch.from_numpy(x.view(np.int64)).cuda()
+    b = torch.zeros(max(n, 1), dtype=torch.int16, device="cuda:0")
+    bb = torch.zeros(2 * v + 2, dtype=torch.int32, device="cuda:0")
+    order = torch.zeros(max(n, 1), dtype=torch.int32, device="cuda:0")
+    P.ss_classify(tk, n, tx, d, b, bb, order)
+    want_b = oracle.s5_classify(keys, x)
+    want_bb, want_order = oracle.s5_distribute(want_b, v)
+    assert np.array_equal(b[:n].cpu().numpy().view(np.uint16), want_b)
+    assert np.array_equal(bb.cpu().numpy().view(np.uint32).astype(np.uint64), want_bb)
+    assert np.array_equal(order[:n].cpu().numpy().view(np.uint32).astype(np.uint64), want_order)
+
+
+@pytest.mark.parametrize("K", [1, 2, 3, 4, 7, 16])
+def test_merge_runs(K):
+    import torch
+    import paper_1403_2056_gb300 as P
+    rng = np.random.default_rng(K)
+    for ss in (W.url_like(120_000, seed=K), W.sinha_dna_like(50_000, seed=K)):
+        cuts = np.sort(rng.integers(0, ss.n + 1, K - 1))
+        rb = np.concatenate([[0], cuts, [ss.n]]).astype(np.uint32)
+        run_perm = np.empty(ss.n, np.uint32)
+        run_lcp = np.empty(ss.n, np.uint32)
+        for k in range(K):
+            b, e = int(rb[k]), int(rb[k + 1])
+            sub = W.subset(ss, np.arange(b, e))
+            p, l = oracle.sort(sub)
+            run_perm[b:e] = p + b
+            run_lcp[b:e] = l
+        chars, offsets, lengths = to_device(ss)
+        rp = torch.from_numpy(run_perm.view(np.int32)).cuda()
+        rl = torch.from_numpy(run_lcp.view(np.int32)).cuda()
+        perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        P.ss_merge(chars, offsets, lengths, ss.fixed_len, rp, rl, rb, perm, lcp)
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
+        assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
+
+
+@pytest.mark.parametrize("K", [2, 4])
+def test_batch_runs_then_merge_with_bases(K):
+    """The benchmark step: K index-contiguous runs sorted by one ss_sort_batch
+    (request-local indices), then ss_merge with each run's index base."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    for ss in (W.url_like(200_000, seed=13), W.dna_windows(150_000, 400_000, 100, seed=14)):
+        chars, offsets, lengths = to_device(ss)
+        rb = np.array([ss.n * k // K for k in range(K + 1)], np.uint32)
+        rperm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        rlcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        reqs = []
+        for k in range(K):
+            b, e = int(rb[k]), int(rb[k + 1])
+            reqs.append(dict(chars=chars, offsets=offsets[b:e], lengths=None if lengths is None else lengths[b:e],
+                             fixed_len=ss.fixed_len, n=e - b, perm_out=rperm[b:e], lcp_out=rlcp[b:e]))
+        P.ss_sort_batch(reqs)
+        perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        P.ss_merge(chars, offsets, lengths, ss.fixed_len, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1])
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
+        assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
