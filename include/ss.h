@@ -151,6 +151,31 @@ int ss_merge(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32
              uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
 
 /*
+ * ss_merge_noalloc -- ss_merge that allocates nothing, for callers that
+ * cannot let a library allocate: a process whose device memory is reserved
+ * up front by its own arena, code held to a hard memory budget, or a
+ * latency-critical path that must not pay for cudaMalloc/cudaFree or pinned
+ * host allocations.  The paper has no counterpart; this is a deployment
+ * variant of the merge above, with the same arguments, order and results.
+ *   Limits: at most 1,048,576 strings in total and at most 64 runs; larger
+ *   requests return SS_ERR_TOO_LARGE with a message (use ss_merge).
+ *   Memory: its temporary arrays live in a fixed device array of about
+ *   8 MiB inside the library image, held by every GPU that loads the
+ *   library until the process exits.  Every call on a device shares that
+ *   array: calls that overlap on the GPU (unordered streams or threads)
+ *   race and give wrong results, so order them on one stream.
+ *   Set-up: the first call on each device looks up the array's device
+ *   address (with that device current); make that first call before any
+ *   stream capture.
+ *   Completion: the call only queues work on `stream` and returns; results
+ *   are complete when the stream reaches that point.
+ */
+int ss_merge_noalloc(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32_t *lengths_dev,
+                     uint32_t fixed_len, const uint32_t *run_perm_dev, const uint32_t *run_lcp_dev,
+                     const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
+                     uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
+
+/*
  * ss_gather_keys -- chars_h (Section 3.4): for each string i, the 8 bytes at
  * depth depth_dev[i] as a big-endian uint64 (first character in the most
  * significant byte), bytes past the end of the string zero.

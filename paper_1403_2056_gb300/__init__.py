@@ -21,7 +21,7 @@ from . import build as _build
 __all__ = [
     "SortError", "lib", "library_path",
     "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge",
-    "ss_gather_keys", "ss_splitters", "ss_classify",
+    "ss_merge_noalloc", "ss_gather_keys", "ss_splitters", "ss_classify",
     "profile_enable", "profile_reset", "profile_read", "launch_count",
     "STATUS",
 ]
@@ -60,6 +60,7 @@ def lib():
     L.ss_sort_host.argtypes = [vp, u64, vp, vp, u32, u32, u32, vp, vp, vp]
     L.ss_sort_batch.argtypes = [vp, u32, vp]
     L.ss_merge.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, u32, vp, vp, vp]
+    L.ss_merge_noalloc.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, u32, vp, vp, vp]
     L.ss_gather_keys.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp]
     L.ss_splitters.argtypes = [vp, u32, u32, vp, vp]
     L.ss_classify.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp]
@@ -68,7 +69,7 @@ def lib():
     L.ss_launch_count.restype = u64
     L.ss_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
     L.ss_version.restype = i32
-    for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_gather_keys",
+    for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read"):
         getattr(L, name).restype = i32
     _lib = L
@@ -178,6 +179,20 @@ def ss_merge(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, p
                           int(fixed_len), _dev(run_perm, "int32", "run_perm"), _dev(run_lcp, "int32", "run_lcp"),
                           rb.ctypes.data, None if base is None else base.ctypes.data, K,
                           _dev(perm_out, "int32", "perm_out"), _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+
+
+def ss_merge_noalloc(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+                     run_base=None, stream=None):
+    """ss_merge without allocation (fixed 8 MiB device array; <= 1,048,576 strings, <= 64 runs).
+    Only queues work on the stream: synchronize before reading the outputs."""
+    rb = np.ascontiguousarray(np.asarray(run_begin, dtype=np.uint32))
+    K = rb.shape[0] - 1
+    base = None if run_base is None else np.ascontiguousarray(np.asarray(run_base, dtype=np.uint32))
+    _check(lib().ss_merge_noalloc(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
+                                  int(fixed_len), _dev(run_perm, "int32", "run_perm"), _dev(run_lcp, "int32", "run_lcp"),
+                                  rb.ctypes.data, None if base is None else base.ctypes.data, K,
+                                  _dev(perm_out, "int32", "perm_out"), _dev(lcp_out, "int32", "lcp_out"),
+                                  _stream(stream)))
 
 
 def ss_gather_keys(chars, offsets, lengths, fixed_len, n, depth, keys_out, stream=None):

@@ -15,6 +15,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string.h>
 #include <vector>
 
@@ -217,3 +218,159 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
 }
 
 }  // namespace ss
+
+// ---------------------------------------------------------------------------
+// ss_merge_noalloc: the same merge without any allocation.
+//
+// Some callers cannot let a library allocate: a serving process whose device
+// memory is reserved up front by its own arena, code with a hard device-memory
+// budget, or a latency-critical path that must not pay for (or synchronize
+// on) cudaMalloc/cudaFree or pinned host allocations.  This entry point keeps
+// its temporary arrays in one fixed array of device memory that is part of
+// the library image: every GPU that loads the library holds these
+// kNoAllocBytes until the process exits.  The run table of each round is
+// passed to the device by value and stored in the same array by a one-thread
+// kernel, so no host staging buffer is needed either.
+//
+// The array is shared by every call on a device and keeps whatever the last
+// call left in it; nothing here relies on its contents at entry (every word
+// is written before it is read within a call).  Calls that overlap on the GPU
+// (different streams, or different host threads, without ordering between
+// them) race on the array and give wrong results: order them on one stream.
+namespace ss {
+
+constexpr uint32_t kNoAllocMaxStrings = 1u << 20;   // 1,048,576 strings in total
+constexpr uint32_t kNoAllocMaxRuns = 64;
+constexpr uint32_t kNoAllocTableWords = 2 * (kNoAllocMaxRuns + 1);
+constexpr size_t kNoAllocWords = 2ull * kNoAllocMaxStrings + kNoAllocTableWords;
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[kNoAllocWords];
+
+struct RunTable {
+    uint32_t rb[kNoAllocMaxRuns + 1];
+    uint32_t base[kNoAllocMaxRuns];
+};
+
+// writes one round's run starts and index bases into the fixed array
+__global__ void k_store_run_table(RunTable t, uint32_t R, uint32_t *dst) {
+    for (uint32_t k = threadIdx.x; k <= R; k += blockDim.x) dst[k] = t.rb[k];
+    for (uint32_t k = threadIdx.x; k < R; k += blockDim.x) dst[kNoAllocMaxRuns + 1 + k] = t.base[k];
+}
+
+// device address of g_noalloc_scratch, looked up once per device with that
+// device current (in host code the symbol name is only a host-side stand-in)
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[128];
+
+static cudaError_t noalloc_setup(uint32_t **out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = (uint32_t *)g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+static int merge_runs_noalloc(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp,
+                              const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
+                              uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t st) {
+    uint32_t total = run_begin_host[K];
+    uint32_t *scratch = nullptr;
+    cudaError_t e = noalloc_setup(&scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "ss_merge_noalloc: symbol address of the fixed scratch array");
+    uint32_t *tmp_perm = scratch;
+    uint32_t *tmp_lcp = scratch + kNoAllocMaxStrings;
+    uint32_t *d_table = scratch + 2ull * kNoAllocMaxStrings;
+    RunTable t;
+    memset(&t, 0, sizeof(t));
+    uint32_t R = 0;
+    t.rb[0] = 0;
+    for (uint32_t k = 0; k < K; k++)
+        if (run_begin_host[k + 1] > run_begin_host[k]) {
+            t.base[R] = run_base_host ? run_base_host[k] : 0u;
+            t.rb[++R] = run_begin_host[k + 1];
+        }
+    if (R <= 1) {
+        uint32_t base = R ? t.base[0] : 0u;
+        uint32_t grid = (total + 255) / 256;
+        if (grid > 4096) grid = 4096;
+        SS_LAUNCH_U("copy_run", st, total, k_copy_run<<<grid, 256, 0, st>>>(run_perm, run_lcp, base, total, perm_out, lcp_out));
+        e = cudaGetLastError();
+        return e ? cuda_fail(e, "ss_merge_noalloc") : SS_OK;
+    }
+    size_t rounds = 0;
+    for (uint32_t r = R; r > 1; r = (r + 1) / 2) rounds++;
+    const uint32_t *src_p = run_perm, *src_l = run_lcp;
+    size_t round = 0;
+    while (R > 1) {
+        round++;
+        bool last = round == rounds;
+        uint32_t *dst_p = last ? perm_out : ((rounds - round) % 2 ? tmp_perm : perm_out);
+        uint32_t *dst_l = last ? lcp_out : ((rounds - round) % 2 ? tmp_lcp : lcp_out);
+        if (round > 1) memset(t.base, 0, sizeof(t.base));   // later rounds hold set indices
+        SS_LAUNCH("store_run_table", st, k_store_run_table<<<1, 128, 0, st>>>(t, R, d_table));
+        uint32_t threads = (total + kMergeItems - 1) / kMergeItems;
+        SS_LAUNCH_U("merge_round", st, total, k_merge_round<<<(threads + 255) / 256, 256, 0, st>>>(
+            set, src_p, src_l, d_table, R, d_table + kNoAllocMaxRuns + 1, total, dst_p, dst_l));
+        if ((e = cudaGetLastError())) return cuda_fail(e, "ss_merge_noalloc");
+        RunTable nt;
+        memset(&nt, 0, sizeof(nt));
+        uint32_t nR = 0;
+        for (uint32_t k = 2; k <= R; k += 2) nt.rb[++nR] = t.rb[k];
+        if (R % 2) nt.rb[++nR] = t.rb[R];
+        t = nt;
+        R = nR;
+        src_p = dst_p;
+        src_l = dst_l;
+    }
+    return SS_OK;
+}
+
+}  // namespace ss
+
+extern "C" int ss_merge_noalloc(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths,
+                                uint32_t fixed_len, const uint32_t *run_perm, const uint32_t *run_lcp,
+                                const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
+                                uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
+    using namespace ss;
+    set_error_detail("%s", "");
+    if (K == 0 || !run_begin_host || run_begin_host[0] != 0) {
+        set_error_detail("ss_merge_noalloc: K must be >= 1 with run_begin_host[K+1], run_begin_host[0] = 0");
+        return SS_ERR_INVALID;
+    }
+    if (K > kNoAllocMaxRuns) {
+        set_error_detail("ss_merge_noalloc: K = %u runs is beyond the fixed limit of %u runs", K, kNoAllocMaxRuns);
+        return SS_ERR_TOO_LARGE;
+    }
+    for (uint32_t k = 0; k < K; k++)
+        if (run_begin_host[k + 1] < run_begin_host[k]) {
+            set_error_detail("ss_merge_noalloc: run_begin_host must be non-decreasing");
+            return SS_ERR_INVALID;
+        }
+    uint32_t total = run_begin_host[K];
+    if (total > kNoAllocMaxStrings) {
+        set_error_detail("ss_merge_noalloc: %u strings is beyond the fixed scratch limit of %u strings "
+                         "(use ss_merge for larger merges)", total, kNoAllocMaxStrings);
+        return SS_ERR_TOO_LARGE;
+    }
+    if (total == 0) return SS_OK;
+    if (!chars || !offsets || !run_perm || !run_lcp || !perm_out || !lcp_out) {
+        set_error_detail("ss_merge_noalloc: NULL pointer");
+        return SS_ERR_INVALID;
+    }
+    ReqDesc set;
+    memset(&set, 0, sizeof(set));
+    set.chars = chars;
+    set.offsets = offsets;
+    set.lengths = lengths;
+    set.fixed_len = lengths ? 0 : fixed_len;
+    return merge_runs_noalloc(set, run_perm, run_lcp, run_begin_host, run_base_host, K, perm_out, lcp_out,
+                              reinterpret_cast<cudaStream_t>(stream));
+}
