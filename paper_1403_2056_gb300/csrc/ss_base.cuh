@@ -1,0 +1,363 @@
+// Base case of the recursion: segments of at most kSmallMax strings that
+// share their first `depth` characters are sorted completely inside one CTA
+// (or one warp), and their LCPs are written (the role LCP insertion sort,
+// Algorithm 5, plays in the paper's pS5).
+//
+// A segment is sorted by its 8-character keys once, with a CTA merge sort
+// (ITEMS keys per thread sorted in registers, then merge-path passes through
+// shared memory).  Neighbours with different keys are split (LCP = depth +
+// lcp of the keys); neighbours with equal keys that hold the end of the
+// string are equal strings (LCP = their length); runs of equal keys without
+// the end form groups that continue 8 characters deeper.  Groups of at most
+// 32 strings are finished by one warp in registers; larger groups are
+// re-sorted by the CTA, compacted, by (group, next key, position).  Equal
+// strings keep their input order (input order inside a segment is index
+// order).  An LCP belongs to a position: once two neighbouring positions are
+// split, every later re-sort stays on one side of that boundary.
+#pragma once
+
+#include "ss_internal.cuh"
+
+namespace ss {
+
+// ----------------------------------------------------------- warp finish
+struct WElem {
+    uint32_t g;   // group id: first lane of its group (0xFFFFFFFF: padding)
+    uint32_t i;   // string index
+    uint64_t k;   // key at the current depth
+};
+
+__device__ __forceinline__ bool welem_less(const WElem &a, const WElem &b) {
+    if (a.g != b.g) return a.g < b.g;
+    if (a.k != b.k) return a.k < b.k;
+    return a.i < b.i;   // inside a segment input order equals index order
+}
+
+__device__ __forceinline__ WElem shfl_xor_welem(const WElem &e, int m) {
+    WElem r;
+    r.g = __shfl_xor_sync(0xffffffffu, e.g, m);
+    r.i = __shfl_xor_sync(0xffffffffu, e.i, m);
+    r.k = __shfl_xor_sync(0xffffffffu, e.k, m);
+    return r;
+}
+
+// Sort one group of m <= 32 strings completely with one warp (all 32 lanes
+// call this).  Lane l < m holds string index `id` and its key at `depth`.
+// Writes perm and lcp of R-local positions out .. out + m - 1 (not the lcp of
+// position `out`, which the caller owns).
+__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t key,
+                                            uint32_t out) {
+    const uint32_t lane = threadIdx.x & 31;
+    WElem e;
+    if (lane < m) { e.g = 0; e.i = id; e.k = key; }
+    else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k = ~0ull; }
+    uint32_t lcp = 0;
+    for (;;) {
+        for (int k = 2; k <= 32; k <<= 1) {
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                WElem o = shfl_xor_welem(e, j);
+                bool up = (lane & k) == 0;
+                bool lower = (lane & j) == 0;
+                bool take_o = lower == up ? welem_less(o, e) : welem_less(e, o);
+                if (take_o) e = o;
+            }
+        }
+        uint32_t pg = __shfl_up_sync(0xffffffffu, e.g, 1);
+        uint64_t pk = __shfl_up_sync(0xffffffffu, e.k, 1);
+        bool start = true;
+        if (lane > 0 && lane < m && pg == e.g) {
+            if (pk != e.k) lcp = depth + lcp8(pk, e.k);
+            else if (has_zero(e.k)) lcp = depth + nulpos(e.k);
+            else start = false;
+        }
+        if (lane >= m) start = true;
+        uint32_t sg = start ? lane : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, sg, o);
+            if (lane >= (uint32_t)o) sg = max(sg, y);
+        }
+        bool next_start = __shfl_down_sync(0xffffffffu, start, 1) || lane == 31;
+        bool active = lane < m && !(start && next_start);
+        if (lane < m) e.g = sg;
+        if (!__any_sync(0xffffffffu, active)) break;
+        depth += 8;
+        if (active) e.k = load_key(R, e.i, depth);
+    }
+    if (lane < m) {
+        R.perm_out[out + lane] = e.i;
+        if (lane > 0) R.lcp_out[out + lane] = lcp;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
+                                                         const uint32_t *idx0, const uint64_t *key0,
+                                                         const uint32_t *idx1, const uint64_t *key1) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    for (uint32_t tk = gw; tk < ntask; tk += nw) {
+        SmallTask t = tasks[tk];
+        const uint32_t *idx = t.parity ? idx1 : idx0;
+        const uint64_t *key = t.parity ? key1 : key0;
+        const ReqDesc &R = reqs[t.req];
+        uint32_t id = 0;
+        uint64_t k = 0;
+        if (lane < t.size) { id = idx[t.begin + lane]; k = key[t.begin + lane]; }
+        warp_finish(R, t.size, t.depth, id, k, t.begin - R.base);
+    }
+}
+
+// -------------------------------------------------------- CTA merge sort
+// element: 64-bit key k and g = group << 12 | original index (both < 4096);
+// order (group, key, original index); padding g = 0xFFFFFFFF sorts last
+
+__device__ __forceinline__ bool gk_less(uint64_t ka, uint32_t ga, uint64_t kb, uint32_t gb) {
+    uint32_t xa = ga >> 12, xb = gb >> 12;
+    if (xa != xb) return xa < xb;
+    if (ka != kb) return ka < kb;
+    return (ga & 0xFFFu) < (gb & 0xFFFu);
+}
+
+template <int ITEMS>
+__device__ __forceinline__ void reg_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITEMS]) {
+    // odd-even transposition network, fully unrolled
+#pragma unroll
+    for (int r = 0; r < ITEMS; r++) {
+#pragma unroll
+        for (int j = r & 1; j + 1 < ITEMS; j += 2) {
+            if (gk_less(k[j + 1], g[j + 1], k[j], g[j])) {
+                uint64_t tk = k[j]; k[j] = k[j + 1]; k[j + 1] = tk;
+                uint32_t tg = g[j]; g[j] = g[j + 1]; g[j + 1] = tg;
+            }
+        }
+    }
+}
+
+// Sort the P (power of two, >= ITEMS) slots held blocked in registers
+// (thread t holds slots t*ITEMS ..) through the shared buffers MK / MG.
+// On return each thread holds its ITEMS slots of the sorted sequence.
+template <int NT, int ITEMS>
+__device__ __forceinline__ void block_merge_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITEMS], uint32_t P, uint64_t *MK,
+                                                 uint32_t *MG) {
+    reg_sort<ITEMS>(k, g);
+    const uint32_t o = threadIdx.x * ITEMS;
+    for (uint32_t L = ITEMS; L < P; L <<= 1) {
+        if (o < P) {
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) { MK[o + j] = k[j]; MG[o + j] = g[j]; }
+        }
+        __syncthreads();
+        if (o < P) {
+            const uint32_t base = o & ~(2 * L - 1), d = o - base;
+            const uint32_t a = base, b = base + L;
+            uint32_t lo = d > L ? d - L : 0, hi = d < L ? d : L;
+            while (lo < hi) {   // merge path: A[mid] goes first unless B[d-1-mid] < A[mid]
+                uint32_t mid = (lo + hi) >> 1;
+                uint32_t bi = b + d - 1 - mid;
+                if (!gk_less(MK[bi], MG[bi], MK[a + mid], MG[a + mid])) lo = mid + 1; else hi = mid;
+            }
+            uint32_t i = lo, jj = d - lo;
+            uint64_t ka = i < L ? MK[a + i] : 0, kb = jj < L ? MK[b + jj] : 0;
+            uint32_t ga = i < L ? MG[a + i] : 0, gb = jj < L ? MG[b + jj] : 0;
+#pragma unroll
+            for (int q = 0; q < ITEMS; q++) {
+                bool takeA = jj >= L || (i < L && !gk_less(kb, gb, ka, ga));
+                if (takeA) {
+                    k[q] = ka; g[q] = ga; i++;
+                    if (i < L) { ka = MK[a + i]; ga = MG[a + i]; }
+                } else {
+                    k[q] = kb; g[q] = gb; jj++;
+                    if (jj < L) { kb = MK[b + jj]; gb = MG[b + jj]; }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// block-wide scan over slots [0, M) of v (blocked, ITEMS per thread):
+// MAXSCAN: inclusive max; else exclusive sum (returns the total)
+template <int NT, int ITEMS, bool MAXSCAN>
+__device__ __forceinline__ uint32_t block_scan(uint32_t *v, uint32_t M, uint32_t *wsum) {
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    constexpr int NW = NT / 32;
+    const uint32_t base = threadIdx.x * ITEMS;
+    uint32_t loc[ITEMS];
+    uint32_t run = 0;
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++) {
+        uint32_t x = (base + j < M) ? v[base + j] : 0;
+        if (MAXSCAN) { run = max(run, x); loc[j] = run; }
+        else { loc[j] = run; run += x; }
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= (uint32_t)o) incl = MAXSCAN ? max(incl, y) : incl + y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t prev = 0, total = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) {
+        uint32_t x = wsum[w];
+        if (w < (int)warp) prev = MAXSCAN ? max(prev, x) : prev + x;
+        total = MAXSCAN ? max(total, x) : total + x;
+    }
+    uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) ex = MAXSCAN ? 0u : 0u;
+    ex = MAXSCAN ? max(ex, prev) : ex + prev;
+#pragma unroll
+    for (int j = 0; j < ITEMS; j++)
+        if (base + j < M) v[base + j] = MAXSCAN ? max(loc[j], ex) : loc[j] + ex;
+    __syncthreads();
+    return total;
+}
+
+template <int NT, int ITEMS>
+struct BaseSmem {
+    static constexpr uint32_t CAP = NT * ITEMS;
+    uint64_t SK[CAP];        // key at the current depth by position; merge buffer while sorting
+    uint32_t MG[CAP];        // merge buffer; scan buffer between sorts
+    uint32_t SI[CAP];        // string index by original index
+    uint16_t SP[CAP];        // original index at each position
+    uint16_t SG[CAP];        // first position of the group of each position
+    uint16_t GS[CAP];        // size of the group that starts at a position
+    uint16_t ACT[2][CAP];    // positions still being sorted, in order (ping-pong)
+    uint32_t WL[CAP / 2];    // groups of 2..32 strings for the warps: start << 16 | size
+    uint32_t wsum[NT / 32];
+    uint32_t nwl;
+};
+
+template <int NT, int ITEMS>
+__global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
+                                                 const uint32_t *idx0, const uint64_t *key0, const uint32_t *idx1,
+                                                 const uint64_t *key1) {
+    constexpr uint32_t CAP = NT * ITEMS;
+    constexpr int NW = NT / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    BaseSmem<NT, ITEMS> &S = *reinterpret_cast<BaseSmem<NT, ITEMS> *>(smem_raw);
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (uint32_t tk = blockIdx.x; tk < ntask; tk += gridDim.x) {
+        const SmallTask t = tasks[tk];
+        const uint32_t *idx = t.parity ? idx1 : idx0;
+        const uint64_t *key = t.parity ? key1 : key0;
+        const ReqDesc &R = reqs[t.req];
+        const uint32_t m = t.size <= CAP ? t.size : CAP;
+        const uint32_t lbase = t.begin - R.base;
+        for (uint32_t i = tid; i < m; i += NT) {
+            S.SI[i] = idx[t.begin + i];
+            S.SK[i] = key[t.begin + i];
+            S.SP[i] = (uint16_t)i;
+            S.SG[i] = 0;
+            S.ACT[0][i] = (uint16_t)i;
+        }
+        if (tid == 0) { S.GS[0] = (uint16_t)min(m, 0xFFFFu); S.nwl = 0; }
+        uint32_t M = m, depth = t.depth, cur = 0;
+        __syncthreads();
+        while (M > 0) {
+            const uint16_t *act = S.ACT[cur];
+            // load the active slots, sort them by (group, key, original index)
+            uint64_t k[ITEMS];
+            uint32_t g[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                uint32_t s = tid * ITEMS + j;
+                if (s < M) {
+                    uint32_t pos = act[s];
+                    k[j] = S.SK[pos];
+                    g[j] = ((uint32_t)S.SG[pos] << 12) | S.SP[pos];
+                } else {
+                    k[j] = ~0ull;
+                    g[j] = 0xFFFFFFFFu;
+                }
+            }
+            uint32_t P = ITEMS;
+            while (P < M) P <<= 1;
+            __syncthreads();
+            block_merge_sort<NT, ITEMS>(k, g, P, S.SK, S.MG);
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                uint32_t s = tid * ITEMS + j;
+                if (s < M) {
+                    uint32_t pos = act[s];
+                    S.SK[pos] = k[j];
+                    S.SP[pos] = (uint16_t)(g[j] & 0xFFFu);
+                }
+            }
+            __syncthreads();
+            // split groups: LCPs at new boundaries, new group starts (as positions, max-scanned)
+            for (uint32_t s = tid; s < M; s += NT) {
+                uint32_t pos = act[s];
+                uint32_t st = 1;
+                if (pos != S.SG[pos]) {   // not the first position of its group
+                    uint64_t a = S.SK[pos - 1], b = S.SK[pos];
+                    if (a != b) R.lcp_out[lbase + pos] = depth + lcp8(a, b);
+                    else if (has_zero(b)) R.lcp_out[lbase + pos] = depth + nulpos(b);
+                    else st = 0;
+                }
+                S.MG[s] = st ? pos : 0u;
+            }
+            __syncthreads();
+            block_scan<NT, ITEMS, true>(S.MG, M, S.wsum);
+            // group sizes at each group's last slot; small groups to the warp list
+            for (uint32_t s = tid; s < M; s += NT) {
+                uint32_t pos = act[s];
+                uint32_t ng = S.MG[s];
+                bool last = (s + 1 == M) || S.MG[s + 1] != ng;
+                S.SG[pos] = (uint16_t)ng;
+                if (last) {
+                    uint32_t size = pos - ng + 1;
+                    S.GS[ng] = (uint16_t)size;
+                    if (size >= 2 && size <= 32) {
+                        uint32_t w = atomicAdd(&S.nwl, 1u);
+                        S.WL[w] = (ng << 16) | size;
+                    }
+                }
+            }
+            __syncthreads();
+            // positions in groups of more than 32 stay; they read the key 8 characters deeper
+            uint16_t *nact = S.ACT[cur ^ 1];
+            for (uint32_t s = tid; s < M; s += NT) {
+                uint32_t pos = act[s];
+                S.MG[s] = S.GS[S.SG[pos]] > 32 ? 1u : 0u;
+            }
+            __syncthreads();
+            uint32_t M2 = block_scan<NT, ITEMS, false>(S.MG, M, S.wsum);
+            for (uint32_t s = tid; s < M; s += NT) {
+                uint32_t pos = act[s];
+                if (S.GS[S.SG[pos]] > 32) {
+                    nact[S.MG[s]] = (uint16_t)pos;
+                    S.SK[pos] = load_key(R, S.SI[S.SP[pos]], depth + 8);
+                }
+            }
+            // warps finish the small groups
+            const uint32_t nwl = S.nwl;
+            for (uint32_t w = warp; w < nwl; w += NW) {
+                uint32_t e = S.WL[w];
+                uint32_t s0 = e >> 16, sz = e & 0xFFFFu;
+                uint32_t id = 0;
+                uint64_t kk = 0;
+                if (lane < sz) {
+                    id = S.SI[S.SP[s0 + lane]];
+                    kk = load_key(R, id, depth + 8);
+                }
+                warp_finish(R, sz, depth + 8, id, kk, lbase + s0);
+            }
+            __syncthreads();
+            if (tid == 0) S.nwl = 0;
+            M = M2;
+            depth += 8;
+            cur ^= 1;
+            __syncthreads();
+        }
+        // positions that ended as groups of one
+        for (uint32_t i = tid; i < m; i += NT)
+            if (S.GS[S.SG[i]] == 1) R.perm_out[lbase + i] = S.SI[S.SP[i]];
+        __syncthreads();
+    }
+}
+
+}  // namespace ss

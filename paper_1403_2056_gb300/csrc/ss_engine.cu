@@ -16,7 +16,7 @@
 //                  the base case; bucket boundaries recorded for LCPs
 //
 // Segments of at most kSmallMax strings are sorted completely by the base
-// case (k_small_warp / k_small_cta), which also emits their LCPs
+// case (k_small_warp / k_base_cta in ss_base.cuh), which also emits their LCPs
 // (the role of LCP insertion sort, Algorithm 5).  The LCP between the last
 // string of one bucket and the first of the next is depth + lcp of their keys
 // at that depth (Section 4.4, "LCPs for free"), computed in k_boundary once all
@@ -29,6 +29,7 @@
 #include <vector>
 
 #include "ss_internal.cuh"
+#include "ss_base.cuh"
 
 namespace ss {
 
@@ -641,219 +642,7 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
     }
 }
 
-// ------------------------------------------------------- base case sorters
-// A base-case segment shares its first `depth` characters.  Repeat: sort by
-// (group, key, index); neighbours of one group with different keys are split
-// (LCP = depth + lcp of keys); equal keys that hold the string end are equal
-// strings (LCP = depth + their length past depth); groups of equal keys
-// without the end continue 8 characters deeper.  Groups are contiguous and
-// carry their first position as id, so sorting by it keeps them in place,
-// and positions already split never move.  The LCP belongs to the position
-// (every member of a group shares the key that fixed it).
-
-struct Elem {
-    uint32_t g;   // group id: first position of the group (0xFFFFFFFF: padding)
-    uint32_t i;   // string index
-    uint64_t k;   // key at the current depth
-};
-
-__device__ __forceinline__ bool elem_less(const Elem &a, const Elem &b) {
-    if (a.g != b.g) return a.g < b.g;
-    if (a.k != b.k) return a.k < b.k;
-    return a.i < b.i;   // inside a segment input order equals index order
-}
-
-__device__ __forceinline__ Elem shfl_xor_elem(const Elem &e, int m) {
-    Elem r;
-    r.g = __shfl_xor_sync(0xffffffffu, e.g, m);
-    r.i = __shfl_xor_sync(0xffffffffu, e.i, m);
-    r.k = __shfl_xor_sync(0xffffffffu, e.k, m);
-    return r;
-}
-
-__global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
-                                                         const uint32_t *idx0, const uint64_t *key0,
-                                                         const uint32_t *idx1, const uint64_t *key1) {
-    const uint32_t lane = threadIdx.x & 31;
-    const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-    for (uint32_t tk = gw; tk < ntask; tk += nw) {
-        SmallTask t = tasks[tk];
-        const uint32_t *idx = t.parity ? idx1 : idx0;
-        const uint64_t *key = t.parity ? key1 : key0;
-        const ReqDesc &R = reqs[t.req];
-        const uint32_t m = t.size;
-        Elem e;
-        if (lane < m) { e.g = 0; e.i = idx[t.begin + lane]; e.k = key[t.begin + lane]; }
-        else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k = ~0ull; }
-        uint32_t lcp = 0;
-        uint32_t depth = t.depth;
-        for (;;) {
-            // bitonic sort across the warp
-            for (int k = 2; k <= 32; k <<= 1) {
-                for (int j = k >> 1; j > 0; j >>= 1) {
-                    Elem o = shfl_xor_elem(e, j);
-                    bool up = (lane & k) == 0;
-                    bool lower = (lane & j) == 0;
-                    bool take_o = lower == up ? elem_less(o, e) : elem_less(e, o);
-                    if (take_o) e = o;
-                }
-            }
-            uint32_t pg = __shfl_up_sync(0xffffffffu, e.g, 1);
-            uint64_t pk = __shfl_up_sync(0xffffffffu, e.k, 1);
-            bool start = true;
-            if (lane > 0 && lane < m && pg == e.g) {
-                if (pk != e.k) lcp = depth + lcp8(pk, e.k);
-                else if (has_zero(e.k)) lcp = depth + nulpos(e.k);
-                else start = false;
-            }
-            if (lane >= m) start = true;
-            uint32_t sg = start ? lane : 0;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                uint32_t y = __shfl_up_sync(0xffffffffu, sg, o);
-                if (lane >= (uint32_t)o) sg = max(sg, y);
-            }
-            bool next_start = __shfl_down_sync(0xffffffffu, start, 1) || lane == 31;
-            bool active = lane < m && !(start && next_start);
-            if (lane < m) e.g = sg;
-            if (!__any_sync(0xffffffffu, active)) break;
-            depth += 8;
-            if (active) e.k = load_key(R, e.i, depth);
-        }
-        if (lane < m) {
-            uint32_t local = t.begin - R.base + lane;
-            R.perm_out[local] = e.i;
-            if (lane > 0) R.lcp_out[local] = lcp;
-        }
-    }
-}
-
-template <uint32_t CAP, int NT>
-struct SmallCtaSmem {
-    Elem e[CAP];
-    uint32_t lcp[CAP];
-    uint32_t flag[CAP];
-    uint32_t wtot[NT / 32];
-    uint32_t any;
-};
-
-// block-wide inclusive max-scan of per-position values v[0..P) held in smem (in place)
-template <uint32_t CAP, int NT>
-__device__ void block_max_scan(uint32_t *v, uint32_t P, uint32_t *wtot) {
-    constexpr uint32_t PER = CAP / NT;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t base = threadIdx.x * PER;
-    uint32_t run = 0;
-    uint32_t loc[PER];
-#pragma unroll
-    for (uint32_t k = 0; k < PER; k++) {
-        uint32_t x = (base + k < P) ? v[base + k] : 0;
-        run = max(run, x);
-        loc[k] = run;
-    }
-    uint32_t incl = run;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= (uint32_t)o) incl = max(incl, y);
-    }
-    if (lane == 31) wtot[warp] = incl;
-    __syncthreads();
-    uint32_t prev = 0;
-    for (uint32_t w = 0; w < warp; w++) prev = max(prev, wtot[w]);
-    uint32_t ex = __shfl_up_sync(0xffffffffu, incl, 1);
-    if (lane == 0) ex = 0;
-    ex = max(ex, prev);
-#pragma unroll
-    for (uint32_t k = 0; k < PER; k++)
-        if (base + k < P) v[base + k] = max(loc[k], ex);
-    __syncthreads();
-}
-
-template <uint32_t CAP, int NT>
-__global__ void __launch_bounds__(NT) k_small_cta(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
-                                                  const uint32_t *idx0, const uint64_t *key0,
-                                                  const uint32_t *idx1, const uint64_t *key1) {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    SmallCtaSmem<CAP, NT> &S = *reinterpret_cast<SmallCtaSmem<CAP, NT> *>(smem_raw);
-    for (uint32_t tk = blockIdx.x; tk < ntask; tk += gridDim.x) {
-        SmallTask t = tasks[tk];
-        const uint32_t *idx = t.parity ? idx1 : idx0;
-        const uint64_t *key = t.parity ? key1 : key0;
-        const ReqDesc &R = reqs[t.req];
-        const uint32_t m = t.size;
-        uint32_t P = 1;
-        while (P < m) P <<= 1;
-        for (uint32_t i = threadIdx.x; i < P; i += NT) {
-            Elem e;
-            if (i < m) { e.g = 0; e.i = idx[t.begin + i]; e.k = key[t.begin + i]; }
-            else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k = ~0ull; }
-            S.e[i] = e;
-            S.lcp[i] = 0;
-        }
-        uint32_t depth = t.depth;
-        __syncthreads();
-        for (;;) {
-            // bitonic sort of S.e[0..P)
-            for (uint32_t k = 2; k <= P; k <<= 1) {
-                for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                    for (uint32_t q = threadIdx.x; q < P / 2; q += NT) {
-                        uint32_t i = 2 * q - (q & (j - 1));
-                        uint32_t l = i + j;
-                        bool up = (i & k) == 0;
-                        Elem a = S.e[i], b = S.e[l];
-                        if (elem_less(b, a) == up) { S.e[i] = b; S.e[l] = a; }
-                    }
-                    __syncthreads();
-                }
-            }
-            // split groups, record LCPs
-            for (uint32_t i = threadIdx.x; i < P; i += NT) {
-                uint32_t start = 1;
-                if (i > 0 && i < m) {
-                    Elem p = S.e[i - 1], c = S.e[i];
-                    if (p.g == c.g) {
-                        if (p.k != c.k) S.lcp[i] = depth + lcp8(p.k, c.k);
-                        else if (has_zero(c.k)) S.lcp[i] = depth + nulpos(c.k);
-                        else start = 0;
-                    }
-                }
-                S.flag[i] = start ? i : 0;
-            }
-            if (threadIdx.x == 0) S.any = 0;
-            __syncthreads();
-            // starts (flag = own position) before the max-scan turns them into group ids
-            bool act_local = false;
-            for (uint32_t i = threadIdx.x; i < m; i += NT) {
-                bool st = (i == 0) || S.flag[i] != 0;
-                bool nst = (i + 1 >= m) || S.flag[i + 1] != 0;
-                if (!(st && nst)) act_local = true;
-            }
-            if (act_local) S.any = 1;
-            __syncthreads();
-            block_max_scan<CAP, NT>(S.flag, P, S.wtot);
-            bool any = S.any != 0;
-            for (uint32_t i = threadIdx.x; i < m; i += NT) S.e[i].g = S.flag[i];
-            __syncthreads();
-            if (!any) break;
-            depth += 8;
-            // reload keys of elements in groups of two or more
-            for (uint32_t i = threadIdx.x; i < m; i += NT) {
-                uint32_t g = S.e[i].g;
-                bool single = (g == i) && (i + 1 >= m || S.e[i + 1].g == i + 1);
-                if (!single) S.e[i].k = load_key(R, S.e[i].i, depth);
-            }
-            __syncthreads();
-        }
-        for (uint32_t i = threadIdx.x; i < m; i += NT) {
-            uint32_t local = t.begin - R.base + i;
-            R.perm_out[local] = S.e[i].i;
-            if (i > 0) R.lcp_out[local] = S.lcp[i];
-        }
-        __syncthreads();
-    }
-}
+// base case sorters: ss_base.cuh
 
 // ------------------------------------------------------------ k_boundary
 
@@ -917,8 +706,8 @@ static cudaError_t ensure_attrs() {
     if ((e = set_smem(k_classify, sizeof(ClassifySmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_SORT>, sizeof(ScatterSmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_CLASSIFY>, sizeof(ScatterSmem)))) return e;
-    if ((e = set_smem(k_small_cta<kMidMax, 256>, sizeof(SmallCtaSmem<kMidMax, 256>)))) return e;
-    if ((e = set_smem(k_small_cta<kSmallMax, 512>, sizeof(SmallCtaSmem<kSmallMax, 512>)))) return e;
+    if ((e = set_smem(k_base_cta<64, 8>, sizeof(BaseSmem<64, 8>)))) return e;
+    if ((e = set_smem(k_base_cta<512, 8>, sizeof(BaseSmem<512, 8>)))) return e;
     if (dev < 64) g_attrs_done[dev] = true;
     return cudaSuccess;
 }
@@ -1113,12 +902,12 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             SS_LAUNCH_U("small_warp", st, hc[C_E_TINY], k_small_warp<<<grid, kThreads, 0, st>>>(tiny, ntiny, dreqs, idx[0], key[0], idx[1], key[1]));
         }
         if (nmid) {
-            uint32_t grid = std::min<uint32_t>(nmid, sms * 8);
-            SS_LAUNCH_U("small_cta512", st, hc[C_E_MID], (k_small_cta<kMidMax, 256><<<grid, 256, sizeof(SmallCtaSmem<kMidMax, 256>), st>>>(mid, nmid, dreqs, idx[0], key[0], idx[1], key[1])));
+            uint32_t grid = std::min<uint32_t>(nmid, sms * 16);
+            SS_LAUNCH_U("small_cta512", st, hc[C_E_MID], (k_base_cta<64, 8><<<grid, 64, sizeof(BaseSmem<64, 8>), st>>>(mid, nmid, dreqs, idx[0], key[0], idx[1], key[1])));
         }
         if (nlarge) {
             uint32_t grid = std::min<uint32_t>(nlarge, sms * 2);
-            SS_LAUNCH_U("small_cta4096", st, hc[C_E_LARGE], (k_small_cta<kSmallMax, 512><<<grid, 512, sizeof(SmallCtaSmem<kSmallMax, 512>), st>>>(large, nlarge, dreqs, idx[0], key[0], idx[1], key[1])));
+            SS_LAUNCH_U("small_cta4096", st, hc[C_E_LARGE], (k_base_cta<512, 8><<<grid, 512, sizeof(BaseSmem<512, 8>), st>>>(large, nlarge, dreqs, idx[0], key[0], idx[1], key[1])));
         }
         TRY(cudaGetLastError(), "base case launch");
         if (nb) {

@@ -23,7 +23,7 @@
 
 namespace ss {
 
-constexpr uint32_t kMergeItems = 16;
+constexpr uint32_t kMergeItems = 64;
 
 // full comparison of strings a and b from depth h on (both share h characters);
 // returns -1/0/+1 and the lcp in *l
