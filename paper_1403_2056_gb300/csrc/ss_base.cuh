@@ -4,8 +4,10 @@
 // Algorithm 5, plays in the paper's pS5).
 //
 // A segment is sorted by its 8-character keys once, with a CTA merge sort
-// (ITEMS keys per thread sorted in registers, then merge-path passes through
-// shared memory).  Neighbours with different keys are split (LCP = depth +
+// (8 keys per thread sorted in registers, then merge-path passes through
+// padded, bank-conflict-free shared memory).  Sorting is skipped when every
+// group's keys are already equal.  Neighbours with different keys are split
+// (LCP = depth +
 // lcp of the keys); neighbours with equal keys that hold the end of the
 // string are equal strings (LCP = their length); runs of equal keys without
 // the end form groups that continue 8 characters deeper.  Groups of at most
@@ -22,14 +24,16 @@ namespace ss {
 
 // ----------------------------------------------------------- warp finish
 struct WElem {
-    uint32_t g;   // group id: first lane of its group (0xFFFFFFFF: padding)
-    uint32_t i;   // string index
-    uint64_t k;   // key at the current depth
+    uint32_t g;    // group id: first lane of its group (0xFFFFFFFF: padding)
+    uint32_t i;    // string index
+    uint64_t k0;   // characters [depth, depth + 8)
+    uint64_t k1;   // characters [depth + 8, depth + 16)
 };
 
 __device__ __forceinline__ bool welem_less(const WElem &a, const WElem &b) {
     if (a.g != b.g) return a.g < b.g;
-    if (a.k != b.k) return a.k < b.k;
+    if (a.k0 != b.k0) return a.k0 < b.k0;
+    if (a.k1 != b.k1) return a.k1 < b.k1;
     return a.i < b.i;   // inside a segment input order equals index order
 }
 
@@ -37,23 +41,25 @@ __device__ __forceinline__ WElem shfl_xor_welem(const WElem &e, int m) {
     WElem r;
     r.g = __shfl_xor_sync(0xffffffffu, e.g, m);
     r.i = __shfl_xor_sync(0xffffffffu, e.i, m);
-    r.k = __shfl_xor_sync(0xffffffffu, e.k, m);
+    r.k0 = __shfl_xor_sync(0xffffffffu, e.k0, m);
+    r.k1 = __shfl_xor_sync(0xffffffffu, e.k1, m);
     return r;
 }
 
 // Sort one group of m <= 32 strings completely with one warp (all 32 lanes
-// call this).  Lane l < m holds string index `id` and its key at `depth`.
-// Writes perm and lcp of R-local positions out .. out + m - 1 (not the lcp of
-// position `out`, which the caller owns).
-__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t key,
-                                            uint32_t out) {
+// call this), 16 characters per round.  Lane l < m holds string index `id`
+// and its 16 characters at `depth`.  Writes perm and lcp of R-local positions
+// out .. out + m - 1 (not the lcp of position `out`, which the caller owns).
+__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t k0,
+                                            uint64_t k1, uint32_t out) {
     const uint32_t lane = threadIdx.x & 31;
     WElem e;
-    if (lane < m) { e.g = 0; e.i = id; e.k = key; }
-    else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k = ~0ull; }
+    if (lane < m) { e.g = 0; e.i = id; e.k0 = k0; e.k1 = k1; }
+    else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k0 = ~0ull; e.k1 = ~0ull; }
     uint32_t lcp = 0;
     for (;;) {
         for (int k = 2; k <= 32; k <<= 1) {
+            if ((uint32_t)(k >> 1) >= m && k > 2) break;   // lanes >= m hold padding only
             for (int j = k >> 1; j > 0; j >>= 1) {
                 WElem o = shfl_xor_welem(e, j);
                 bool up = (lane & k) == 0;
@@ -63,11 +69,14 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
             }
         }
         uint32_t pg = __shfl_up_sync(0xffffffffu, e.g, 1);
-        uint64_t pk = __shfl_up_sync(0xffffffffu, e.k, 1);
+        uint64_t p0 = __shfl_up_sync(0xffffffffu, e.k0, 1);
+        uint64_t p1 = __shfl_up_sync(0xffffffffu, e.k1, 1);
         bool start = true;
         if (lane > 0 && lane < m && pg == e.g) {
-            if (pk != e.k) lcp = depth + lcp8(pk, e.k);
-            else if (has_zero(e.k)) lcp = depth + nulpos(e.k);
+            if (p0 != e.k0) lcp = depth + lcp8(p0, e.k0);
+            else if (has_zero(e.k0)) lcp = depth + nulpos(e.k0);
+            else if (p1 != e.k1) lcp = depth + 8 + lcp8(p1, e.k1);
+            else if (has_zero(e.k1)) lcp = depth + 8 + nulpos(e.k1);
             else start = false;
         }
         if (lane >= m) start = true;
@@ -81,8 +90,8 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
         bool active = lane < m && !(start && next_start);
         if (lane < m) e.g = sg;
         if (!__any_sync(0xffffffffu, active)) break;
-        depth += 8;
-        if (active) e.k = load_key(R, e.i, depth);
+        depth += 16;
+        if (active) load_key2(R, e.i, depth, e.k0, e.k1);
     }
     if (lane < m) {
         R.perm_out[out + lane] = e.i;
@@ -90,21 +99,33 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
     }
 }
 
-__global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
-                                                         const uint32_t *idx0, const uint64_t *key0,
-                                                         const uint32_t *idx1, const uint64_t *key1) {
+// Tiny base cases (2..32 strings), one warp each.  The task count is read on
+// the device: the CTA base cases below append groups to the same list.
+__global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, const uint32_t *ntask_dev,
+                                                         const ReqDesc *reqs, const uint32_t *idx0,
+                                                         const uint64_t *key0, const uint32_t *idx1,
+                                                         const uint64_t *key1) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+    const uint32_t ntask = *ntask_dev;
     for (uint32_t tk = gw; tk < ntask; tk += nw) {
         SmallTask t = tasks[tk];
         const uint32_t *idx = t.parity ? idx1 : idx0;
         const uint64_t *key = t.parity ? key1 : key0;
         const ReqDesc &R = reqs[t.req];
         uint32_t id = 0;
-        uint64_t k = 0;
-        if (lane < t.size) { id = idx[t.begin + lane]; k = key[t.begin + lane]; }
-        warp_finish(R, t.size, t.depth, id, k, t.begin - R.base);
+        uint64_t k0 = 0, k1 = 0;
+        if (lane < t.size) {
+            id = idx[t.begin + lane];
+            if (t.gather) {
+                load_key2(R, id, t.depth, k0, k1);
+            } else {
+                k0 = key[t.begin + lane];
+                k1 = has_zero(k0) ? 0ull : load_key(R, id, t.depth + 8);
+            }
+        }
+        warp_finish(R, t.size, t.depth, id, k0, k1, t.begin - R.base);
     }
 }
 
@@ -118,6 +139,11 @@ __device__ __forceinline__ bool gk_less(uint64_t ka, uint32_t ga, uint64_t kb, u
     if (ka != kb) return ka < kb;
     return (ga & 0xFFFu) < (gb & 0xFFFu);
 }
+
+// Shared-memory slot index with one pad word per 8 slots: thread t's blocked
+// slots t*8 .. t*8+7 then fall in distinct banks across a warp (9t + j is a
+// bijection mod 32), so the blocked stores and loads below are conflict-free.
+__device__ __forceinline__ uint32_t padx(uint32_t x) { return x + (x >> 3); }
 
 template <int ITEMS>
 __device__ __forceinline__ void reg_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITEMS]) {
@@ -135,8 +161,9 @@ __device__ __forceinline__ void reg_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITE
 }
 
 // Sort the P (power of two, >= ITEMS) slots held blocked in registers
-// (thread t holds slots t*ITEMS ..) through the shared buffers MK / MG.
-// On return each thread holds its ITEMS slots of the sorted sequence.
+// (thread t holds slots t*ITEMS ..) through the padded shared buffers MK / MG
+// (sized for padx(P)).  On return each thread holds its ITEMS slots of the
+// sorted sequence.
 template <int NT, int ITEMS>
 __device__ __forceinline__ void block_merge_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITEMS], uint32_t P, uint64_t *MK,
                                                  uint32_t *MG) {
@@ -145,7 +172,7 @@ __device__ __forceinline__ void block_merge_sort(uint64_t (&k)[ITEMS], uint32_t 
     for (uint32_t L = ITEMS; L < P; L <<= 1) {
         if (o < P) {
 #pragma unroll
-            for (int j = 0; j < ITEMS; j++) { MK[o + j] = k[j]; MG[o + j] = g[j]; }
+            for (int j = 0; j < ITEMS; j++) { MK[padx(o + j)] = k[j]; MG[padx(o + j)] = g[j]; }
         }
         __syncthreads();
         if (o < P) {
@@ -154,21 +181,21 @@ __device__ __forceinline__ void block_merge_sort(uint64_t (&k)[ITEMS], uint32_t 
             uint32_t lo = d > L ? d - L : 0, hi = d < L ? d : L;
             while (lo < hi) {   // merge path: A[mid] goes first unless B[d-1-mid] < A[mid]
                 uint32_t mid = (lo + hi) >> 1;
-                uint32_t bi = b + d - 1 - mid;
-                if (!gk_less(MK[bi], MG[bi], MK[a + mid], MG[a + mid])) lo = mid + 1; else hi = mid;
+                uint32_t bi = padx(b + d - 1 - mid), ai = padx(a + mid);
+                if (!gk_less(MK[bi], MG[bi], MK[ai], MG[ai])) lo = mid + 1; else hi = mid;
             }
             uint32_t i = lo, jj = d - lo;
-            uint64_t ka = i < L ? MK[a + i] : 0, kb = jj < L ? MK[b + jj] : 0;
-            uint32_t ga = i < L ? MG[a + i] : 0, gb = jj < L ? MG[b + jj] : 0;
+            uint64_t ka = i < L ? MK[padx(a + i)] : 0, kb = jj < L ? MK[padx(b + jj)] : 0;
+            uint32_t ga = i < L ? MG[padx(a + i)] : 0, gb = jj < L ? MG[padx(b + jj)] : 0;
 #pragma unroll
             for (int q = 0; q < ITEMS; q++) {
                 bool takeA = jj >= L || (i < L && !gk_less(kb, gb, ka, ga));
                 if (takeA) {
                     k[q] = ka; g[q] = ga; i++;
-                    if (i < L) { ka = MK[a + i]; ga = MG[a + i]; }
+                    if (i < L) { ka = MK[padx(a + i)]; ga = MG[padx(a + i)]; }
                 } else {
                     k[q] = kb; g[q] = gb; jj++;
-                    if (jj < L) { kb = MK[b + jj]; gb = MG[b + jj]; }
+                    if (jj < L) { kb = MK[padx(b + jj)]; gb = MG[padx(b + jj)]; }
                 }
             }
         }
@@ -219,22 +246,23 @@ __device__ __forceinline__ uint32_t block_scan(uint32_t *v, uint32_t M, uint32_t
 template <int NT, int ITEMS>
 struct BaseSmem {
     static constexpr uint32_t CAP = NT * ITEMS;
-    uint64_t SK[CAP];        // key at the current depth by position; merge buffer while sorting
-    uint32_t MG[CAP];        // merge buffer; scan buffer between sorts
+    uint64_t SK[CAP + CAP / 8];   // key at the current depth by position; padded merge buffer while sorting
+    uint32_t MG[CAP + CAP / 8];   // padded merge buffer; scan buffer between sorts
     uint32_t SI[CAP];        // string index by original index
     uint16_t SP[CAP];        // original index at each position
     uint16_t SG[CAP];        // first position of the group of each position
     uint16_t GS[CAP];        // size of the group that starts at a position
-    uint16_t ACT[2][CAP];    // positions still being sorted, in order (ping-pong)
+    uint16_t ACT[CAP];       // positions still being sorted, in order
     uint32_t WL[CAP / 2];    // groups of 2..32 strings for the warps: start << 16 | size
     uint32_t wsum[NT / 32];
-    uint32_t nwl;
+    uint32_t nwl, nws, wbase;   // small groups, their strings, first reserved list slot
 };
 
 template <int NT, int ITEMS>
 __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
-                                                 const uint32_t *idx0, const uint64_t *key0, const uint32_t *idx1,
-                                                 const uint64_t *key1) {
+                                                 uint32_t *idx0, const uint64_t *key0, uint32_t *idx1,
+                                                 const uint64_t *key1, SmallTask *tiny, uint32_t tiny_cap,
+                                                 uint32_t *counters) {
     constexpr uint32_t CAP = NT * ITEMS;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -242,7 +270,7 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t tk = blockIdx.x; tk < ntask; tk += gridDim.x) {
         const SmallTask t = tasks[tk];
-        const uint32_t *idx = t.parity ? idx1 : idx0;
+        uint32_t *idx = t.parity ? idx1 : idx0;
         const uint64_t *key = t.parity ? key1 : key0;
         const ReqDesc &R = reqs[t.req];
         const uint32_t m = t.size <= CAP ? t.size : CAP;
@@ -252,13 +280,13 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
             S.SK[i] = key[t.begin + i];
             S.SP[i] = (uint16_t)i;
             S.SG[i] = 0;
-            S.ACT[0][i] = (uint16_t)i;
+            S.ACT[i] = (uint16_t)i;
         }
-        if (tid == 0) { S.GS[0] = (uint16_t)min(m, 0xFFFFu); S.nwl = 0; }
-        uint32_t M = m, depth = t.depth, cur = 0;
+        if (tid == 0) { S.GS[0] = (uint16_t)min(m, 0xFFFFu); S.nwl = 0; S.nws = 0; }
+        uint32_t M = m, depth = t.depth;
         __syncthreads();
         while (M > 0) {
-            const uint16_t *act = S.ACT[cur];
+            const uint16_t *act = S.ACT;
             // load the active slots, sort them by (group, key, original index)
             uint64_t k[ITEMS];
             uint32_t g[ITEMS];
@@ -274,17 +302,29 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
                     g[j] = 0xFFFFFFFFu;
                 }
             }
-            uint32_t P = ITEMS;
-            while (P < M) P <<= 1;
-            __syncthreads();
-            block_merge_sort<NT, ITEMS>(k, g, P, S.SK, S.MG);
+            // groups whose keys are all equal need no sort (common when a whole
+            // segment shares a long prefix): sort only if some neighbour differs
+            bool differ = false;
 #pragma unroll
             for (int j = 0; j < ITEMS; j++) {
                 uint32_t s = tid * ITEMS + j;
-                if (s < M) {
-                    uint32_t pos = act[s];
-                    S.SK[pos] = k[j];
-                    S.SP[pos] = (uint16_t)(g[j] & 0xFFFu);
+                if (s > 0 && s < M) {
+                    uint32_t pos = act[s], prv = act[s - 1];
+                    if (S.SG[pos] == S.SG[prv] && S.SK[pos] != S.SK[prv]) differ = true;
+                }
+            }
+            if (__syncthreads_or(differ)) {
+                uint32_t P = ITEMS;
+                while (P < M) P <<= 1;
+                block_merge_sort<NT, ITEMS>(k, g, P, S.SK, S.MG);
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) {
+                    uint32_t s = tid * ITEMS + j;
+                    if (s < M) {
+                        uint32_t pos = act[s];
+                        S.SK[pos] = k[j];
+                        S.SP[pos] = (uint16_t)(g[j] & 0xFFFu);
+                    }
                 }
             }
             __syncthreads();
@@ -313,44 +353,62 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
                     S.GS[ng] = (uint16_t)size;
                     if (size >= 2 && size <= 32) {
                         uint32_t w = atomicAdd(&S.nwl, 1u);
+                        atomicAdd(&S.nws, size);
                         S.WL[w] = (ng << 16) | size;
                     }
                 }
             }
             __syncthreads();
-            // positions in groups of more than 32 stay; they read the key 8 characters deeper
-            uint16_t *nact = S.ACT[cur ^ 1];
-            for (uint32_t s = tid; s < M; s += NT) {
-                uint32_t pos = act[s];
-                S.MG[s] = S.GS[S.SG[pos]] > 32 ? 1u : 0u;
+            // positions in groups of more than 32 stay; they read the key 8 characters
+            // deeper.  The list of positions is compacted in place: every thread
+            // holds its slots in registers before any slot is overwritten.
+            uint32_t spos[ITEMS];
+            bool stays[ITEMS];
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                uint32_t s = tid * ITEMS + j;
+                stays[j] = false;
+                spos[j] = 0;
+                if (s < M) {
+                    spos[j] = act[s];
+                    stays[j] = S.GS[S.SG[spos[j]]] > 32;
+                    S.MG[s] = stays[j] ? 1u : 0u;
+                }
             }
             __syncthreads();
             uint32_t M2 = block_scan<NT, ITEMS, false>(S.MG, M, S.wsum);
-            for (uint32_t s = tid; s < M; s += NT) {
-                uint32_t pos = act[s];
-                if (S.GS[S.SG[pos]] > 32) {
-                    nact[S.MG[s]] = (uint16_t)pos;
+#pragma unroll
+            for (int j = 0; j < ITEMS; j++) {
+                uint32_t s = tid * ITEMS + j;
+                if (s < M && stays[j]) {
+                    uint32_t pos = spos[j];
+                    S.ACT[S.MG[s]] = (uint16_t)pos;
                     S.SK[pos] = load_key(R, S.SI[S.SP[pos]], depth + 8);
                 }
             }
-            // warps finish the small groups
+            // groups of 2..32 strings go to the warp kernel: their string indices in
+            // sorted order back to the index buffer, keys gathered there; one
+            // reservation of list slots per CTA and iteration
             const uint32_t nwl = S.nwl;
+            if (tid == 0 && nwl) {
+                S.wbase = atomicAdd(counters + C_NTASK + 0, nwl);
+                atomicAdd(counters + C_ETASK + 0, S.nws);
+            }
+            __syncthreads();
             for (uint32_t w = warp; w < nwl; w += NW) {
                 uint32_t e = S.WL[w];
                 uint32_t s0 = e >> 16, sz = e & 0xFFFFu;
-                uint32_t id = 0;
-                uint64_t kk = 0;
-                if (lane < sz) {
-                    id = S.SI[S.SP[s0 + lane]];
-                    kk = load_key(R, id, depth + 8);
+                if (lane < sz) idx[t.begin + s0 + lane] = S.SI[S.SP[s0 + lane]];
+                if (lane == 0) {
+                    uint32_t k = S.wbase + w;
+                    if (k < tiny_cap) tiny[k] = SmallTask{t.begin + s0, sz, depth + 8, t.req, t.parity, 1u};
+                    else set_error(counters, E_SMALL_OVERFLOW, k);
                 }
-                warp_finish(R, sz, depth + 8, id, kk, lbase + s0);
             }
             __syncthreads();
-            if (tid == 0) S.nwl = 0;
+            if (tid == 0) { S.nwl = 0; S.nws = 0; }
             M = M2;
             depth += 8;
-            cur ^= 1;
             __syncthreads();
         }
         // positions that ended as groups of one

@@ -91,9 +91,11 @@ __global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t 
 }
 
 // ------------------------------------------------------ k_setup_big
-// Exclusive prefix sums over the big list: tile_base, cnt_base, bkt_base, scan_base.
+// Exclusive prefix sums over the big list: tile_base, cnt_base, bkt_base,
+// scan_base, from each segment's tree depth as k_build_trees chose it.  The
+// totals of counters and (segment, bucket) pairs go to totals[0..1].
 
-__global__ void __launch_bounds__(1024) k_setup_big(BigSeg *segs, uint32_t nseg) {
+__global__ void __launch_bounds__(1024) k_setup_big(BigSeg *segs, uint32_t nseg, uint32_t *totals) {
     __shared__ uint32_t wsum[4][32];
     __shared__ uint32_t carry[4];
     if (threadIdx.x < 4) carry[threadIdx.x] = 0;
@@ -104,7 +106,7 @@ __global__ void __launch_bounds__(1024) k_setup_big(BigSeg *segs, uint32_t nseg)
         uint32_t v[4] = {0, 0, 0, 0};
         if (i < nseg) {
             BigSeg s = segs[i];
-            uint32_t d = choose_d(s.size);
+            uint32_t d = s.d;
             uint32_t t = tiles_of(s.size);
             uint32_t B = buckets_of(d);
             v[0] = t;
@@ -143,7 +145,6 @@ __global__ void __launch_bounds__(1024) k_setup_big(BigSeg *segs, uint32_t nseg)
         for (int k = 0; k < 4; k++) excl[k] = carry[k] + (warp ? wsum[k][warp - 1] : 0) + incl[k] - v[k];
         if (i < nseg) {
             BigSeg s = segs[i];
-            s.d = choose_d(s.size);
             s.tiles = v[0];
             s.tile_base = excl[0];
             s.cnt_base = excl[1];
@@ -157,6 +158,10 @@ __global__ void __launch_bounds__(1024) k_setup_big(BigSeg *segs, uint32_t nseg)
             for (int k = 0; k < 4; k++) carry[k] += wsum[k][31];
         }
         __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        totals[0] = carry[1];
+        totals[1] = carry[2];
     }
 }
 
@@ -234,14 +239,22 @@ struct TreeSmem {
     PickNode n0[(kMaxV + 1) / 2], n1[(kMaxV + 1) / 2];
 };
 
-__global__ void __launch_bounds__(kThreads) k_build_trees(const BigSeg *segs, const uint64_t *key, uint64_t *splitters) {
+// The sample has alpha * v + alpha - 1 keys (alpha = 2) for the tree size the
+// segment's length allows (choose_d); the tree actually built has just enough
+// levels for the distinct keys of the sample (adaptivity, Section 7): a
+// segment whose sample holds 27 distinct keys gets 31 splitters, not 1023.
+// The chosen depth is stored in the segment record; k_setup_big lays out the
+// counters from it.
+__global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const uint64_t *key, uint64_t *splitters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TreeSmem &S = *reinterpret_cast<TreeSmem *>(smem_raw);
+    __shared__ uint32_t distinct;
     BigSeg sg = segs[blockIdx.x];
-    uint32_t d = sg.d;
-    uint32_t v = (1u << d) - 1;
+    const uint32_t dmax = choose_d(sg.size);
+    uint32_t v = (1u << dmax) - 1;
     uint32_t a = 2 * v + 1;            // alpha * v + alpha - 1 with alpha = 2
     uint32_t P = a + 1;
+    if (threadIdx.x == 0) distinct = 0;
     uint64_t seed = ((uint64_t)sg.begin << 32) ^ (uint64_t)sg.depth * 0x9E3779B97F4A7C15ULL;
     for (uint32_t j = threadIdx.x; j < P; j += blockDim.x) {
         if (j < a) {
@@ -253,6 +266,14 @@ __global__ void __launch_bounds__(kThreads) k_build_trees(const BigSeg *segs, co
     }
     __syncthreads();
     bitonic_u64(S.s, P);
+    uint32_t mine = 0;
+    for (uint32_t j = threadIdx.x; j < a; j += blockDim.x) mine += (j == 0 || S.s[j] != S.s[j - 1]) ? 1u : 0u;
+    for (int o = 16; o > 0; o >>= 1) mine += __shfl_xor_sync(0xffffffffu, mine, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&distinct, mine);
+    __syncthreads();
+    uint32_t d = 1;
+    while (d < dmax && ((1u << d) - 1) < distinct) d++;
+    if (threadIdx.x == 0) segs[blockIdx.x].d = d;
     uint64_t *x = splitters + (size_t)blockIdx.x * kMaxV;
     pick_splitters(S.s, a, d, x, S.n0, S.n1);
 }
@@ -374,9 +395,13 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t x, uint32_t *wsum, 
     return r;
 }
 
-__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t *a, uint32_t n, uint32_t *partial) {
+// The scans read their length n from device memory (the level's counter
+// total is known only on the device); the grid is sized for an upper bound.
+__global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t *a, const uint32_t *n_dev, uint32_t *partial) {
     __shared__ uint32_t wsum[32];
+    const uint32_t n = *n_dev;
     uint32_t base = blockIdx.x * kScanChunk;
+    if (base >= n) return;
     uint32_t s = 0;
 #pragma unroll
     for (int k = 0; k < kScanItems; k++) {
@@ -388,9 +413,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_reduce(const uint32_t *a, uin
     if (threadIdx.x == 0) partial[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partial, uint32_t np) {
+__global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partial, const uint32_t *n_dev) {
     __shared__ uint32_t wsum[32];
     __shared__ uint32_t carry;
+    const uint32_t np = (*n_dev + kScanChunk - 1) / kScanChunk;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -422,8 +448,10 @@ __global__ void __launch_bounds__(1024) k_scan_partials(uint32_t *partial, uint3
 }
 
 // in-place exclusive scan of a chunk plus its partial offset
-__global__ void __launch_bounds__(kThreads) k_scan_down(uint32_t *a, uint32_t n, const uint32_t *partial) {
+__global__ void __launch_bounds__(kThreads) k_scan_down(uint32_t *a, const uint32_t *n_dev, const uint32_t *partial) {
     __shared__ uint32_t wsum[32];
+    const uint32_t n = *n_dev;
+    if (blockIdx.x * kScanChunk >= n) return;
     uint32_t base = blockIdx.x * kScanChunk + threadIdx.x * kScanItems;   // thread-contiguous
     uint32_t v[kScanItems];
     uint32_t s = 0;
@@ -445,9 +473,10 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(uint32_t *a, uint32_t n,
 // ------------------------------------------------------------ k_scatter
 
 struct ScatterSmem {
-    uint32_t wpos[kWarps][kMaxB + 1];   // per warp: count, then running output position
+    uint32_t tbase[kMaxB + 1];          // global position of each bucket's first string from this tile
     uint32_t bstart[kMaxB + 1];         // global start of each bucket
     uint32_t binfo[kMaxB + 1];          // delta | final << 4 | done << 5 | nulpos << 8
+    uint16_t wpos[kWarps][kMaxB + 1];   // per warp: count, then running offset inside the tile's bucket
 };
 
 enum { MODE_SORT = 0, MODE_CLASSIFY = 1 };
@@ -460,6 +489,8 @@ __device__ __forceinline__ uint32_t tile_pos(const BigSeg &sg, const uint32_t *s
 __device__ __forceinline__ uint32_t bucket_start(const BigSeg &sg, const uint32_t *scan, uint32_t b, uint32_t B) {
     return b < B ? tile_pos(sg, scan, b, 0) : sg.begin + sg.size;
 }
+
+constexpr int kScatterBatch = 8;   // placements computed, then gathers in flight, per step
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32_t nseg, const ReqDesc *reqs,
@@ -479,7 +510,8 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
     const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
     const uint64_t *xs = splitters + (size_t)si * kMaxV;
 
-    for (uint32_t k = threadIdx.x; k < kWarps * (kMaxB + 1); k += blockDim.x) (&S.wpos[0][0])[k] = 0;
+    for (uint32_t k = threadIdx.x; k < kWarps * (kMaxB + 1) / 2; k += blockDim.x)
+        reinterpret_cast<uint32_t *>(&S.wpos[0][0])[k] = 0;
     __syncthreads();
     // phase A: per-warp bucket counts of its contiguous span
     for (uint32_t it = 0; it < (uint32_t)kItems; it++) {
@@ -487,19 +519,20 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
         bool ok = p < seg_end;
         uint32_t b = ok ? obuf[p] : 0xFFFFu;
         uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][b] += __popc(peers);
+        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][b] += (uint16_t)__popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // phase B: running positions per (warp, bucket); bucket facts
+    // phase B: each warp's offset inside the tile's part of every bucket; bucket facts
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-        uint32_t pos = tile_pos(sg, scan, b, tl);
+        uint32_t run = 0;
 #pragma unroll
         for (int w = 0; w < kWarps; w++) {
             uint32_t c = S.wpos[w][b];
-            S.wpos[w][b] = pos;
-            pos += c;
+            S.wpos[w][b] = (uint16_t)run;
+            run += c;
         }
+        S.tbase[b] = tile_pos(sg, scan, b, tl);
         if (MODE == MODE_SORT) {
             uint32_t st = bucket_start(sg, scan, b, B);
             uint32_t en = bucket_start(sg, scan, b + 1, B);
@@ -520,33 +553,37 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
     }
     __syncthreads();
     // phase C: stable placement; lanes in order inside the warp, warps in order inside the tile
-    for (uint32_t it = 0; it < (uint32_t)kItems; it += 4) {
-        uint32_t pos[4], id[4], bk[4];
-        bool ok[4];
+    const ReqDesc *Rp = MODE == MODE_SORT ? reqs + sg.req : nullptr;
+    for (uint32_t it = 0; it < (uint32_t)kItems; it += kScatterBatch) {
+        uint32_t pos[kScatterBatch], id[kScatterBatch], bk[kScatterBatch];
+        bool ok[kScatterBatch];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < kScatterBatch; u++) {
             uint32_t p = wbeg + (it + u) * 32 + lane;
             ok[u] = p < seg_end;
             bk[u] = ok[u] ? obuf[p] : 0xFFFFu;
             id[u] = ok[u] ? (MODE == MODE_SORT ? idx_in[p] : p - sg.begin) : 0u;
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterBatch; u++) {
             uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
             uint32_t rank = __popc(peers & lanemask_lt());
-            uint32_t basep = ok[u] ? S.wpos[warp][bk[u]] : 0u;
-            pos[u] = basep + rank;
+            uint32_t off = ok[u] ? S.wpos[warp][bk[u]] : 0u;
+            pos[u] = ok[u] ? S.tbase[bk[u]] + off + rank : 0u;
             __syncwarp();
-            if (ok[u] && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][bk[u]] = basep + __popc(peers);
+            if (ok[u] && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][bk[u]] = (uint16_t)(off + __popc(peers));
             __syncwarp();
         }
         if (MODE == MODE_CLASSIFY) {
 #pragma unroll
-            for (int u = 0; u < 4; u++)
+            for (int u = 0; u < kScatterBatch; u++)
                 if (ok[u]) idx_out[pos[u] - sg.begin] = id[u];
             continue;
         }
-        const ReqDesc &R = reqs[sg.req];
-        uint64_t nk[4];
+        const ReqDesc &R = *Rp;
+        uint64_t nk[kScatterBatch];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < kScatterBatch; u++) {
             nk[u] = 0;
             if (!ok[u]) continue;
             uint32_t info = S.binfo[bk[u]];
@@ -556,7 +593,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
             nk[u] = delta == 0 ? key_in[p] : load_key(R, id[u], sg.depth + delta);
         }
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
+        for (int u = 0; u < kScatterBatch; u++) {
             if (!ok[u]) continue;
             uint32_t info = S.binfo[bk[u]];
             uint32_t q = pos[u];
@@ -575,30 +612,19 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
 
 // ------------------------------------------------------------ k_buckets
 
-__device__ __forceinline__ void push_small(SmallTask *tiny, SmallTask *mid, SmallTask *large, const Caps &caps,
-                                           uint32_t *counters, SmallTask t) {
-    if (t.size <= kTinyMax) {
-        uint32_t k = atomicAdd(counters + C_NTINY, 1u);
-        atomicAdd(counters + C_E_TINY, t.size);
-        if (k < caps.small_tiny) tiny[k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
-    } else if (t.size <= kMidMax) {
-        uint32_t k = atomicAdd(counters + C_NMID, 1u);
-        atomicAdd(counters + C_E_MID, t.size);
-        if (k < caps.small_mid) mid[k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
-    } else {
-        uint32_t k = atomicAdd(counters + C_NLARGE, 1u);
-        atomicAdd(counters + C_E_LARGE, t.size);
-        if (k < caps.small_large) large[k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
-    }
+__device__ __forceinline__ void push_small(const TaskLists &tl, uint32_t *counters, SmallTask t) {
+    const int c = class_of(t.size);
+    uint32_t k = atomicAdd(counters + C_NTASK + c, 1u);
+    atomicAdd(counters + C_ETASK + c, t.size);
+    if (k < tl.cap[c]) tl.l[c][k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
 }
 
-__global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32_t nseg, uint32_t npairs,
+__global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32_t nseg, const uint32_t *npairs_dev,
                                                       const uint32_t *scan, const uint64_t *splitters,
-                                                      uint32_t next_parity, BigSeg *next_big, SmallTask *tiny,
-                                                      SmallTask *mid, SmallTask *large, Boundary *bounds,
-                                                      Caps caps, uint32_t *counters) {
+                                                      uint32_t next_parity, BigSeg *next_big, TaskLists tl,
+                                                      Boundary *bounds, Caps caps, uint32_t *counters) {
     uint32_t pr = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pr >= npairs) return;
+    if (pr >= *npairs_dev) return;
     uint32_t si = find_seg(segs, nseg, pr, [](const BigSeg &s) { return s.bkt_base; });
     BigSeg sg = segs[si];
     uint32_t b = pr - sg.bkt_base;
@@ -638,7 +664,7 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
             set_error(counters, E_BIG_OVERFLOW, k);
         }
     } else {
-        push_small(tiny, mid, large, caps, counters, SmallTask{st, size, depth, sg.req, next_parity});
+        push_small(tl, counters, SmallTask{st, size, depth, sg.req, next_parity, 0});
     }
 }
 
@@ -706,7 +732,8 @@ static cudaError_t ensure_attrs() {
     if ((e = set_smem(k_classify, sizeof(ClassifySmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_SORT>, sizeof(ScatterSmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_CLASSIFY>, sizeof(ScatterSmem)))) return e;
-    if ((e = set_smem(k_base_cta<64, 8>, sizeof(BaseSmem<64, 8>)))) return e;
+    if ((e = set_smem(k_base_cta<32, 8>, sizeof(BaseSmem<32, 8>)))) return e;
+    if ((e = set_smem(k_base_cta<128, 8>, sizeof(BaseSmem<128, 8>)))) return e;
     if ((e = set_smem(k_base_cta<512, 8>, sizeof(BaseSmem<512, 8>)))) return e;
     if (dev < 64) g_attrs_done[dev] = true;
     return cudaSuccess;
@@ -727,11 +754,13 @@ struct Carve {
 
 static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     caps.big = (uint32_t)(N / (kSmallMax + 1) + nreq + 1);
-    caps.small_tiny = (uint32_t)(N / 2 + nreq + 1);
-    caps.small_mid = (uint32_t)(N / (kTinyMax + 1) + nreq + 1);
-    caps.small_large = (uint32_t)(N / (kMidMax + 1) + nreq + 1);
+    for (int c = 0; c < kClasses; c++) {   // disjoint tasks of at least class_max(c - 1) + 1 strings
+        size_t least = c == 0 ? 2 : class_max(c - 1) + 1;
+        caps.small[c] = (uint32_t)(N / least + nreq + 1);
+    }
     caps.bound = (uint32_t)(N + 1);
-    caps.counts = (uint32_t)(N + (size_t)caps.big * 8 + 4096);
+    // sum over big segments of B * tiles <= 2047 (N / kTile + big) + 8 big
+    caps.counts = (uint32_t)std::min<size_t>(0xFFFFFFF0ull, (size_t)kMaxB * ((size_t)N / kTile + caps.big) + (size_t)caps.big * 8 + 4096);
     np = caps.counts / kScanChunk + 2;
     Carve c{nullptr, 0};
     c.take<uint32_t>(N); c.take<uint32_t>(N);
@@ -741,7 +770,7 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     c.take<uint32_t>(np);
     c.take<uint64_t>((size_t)caps.big * kMaxV);
     c.take<BigSeg>(caps.big); c.take<BigSeg>(caps.big);
-    c.take<SmallTask>(caps.small_tiny); c.take<SmallTask>(caps.small_mid); c.take<SmallTask>(caps.small_large);
+    for (int k = 0; k < kClasses; k++) c.take<SmallTask>(caps.small[k]);
     c.take<Boundary>(caps.bound);
     c.take<uint32_t>(C_NUM);
     c.take<ReqDesc>(nreq);
@@ -750,12 +779,13 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
 
 static int check(cudaError_t e, const char *what) { return e == cudaSuccess ? SS_OK : cuda_fail(e, what); }
 
-static int launch_scan(uint32_t *a, uint32_t n, uint32_t *partial, cudaStream_t st) {
-    if (n == 0) return SS_OK;
-    uint32_t nb = (n + kScanChunk - 1) / kScanChunk;
-    SS_LAUNCH_U("scan_reduce", st, n, k_scan_reduce<<<nb, kThreads, 0, st>>>(a, n, partial));
-    SS_LAUNCH_U("scan_partials", st, nb, k_scan_partials<<<1, 1024, 0, st>>>(partial, nb));
-    SS_LAUNCH_U("scan_down", st, n, k_scan_down<<<nb, kThreads, 0, st>>>(a, n, partial));
+// exclusive scan of a[0 .. *n_dev), grid sized for n_bound >= *n_dev
+static int launch_scan(uint32_t *a, uint32_t n_bound, const uint32_t *n_dev, uint32_t *partial, cudaStream_t st) {
+    if (n_bound == 0) return SS_OK;
+    uint32_t nb = (n_bound + kScanChunk - 1) / kScanChunk;
+    SS_LAUNCH_U("scan_reduce", st, n_bound, k_scan_reduce<<<nb, kThreads, 0, st>>>(a, n_dev, partial));
+    SS_LAUNCH_U("scan_partials", st, nb, k_scan_partials<<<1, 1024, 0, st>>>(partial, n_dev));
+    SS_LAUNCH_U("scan_down", st, n_bound, k_scan_down<<<nb, kThreads, 0, st>>>(a, n_dev, partial));
     return check(cudaGetLastError(), "scan launch");
 }
 
@@ -799,9 +829,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     uint32_t *partial = c.take<uint32_t>(np);
     uint64_t *splitters = c.take<uint64_t>((size_t)caps.big * kMaxV);
     BigSeg *big[2] = {c.take<BigSeg>(caps.big), c.take<BigSeg>(caps.big)};
-    SmallTask *tiny = c.take<SmallTask>(caps.small_tiny);
-    SmallTask *mid = c.take<SmallTask>(caps.small_mid);
-    SmallTask *large = c.take<SmallTask>(caps.small_large);
+    TaskLists tl;
+    for (int k = 0; k < kClasses; k++) {
+        tl.l[k] = c.take<SmallTask>(caps.small[k]);
+        tl.cap[k] = caps.small[k];
+    }
     Boundary *bounds = c.take<Boundary>(caps.bound);
     uint32_t *counters = c.take<uint32_t>(C_NUM);
     ReqDesc *dreqs = c.take<ReqDesc>(nreq);
@@ -810,7 +842,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     uint32_t *hc = (uint32_t *)host_staging(sizeof(uint32_t) * C_NUM + 64);
     // initial segments: one per request
     std::vector<BigSeg> big0;
-    std::vector<SmallTask> s_tiny, s_mid, s_large;
+    std::vector<SmallTask> s_task[kClasses];
     uint32_t tiles0 = 0, counts0 = 0, pairs0 = 0;
     for (uint32_t r = 0; r < nreq; r++) {
         const ReqDesc &q = reqs[r];
@@ -822,19 +854,17 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             uint32_t d = choose_d(q.n), t = tiles_of(q.n), B = buckets_of(d);
             tiles0 += t; counts0 += B * t; pairs0 += B;
         } else {
-            SmallTask t{q.base, q.n, 0, r, 0};
-            (q.n <= kTinyMax ? s_tiny : q.n <= kMidMax ? s_mid : s_large).push_back(t);
+            SmallTask t{q.base, q.n, 0, r, 0, 0};
+            s_task[class_of(q.n)].push_back(t);
         }
     }
     uint32_t hcnt[C_NUM] = {0};
     uint32_t elems0 = 0;
     for (auto &s : big0) elems0 += s.size;
-    hcnt[C_NTINY] = (uint32_t)s_tiny.size();
-    hcnt[C_NMID] = (uint32_t)s_mid.size();
-    hcnt[C_NLARGE] = (uint32_t)s_large.size();
-    for (auto &t : s_tiny) hcnt[C_E_TINY] += t.size;
-    for (auto &t : s_mid) hcnt[C_E_MID] += t.size;
-    for (auto &t : s_large) hcnt[C_E_LARGE] += t.size;
+    for (int k = 0; k < kClasses; k++) {
+        hcnt[C_NTASK + k] = (uint32_t)s_task[k].size();
+        for (auto &t : s_task[k]) hcnt[C_ETASK + k] += t.size;
+    }
 #define TRY(x, what)                                     \
     do {                                                 \
         cudaError_t _e = (x);                            \
@@ -843,9 +873,10 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     TRY(cudaMemcpyAsync(dreqs, reqs.data(), sizeof(ReqDesc) * nreq, cudaMemcpyHostToDevice, st), "copy requests");
     TRY(cudaMemcpyAsync(counters, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, st), "copy counters");
     if (!big0.empty()) TRY(cudaMemcpyAsync(big[0], big0.data(), sizeof(BigSeg) * big0.size(), cudaMemcpyHostToDevice, st), "copy big");
-    if (!s_tiny.empty()) TRY(cudaMemcpyAsync(tiny, s_tiny.data(), sizeof(SmallTask) * s_tiny.size(), cudaMemcpyHostToDevice, st), "copy tiny");
-    if (!s_mid.empty()) TRY(cudaMemcpyAsync(mid, s_mid.data(), sizeof(SmallTask) * s_mid.size(), cudaMemcpyHostToDevice, st), "copy mid");
-    if (!s_large.empty()) TRY(cudaMemcpyAsync(large, s_large.data(), sizeof(SmallTask) * s_large.size(), cudaMemcpyHostToDevice, st), "copy large");
+    for (int k = 0; k < kClasses; k++)
+        if (!s_task[k].empty())
+            TRY(cudaMemcpyAsync(tl.l[k], s_task[k].data(), sizeof(SmallTask) * s_task[k].size(), cudaMemcpyHostToDevice, st),
+                "copy base-case tasks");
     {
         uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
         SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], key[0]));
@@ -863,18 +894,19 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
                 goto done;
             }
             uint32_t nxt = cur ^ 1;
-            SS_LAUNCH_U("setup_big", st, nbig, k_setup_big<<<1, 1024, 0, st>>>(big[cur], nbig));
+            // trees first: each chooses its depth; then the counter layout follows
             SS_LAUNCH_U("build_trees", st, nbig, k_build_trees<<<nbig, kThreads, sizeof(TreeSmem), st>>>(big[cur], key[cur], splitters));
+            SS_LAUNCH_U("setup_big", st, nbig, k_setup_big<<<1, 1024, 0, st>>>(big[cur], nbig, counters + C_LVL_COUNTS));
             SS_LAUNCH_U("classify", st, nelems, k_classify<<<ntiles, kThreads, sizeof(ClassifySmem), st>>>(big[cur], nbig, key[cur], splitters, obuf, counts));
             TRY(cudaGetLastError(), "classify launch");
-            if ((rc = launch_scan(counts, ncounts, partial, st)) != SS_OK) goto done;
+            if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) goto done;
             SS_LAUNCH_U("scatter", st, nelems, k_scatter<MODE_SORT><<<ntiles, kThreads, sizeof(ScatterSmem), st>>>(
                 big[cur], nbig, dreqs, idx[cur], key[cur], obuf, counts, splitters, idx[nxt], key[nxt], counters));
             TRY(cudaMemsetAsync(counters + C_NBIG, 0, sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_TILES, 0, 3 * sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_ELEMS, 0, sizeof(uint32_t), st), "reset");
             SS_LAUNCH_U("buckets", st, npairs, k_buckets<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(
-                big[cur], nbig, npairs, counts, splitters, nxt, big[nxt], tiny, mid, large, bounds, caps, counters));
+                big[cur], nbig, counters + C_LVL_PAIRS, counts, splitters, nxt, big[nxt], tl, bounds, caps, counters));
             TRY(cudaGetLastError(), "level launch");
             TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
             TRY(cudaStreamSynchronize(st), "level sync");
@@ -895,19 +927,29 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             rc = SS_ERR_INTERNAL;
             goto done;
         }
-        uint32_t ntiny = hc[C_NTINY], nmid = hc[C_NMID], nlarge = hc[C_NLARGE], nb = hc[C_NBOUND];
+        uint32_t nb = hc[C_NBOUND];
         uint32_t sms = (uint32_t)sm_count();
-        if (ntiny) {
-            uint32_t grid = std::min<uint32_t>((ntiny + kWarps - 1) / kWarps, sms * 8);
-            SS_LAUNCH_U("small_warp", st, hc[C_E_TINY], k_small_warp<<<grid, kThreads, 0, st>>>(tiny, ntiny, dreqs, idx[0], key[0], idx[1], key[1]));
+        // CTA base cases first: they append their small equal-key groups to the
+        // class-0 list, which the warp kernel then drains (count read on the device)
+        SmallTask *const *L = tl.l;
+        if (uint32_t n1 = hc[C_NTASK + 1]) {
+            uint32_t grid = std::min<uint32_t>(n1, sms * 32);
+            SS_LAUNCH_U("small_cta256", st, hc[C_ETASK + 1], (k_base_cta<32, 8><<<grid, 32, sizeof(BaseSmem<32, 8>), st>>>(
+                L[1], n1, dreqs, idx[0], key[0], idx[1], key[1], L[0], tl.cap[0], counters)));
         }
-        if (nmid) {
-            uint32_t grid = std::min<uint32_t>(nmid, sms * 16);
-            SS_LAUNCH_U("small_cta512", st, hc[C_E_MID], (k_base_cta<64, 8><<<grid, 64, sizeof(BaseSmem<64, 8>), st>>>(mid, nmid, dreqs, idx[0], key[0], idx[1], key[1])));
+        if (uint32_t n2 = hc[C_NTASK + 2]) {
+            uint32_t grid = std::min<uint32_t>(n2, sms * 8);
+            SS_LAUNCH_U("small_cta1024", st, hc[C_ETASK + 2], (k_base_cta<128, 8><<<grid, 128, sizeof(BaseSmem<128, 8>), st>>>(
+                L[2], n2, dreqs, idx[0], key[0], idx[1], key[1], L[0], tl.cap[0], counters)));
         }
-        if (nlarge) {
-            uint32_t grid = std::min<uint32_t>(nlarge, sms * 2);
-            SS_LAUNCH_U("small_cta4096", st, hc[C_E_LARGE], (k_base_cta<512, 8><<<grid, 512, sizeof(BaseSmem<512, 8>), st>>>(large, nlarge, dreqs, idx[0], key[0], idx[1], key[1])));
+        if (uint32_t n3 = hc[C_NTASK + 3]) {
+            uint32_t grid = std::min<uint32_t>(n3, sms * 2);
+            SS_LAUNCH_U("small_cta4096", st, hc[C_ETASK + 3], (k_base_cta<512, 8><<<grid, 512, sizeof(BaseSmem<512, 8>), st>>>(
+                L[3], n3, dreqs, idx[0], key[0], idx[1], key[1], L[0], tl.cap[0], counters)));
+        }
+        if (hc[C_NTASK + 0] || hc[C_NTASK + 1] || hc[C_NTASK + 2] || hc[C_NTASK + 3]) {
+            uint32_t grid = sms * 8;
+            SS_LAUNCH_U("small_warp", st, hc[C_ETASK + 0], k_small_warp<<<grid, kThreads, 0, st>>>(L[0], counters + C_NTASK + 0, dreqs, idx[0], key[0], idx[1], key[1]));
         }
         TRY(cudaGetLastError(), "base case launch");
         if (nb) {
@@ -917,7 +959,13 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         }
         SS_LAUNCH("status", st, k_status<<<(nreq + 255) / 256, 256, 0, st>>>(dreqs, nreq, 0));
         TRY(cudaGetLastError(), "status launch");
+        TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
         TRY(cudaStreamSynchronize(st), "final sync");
+        if (hc[C_ERROR]) {
+            set_error_detail("device-side check failed in the base case: code %u info %u", hc[C_ERROR], hc[C_ERRINFO]);
+            rc = SS_ERR_INTERNAL;
+            goto done;
+        }
     }
 done:
 #undef TRY
@@ -951,14 +999,17 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
     s.begin = 0; s.size = n; s.depth = 0; s.req = 0; s.d = d; s.tiles = tiles;
     s.tile_base = 0; s.cnt_base = 0; s.bkt_base = 0; s.scan_base = 0;
     int rc = SS_OK;
+    uint32_t hcnt[C_NUM] = {0};
+    hcnt[C_LVL_COUNTS] = ncounts;
+    hcnt[C_LVL_PAIRS] = B;
     do {
         if ((e = cudaMemcpyAsync(seg, &s, sizeof(s), cudaMemcpyHostToDevice, st))) break;
         if ((e = cudaMemcpyAsync(spl, x, sizeof(uint64_t) * v, cudaMemcpyDeviceToDevice, st))) break;
-        if ((e = cudaMemsetAsync(counters, 0, sizeof(uint32_t) * C_NUM, st))) break;
+        if ((e = cudaMemcpyAsync(counters, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, st))) break;
         if (n) {
             SS_LAUNCH("classify", st, k_classify<<<tiles, kThreads, sizeof(ClassifySmem), st>>>(seg, 1, keys, spl, bucket_out, counts));
             if ((e = cudaGetLastError())) break;
-            if ((rc = launch_scan(counts, ncounts, partial, st)) != SS_OK) break;
+            if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) break;
             SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY><<<tiles, kThreads, sizeof(ScatterSmem), st>>>(
                 seg, 1, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, counters));
             if ((e = cudaGetLastError())) break;

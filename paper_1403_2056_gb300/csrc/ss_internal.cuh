@@ -20,15 +20,23 @@ namespace ss {
 // ---------------------------------------------------------------- tunables
 constexpr int kThreads = 256;                  // CTA size of the tile kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 32;                     // elements per thread in a tile
-constexpr int kTile = kThreads * kItems;       // 8192 elements per tile
-constexpr int kWarpSpan = kTile / kWarps;      // 1024 contiguous elements per warp
+constexpr int kItems = 16;                     // elements per thread in a tile
+constexpr int kTile = kThreads * kItems;       // 4096 elements per tile
+constexpr int kWarpSpan = kTile / kWarps;      // 512 contiguous elements per warp
 constexpr int kMaxD = 10;                      // tree depth: v = 2^d - 1 <= 1023
 constexpr int kMaxV = (1 << kMaxD) - 1;
 constexpr int kMaxB = 2 * kMaxV + 1;           // 2047 buckets
 constexpr uint32_t kSmallMax = 4096;           // segments up to this size are base cases
 constexpr uint32_t kTinyMax = 32;              // base cases handled by one warp
-constexpr uint32_t kMidMax = 512;              // base cases handled by a 512-capacity CTA
+// base-case size classes: class 0 (2..32 strings) one warp; classes 1..3 one
+// CTA of 32, 128, 512 threads holding up to 256, 1024, 4096 strings
+constexpr int kClasses = 4;
+__host__ __device__ __forceinline__ uint32_t class_max(int c) {
+    return c == 0 ? 32u : c == 1 ? 256u : c == 2 ? 1024u : kSmallMax;
+}
+__host__ __device__ __forceinline__ int class_of(uint32_t size) {
+    return size <= 32u ? 0 : size <= 256u ? 1 : size <= 1024u ? 2 : 3;
+}
 
 // ------------------------------------------------------------ descriptors
 struct ReqDesc {
@@ -52,7 +60,9 @@ struct BigSeg {                 // a segment sorted by one multi-CTA S5 step
 };
 
 struct SmallTask {              // a base-case segment
-    uint32_t begin, size, depth, req, parity;
+    uint32_t begin, size, depth, req;
+    uint32_t parity;            // which idx/key buffer holds it
+    uint32_t gather;            // 1: the key buffer is stale, gather keys at `depth`
 };
 
 struct Boundary {               // lcp at global position pos is depth + lcp8(keys at depth)
@@ -62,20 +72,23 @@ struct Boundary {               // lcp at global position pos is depth + lcp8(ke
 // device counters (one block of u32 per sort)
 enum Counter : int {
     C_NBIG = 0,       // big segments emitted for the next level
-    C_NTINY = 1,      // small tasks by class
-    C_NMID = 2,
-    C_NLARGE = 3,
-    C_NBOUND = 4,     // boundary records
-    C_ERROR = 5,      // first device-side error code (0 = none)
-    C_TILES = 6,      // tiles of the next level's big segments
-    C_COUNTS = 7,     // counters of the next level
-    C_PAIRS = 8,      // (segment, bucket) pairs of the next level
-    C_ERRINFO = 9,
-    C_ELEMS = 10,     // strings in the next level's big segments
-    C_E_TINY = 11,    // strings in small tasks by class
-    C_E_MID = 12,
-    C_E_LARGE = 13,
-    C_NUM = 16
+    C_NBOUND = 1,     // boundary records
+    C_ERROR = 2,      // first device-side error code (0 = none)
+    C_TILES = 3,      // tiles of the next level's big segments
+    C_COUNTS = 4,     // counters of the next level
+    C_PAIRS = 5,      // (segment, bucket) pairs of the next level
+    C_ERRINFO = 6,
+    C_ELEMS = 7,      // strings in the next level's big segments
+    C_LVL_COUNTS = 8, // counters of the current level (k_setup_big)
+    C_LVL_PAIRS = 9,  // (segment, bucket) pairs of the current level
+    C_NTASK = 10,     // base-case tasks of class c at C_NTASK + c
+    C_ETASK = 14,     // their strings at C_ETASK + c
+    C_NUM = 24
+};
+
+struct TaskLists {              // base-case task lists by size class
+    SmallTask *l[kClasses];
+    uint32_t cap[kClasses];
 };
 
 enum DevError : uint32_t {
@@ -88,7 +101,8 @@ enum DevError : uint32_t {
 };
 
 struct Caps {                   // capacities of the scratch lists
-    uint32_t big, small_tiny, small_mid, small_large, bound, counts;
+    uint32_t big, bound, counts;
+    uint32_t small[kClasses];
 };
 
 // ------------------------------------------------------------ device math
@@ -158,6 +172,61 @@ __device__ __forceinline__ uint64_t load_key(const ReqDesc &R, uint32_t i, uint3
         key &= k ? (~0ULL << (64 - 8 * k)) : 0ULL;
     }
     return key;
+}
+
+// keep the bytes of a big-endian key before byte k (k in 0..8)
+__device__ __forceinline__ uint64_t keep_bytes(uint64_t key, uint32_t k) {
+    return k >= 8 ? key : (k ? key & (~0ULL << (64 - 8 * k)) : 0ULL);
+}
+
+// chars_h for 16 characters: k0 = bytes [h, h+8), k1 = [h+8, h+16), zero past
+// the end.  Each further aligned word is read only when the string continues
+// into it, so no read leaves the string and its terminator.
+__device__ __forceinline__ void load_key2(const ReqDesc &R, uint32_t i, uint32_t h, uint64_t &k0, uint64_t &k1) {
+    uint64_t off = __ldg(R.offsets + i);
+    uint64_t rem = ~0ULL;
+    if (R.lengths) {
+        uint32_t len = __ldg(R.lengths + i);
+        if (h >= len) { k0 = 0; k1 = 0; return; }
+        rem = len - h;
+    } else if (R.fixed_len) {
+        if (h >= R.fixed_len) { k0 = 0; k1 = 0; return; }
+        rem = R.fixed_len - h;
+    }
+    const uint8_t *p = R.chars + off + h;
+    uintptr_t a = (uintptr_t)p;
+    const uint64_t *w = (const uint64_t *)(a & ~(uintptr_t)7);
+    const uint32_t sh = (uint32_t)(a & 7) * 8;
+    const uint64_t avail0 = 8 - (a & 7);   // bytes of the string's window in the first word
+    uint64_t w0 = __ldg(w);
+    bool more1, more2;
+    uint64_t w1 = 0, w2 = 0;
+    if (rem == ~0ULL) {
+        more1 = !has_zero((w0 >> sh) | (sh ? (~0ULL << (64 - sh)) : 0ULL));
+        if (more1) w1 = __ldg(w + 1);
+        more2 = more1 && sh && !has_zero(w1);
+    } else {
+        more1 = rem > avail0;
+        if (more1) w1 = __ldg(w + 1);
+        more2 = sh && rem > avail0 + 8;
+    }
+    if (more2) w2 = __ldg(w + 2);
+    uint64_t v0 = sh ? ((w0 >> sh) | (w1 << (64 - sh))) : w0;
+    uint64_t v1 = sh ? ((w1 >> sh) | (w2 << (64 - sh))) : w1;
+    k0 = bswap64(v0);
+    k1 = bswap64(v1);
+    if (rem < 16) {
+        if (rem < 8) { k0 = keep_bytes(k0, (uint32_t)rem); k1 = 0; }
+        else k1 = keep_bytes(k1, (uint32_t)(rem - 8));
+    }
+    uint64_t z0 = zero_bytes(k0);
+    if (z0) {
+        k0 = keep_bytes(k0, (uint32_t)(__clzll(z0) >> 3));
+        k1 = 0;
+    } else {
+        uint64_t z1 = zero_bytes(k1);
+        if (z1) k1 = keep_bytes(k1, (uint32_t)(__clzll(z1) >> 3));
+    }
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finaliser

@@ -23,23 +23,111 @@
 
 namespace ss {
 
-constexpr uint32_t kMergeItems = 64;
+constexpr uint32_t kMergeItems = 16;   // outputs per thread
+constexpr uint32_t kCoarse = 256;      // outputs per merge-path window
 
-// full comparison of strings a and b from depth h on (both share h characters);
-// returns -1/0/+1 and the lcp in *l
+// full comparison of strings a and b from depth h on (both share h characters),
+// 16 characters per round; returns -1/0/+1 and the lcp in *l
 __device__ __forceinline__ int str_cmp_from(const ReqDesc &S, uint32_t a, uint32_t b, uint32_t h, uint32_t *l) {
     for (;;) {
-        uint64_t ka = load_key(S, a, h), kb = load_key(S, b, h);
-        if (ka != kb) {
-            *l = h + lcp8(ka, kb);
-            return ka < kb ? -1 : 1;
-        }
-        if (has_zero(ka)) {
-            *l = h + nulpos(ka);
-            return 0;
-        }
-        h += 8;
+        uint64_t a0, a1, b0, b1;
+        load_key2(S, a, h, a0, a1);
+        load_key2(S, b, h, b0, b1);
+        if (a0 != b0) { *l = h + lcp8(a0, b0); return a0 < b0 ? -1 : 1; }
+        if (has_zero(a0)) { *l = h + nulpos(a0); return 0; }
+        if (a1 != b1) { *l = h + 8 + lcp8(a1, b1); return a1 < b1 ? -1 : 1; }
+        if (has_zero(a1)) { *l = h + 8 + nulpos(a1); return 0; }
+        h += 16;
     }
+}
+
+// pair (2p, 2p+1) of the round's runs; an unpaired last run has B empty
+struct PairView {
+    uint32_t a0, na, nb, baseA, baseB;
+    const uint32_t *Ap, *Bp, *HA, *HB;
+    __device__ __forceinline__ uint32_t A(uint32_t k) const { return Ap[k] + baseA; }
+    __device__ __forceinline__ uint32_t B(uint32_t k) const { return Bp[k] + baseB; }
+};
+
+__device__ __forceinline__ PairView pair_view(uint32_t p, const uint32_t *in_perm, const uint32_t *in_lcp,
+                                              const uint32_t *rb, uint32_t R, const uint32_t *rbase) {
+    PairView v;
+    uint32_t a1 = rb[2 * p + 1];
+    uint32_t b1 = (2 * p + 1 < R) ? rb[2 * p + 2] : a1;
+    v.a0 = rb[2 * p];
+    v.na = a1 - v.a0;
+    v.nb = b1 - a1;
+    v.Ap = in_perm + v.a0;
+    v.Bp = in_perm + a1;
+    v.HA = in_lcp + v.a0;
+    v.HB = in_lcp + a1;
+    // string index of a run entry: entry + the run's index base (first round only)
+    v.baseA = rbase ? rbase[2 * p] : 0u;
+    v.baseB = (rbase && 2 * p + 1 < R) ? rbase[2 * p + 1] : 0u;
+    return v;
+}
+
+// merge path: number of strings taken from A among the first diag outputs
+// (A first on ties), searched in [lo, hi); all compared strings share h characters
+__device__ __forceinline__ uint32_t path_search(const ReqDesc &S, const PairView &v, uint32_t diag, uint32_t lo,
+                                                uint32_t hi, uint32_t h) {
+    while (lo < hi) {
+        uint32_t mid = (lo + hi) / 2;
+        uint32_t l;
+        if (str_cmp_from(S, v.A(mid), v.B(diag - 1 - mid), h, &l) <= 0) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+struct Coarse {
+    uint32_t i;   // strings from A among the outputs before this window's first output
+    uint32_t h;   // characters shared by every string of the window
+};
+
+__device__ __forceinline__ uint32_t pair_of_entry(const uint32_t *cbase, uint32_t npairs, uint32_t e) {
+    uint32_t lo = 0, hi = npairs;   // last pair with cbase[p] <= e
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) / 2;
+        if (cbase[mid] <= e) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// window cuts: pair p has entries cbase[p] + k for diagonals min(k kCoarse, na + nb)
+__global__ void k_merge_cuts(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb,
+                             uint32_t R, const uint32_t *rbase, const uint32_t *cbase, uint32_t npairs,
+                             uint32_t nentries, Coarse *C) {
+    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nentries) return;
+    uint32_t p = pair_of_entry(cbase, npairs, e);
+    PairView v = pair_view(p, in_perm, in_lcp, rb, R, rbase);
+    uint32_t len = v.na + v.nb;
+    uint32_t diag = min((e - cbase[p]) * kCoarse, len);
+    uint32_t lo = diag > v.nb ? diag - v.nb : 0, hi = min(diag, v.na);
+    C[e].i = path_search(S, v, diag, lo, hi, 0);
+}
+
+// characters shared by a whole window: the strings of a window are a
+// contiguous run of the merged order, so they share min(lcp(A_i0, A_i1-1),
+// lcp(B_j0, B_j1-1), lcp(A_i0, B_j0)) characters
+__global__ void k_merge_windows(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb,
+                                uint32_t R, const uint32_t *rbase, const uint32_t *cbase, uint32_t npairs,
+                                uint32_t nentries, Coarse *C) {
+    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nentries) return;
+    uint32_t p = pair_of_entry(cbase, npairs, e);
+    uint32_t last = (p + 1 < npairs ? cbase[p + 1] : nentries) - 1;
+    if (e == last) { C[e].h = 0; return; }
+    PairView v = pair_view(p, in_perm, in_lcp, rb, R, rbase);
+    uint32_t len = v.na + v.nb;
+    uint32_t k = e - cbase[p];
+    uint32_t d0 = min(k * kCoarse, len), d1 = min((k + 1) * kCoarse, len);
+    uint32_t i0 = C[e].i, i1 = C[e + 1].i, j0 = d0 - i0, j1 = d1 - i1;
+    uint32_t h = 0xFFFFFFFFu, l;
+    if (i1 > i0) { str_cmp_from(S, v.A(i0), v.A(i1 - 1), 0, &l); h = min(h, l); }
+    if (j1 > j0) { str_cmp_from(S, v.B(j0), v.B(j1 - 1), 0, &l); h = min(h, l); }
+    if (i1 > i0 && j1 > j0) { str_cmp_from(S, v.A(i0), v.B(j0), 0, &l); h = min(h, l); }
+    C[e].h = h == 0xFFFFFFFFu ? 0u : h;
 }
 
 __device__ __forceinline__ uint32_t upper_run(const uint32_t *rb, uint32_t R, uint32_t o) {
@@ -52,9 +140,13 @@ __device__ __forceinline__ uint32_t upper_run(const uint32_t *rb, uint32_t R, ui
 }
 
 // One round: pair (2p, 2p+1) of the R runs rb[0..R] is merged into the same
-// output positions; an unpaired last run is copied.
+// output positions; an unpaired last run is copied.  With a window table
+// (C, cbase) each thread's merge path search stays inside its window and
+// compares from the window's shared prefix; without one (C == NULL) it
+// searches the whole pair from depth 0.
 __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R,
-                              const uint32_t *rbase, uint32_t total, uint32_t *out_perm, uint32_t *out_lcp) {
+                              const uint32_t *rbase, uint32_t total, uint32_t *out_perm, uint32_t *out_lcp,
+                              const Coarse *C, const uint32_t *cbase) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t o64 = (uint64_t)t * kMergeItems;
     if (o64 >= total) return;
@@ -63,27 +155,43 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
     while (o < end) {
         uint32_t r = upper_run(rb, R, o);
         uint32_t p = r / 2;
-        uint32_t a0 = rb[2 * p], a1 = rb[2 * p + 1];
-        uint32_t b1 = (2 * p + 1 < R) ? rb[2 * p + 2] : a1;   // unpaired last run: B empty
-        const uint32_t na = a1 - a0, nb = b1 - a1;
-        const uint32_t *Araw = in_perm + a0, *Braw = in_perm + a1;
-        const uint32_t *HA = in_lcp + a0, *HB = in_lcp + a1;
-        // string index of a run entry: entry + the run's index base (first round only)
-        const uint32_t baseA = rbase ? rbase[2 * p] : 0u;
-        const uint32_t baseB = (rbase && 2 * p + 1 < R) ? rbase[2 * p + 1] : 0u;
-        auto A = [&](uint32_t k) { return Araw[k] + baseA; };
-        auto B = [&](uint32_t k) { return Braw[k] + baseB; };
+        const PairView v = pair_view(p, in_perm, in_lcp, rb, R, rbase);
+        const uint32_t a0 = v.a0, na = v.na, nb = v.nb;
+        const uint32_t *HA = v.HA, *HB = v.HB;
+        auto A = [&](uint32_t k) { return v.A(k); };
+        auto B = [&](uint32_t k) { return v.B(k); };
         const uint32_t pair_end = a0 + na + nb;
         const uint32_t stop = min(end, pair_end);
         uint32_t diag = o - a0;
-        // merge path: i = strings taken from A among the first diag outputs (A first on ties)
         uint32_t lo = diag > nb ? diag - nb : 0, hi = min(diag, na);
-        while (lo < hi) {
-            uint32_t mid = (lo + hi) / 2;
-            uint32_t l;
-            if (str_cmp_from(S, A(mid), B(diag - 1 - mid), 0, &l) <= 0) lo = mid + 1; else hi = mid;
+        // window of the diagonal: strings A[i0, i1) and B[j0, j1) share hw characters
+        uint32_t i0 = 0, i1 = na, j0 = 0, j1 = nb, hw = 0;
+        bool win = C != nullptr;
+        uint32_t i;
+        if (win) {
+            uint32_t k = diag / kCoarse;
+            uint32_t e = cbase[p] + k;
+            uint32_t d0 = k * kCoarse;
+            i0 = C[e].i;
+            j0 = d0 - i0;
+            if (d0 == diag) {
+                i = i0;
+                win = false;   // exact cut: no search, no shared prefix needed
+            } else {
+                uint32_t d1 = min(d0 + kCoarse, na + nb);
+                i1 = C[e + 1].i;
+                j1 = d1 - i1;
+                hw = C[e].h;
+                lo = max(lo, max(i0, diag > j1 ? diag - j1 : 0u));
+                hi = min(hi, min(i1, diag - j0));
+                i = path_search(S, v, diag, lo, hi, hw);
+            }
+        } else {
+            i = path_search(S, v, diag, lo, hi, 0);
         }
-        uint32_t i = lo, j = diag - lo;
+        uint32_t j = diag - i;
+        auto inA = [&](uint32_t x) { return win && x >= i0 && x < i1; };
+        auto inB = [&](uint32_t y) { return win && y >= j0 && y < j1; };
         // LCPs of both fronts with the last string written before position o
         uint32_t ha = 0, hb = 0;
         if (diag > 0) {
@@ -92,16 +200,18 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
             else if (j == 0) last_is_b = false;
             else {
                 uint32_t l;
-                last_is_b = str_cmp_from(S, A(i - 1), B(j - 1), 0, &l) <= 0;   // ties: A then B
+                uint32_t h0 = (inA(i - 1) && inB(j - 1)) ? hw : 0u;
+                last_is_b = str_cmp_from(S, A(i - 1), B(j - 1), h0, &l) <= 0;   // ties: A then B
             }
             uint32_t prev = last_is_b ? B(j - 1) : A(i - 1);
+            bool prev_in = last_is_b ? inB(j - 1) : inA(i - 1);
             if (i < na) {
                 if (!last_is_b) ha = HA[i];
-                else { uint32_t l; str_cmp_from(S, prev, A(i), 0, &l); ha = l; }
+                else { uint32_t l; str_cmp_from(S, prev, A(i), (prev_in && inA(i)) ? hw : 0u, &l); ha = l; }
             }
             if (j < nb) {
                 if (last_is_b) hb = HB[j];
-                else { uint32_t l; str_cmp_from(S, prev, B(j), 0, &l); hb = l; }
+                else { uint32_t l; str_cmp_from(S, prev, B(j), (prev_in && inB(j)) ? hw : 0u, &l); hb = l; }
             }
         }
         // binary LCP-merge (Algorithm 3) over positions [o, stop)
@@ -160,7 +270,10 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
     uint32_t R = (uint32_t)rb.size() - 1;
     size_t rounds = 0;
     for (uint32_t r = R; r > 1; r = (r + 1) / 2) rounds++;
-    size_t bytes = 2ull * 4 * total + 8ull * (K + 2) + 2048;
+    // window table: at most total / kCoarse + 2 entries per pair
+    const size_t max_entries = (size_t)total / kCoarse + 2ull * (K + 1) + 2;
+    const size_t a64 = 63;
+    size_t bytes = 2ull * 4 * (((size_t)total + a64) & ~a64) + 4ull * (4 * (K + 2) + 64) + sizeof(Coarse) * max_entries + 4096;
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
     if (e) {
@@ -169,11 +282,11 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
         return SS_ERR_OOM;
     }
     uint32_t *tmp_perm = (uint32_t *)block;
-    uint32_t *tmp_lcp = tmp_perm + (((size_t)total + 63) & ~(size_t)63);
-    uint32_t *d_rb = tmp_lcp + (((size_t)total + 63) & ~(size_t)63);
-    uint32_t *d_base = d_rb + ((K + 2 + 63) & ~63u);
+    uint32_t *tmp_lcp = tmp_perm + (((size_t)total + a64) & ~a64);
+    uint32_t *d_rb = tmp_lcp + (((size_t)total + a64) & ~a64);   // rb[R+1], bases[R], cbase[pairs]
+    Coarse *d_coarse = (Coarse *)(d_rb + ((4 * (K + 2) + 63) & ~63u));
     int rc = SS_OK;
-    uint32_t *stage = (uint32_t *)host_staging(sizeof(uint32_t) * 2 * (K + 2));
+    uint32_t *stage = (uint32_t *)host_staging(sizeof(uint32_t) * 4 * (K + 2));
     do {
         if (R <= 1) {
             uint32_t base = rbase.empty() ? 0u : rbase[0];
@@ -192,14 +305,28 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             bool last = round == rounds;
             uint32_t *dst_p = last ? perm_out : ((rounds - round) % 2 ? tmp_perm : perm_out);
             uint32_t *dst_l = last ? lcp_out : ((rounds - round) % 2 ? tmp_lcp : lcp_out);
+            // staging: rb[R+1], bases[R] (first round), cbase[pairs]
+            const uint32_t npairs = (R + 1) / 2;
             memcpy(stage, rb.data(), sizeof(uint32_t) * (R + 1));
             if (round == 1) memcpy(stage + (R + 1), rbase.data(), sizeof(uint32_t) * R);
-            size_t cp = sizeof(uint32_t) * ((R + 1) + (round == 1 ? R : 0));
+            uint32_t *cb = stage + (2 * R + 1);
+            uint32_t nentries = 0;
+            for (uint32_t p = 0; p < npairs; p++) {
+                uint32_t len = rb[std::min(2 * p + 2, R)] - rb[2 * p];
+                cb[p] = nentries;
+                nentries += (len + kCoarse - 1) / kCoarse + 1;
+            }
+            size_t cp = sizeof(uint32_t) * (2 * R + 1 + npairs);
             if ((e = cudaMemcpyAsync(d_rb, stage, cp, cudaMemcpyHostToDevice, st))) break;
             const uint32_t *bases = round == 1 ? d_rb + (R + 1) : nullptr;
+            const uint32_t *d_cb = d_rb + (2 * R + 1);
+            SS_LAUNCH_U("merge_cuts", st, nentries, k_merge_cuts<<<(nentries + 127) / 128, 128, 0, st>>>(
+                set, src_p, src_l, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
+            SS_LAUNCH_U("merge_windows", st, nentries, k_merge_windows<<<(nentries + 127) / 128, 128, 0, st>>>(
+                set, src_p, src_l, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
             uint32_t threads = (total + kMergeItems - 1) / kMergeItems;
             SS_LAUNCH_U("merge_round", st, total, k_merge_round<<<(threads + 255) / 256, 256, 0, st>>>(
-                set, src_p, src_l, d_rb, R, bases, total, dst_p, dst_l));
+                set, src_p, src_l, d_rb, R, bases, total, dst_p, dst_l, d_coarse, d_cb));
             if ((e = cudaGetLastError())) break;
             // the staging buffer is reused next round: wait for the copy
             if ((e = cudaStreamSynchronize(st))) break;
@@ -318,7 +445,7 @@ static int merge_runs_noalloc(const ReqDesc &set, const uint32_t *run_perm, cons
         SS_LAUNCH("store_run_table", st, k_store_run_table<<<1, 128, 0, st>>>(t, R, d_table));
         uint32_t threads = (total + kMergeItems - 1) / kMergeItems;
         SS_LAUNCH_U("merge_round", st, total, k_merge_round<<<(threads + 255) / 256, 256, 0, st>>>(
-            set, src_p, src_l, d_table, R, d_table + kNoAllocMaxRuns + 1, total, dst_p, dst_l));
+            set, src_p, src_l, d_table, R, d_table + kNoAllocMaxRuns + 1, total, dst_p, dst_l, nullptr, nullptr));
         if ((e = cudaGetLastError())) return cuda_fail(e, "ss_merge_noalloc");
         RunTable nt;
         memset(&nt, 0, sizeof(nt));
