@@ -45,7 +45,8 @@ BYTES_PER_UNIT = {
     "small_cta1024": 4 + 8 + 4 + 4,
     "small_cta4096": 4 + 8 + 4 + 4,
     "boundary": 4 + 4 + 8 + 8 + 4,   # two perm reads, two key gathers, lcp write
-    "merge_round": 4 + 4 + 4 + 4,    # perm + lcp read, perm + lcp write
+    "merge_round": 4 + 4 + 8 + 4 + 4 + 8,   # perm + lcp + offset read, perm + lcp + offset write
+    "run_prep": 4 + 4 + 8 + 8 + 8,   # perm + lcp read, offset gather, offset + cached-key write
     "copy_run": 16,
     "scan_reduce": 4,
     "scan_down": 8,

@@ -26,6 +26,7 @@ namespace ss {
 struct WElem {
     uint32_t g;    // group id: first lane of its group (0xFFFFFFFF: padding)
     uint32_t i;    // string index
+    uint64_t o;    // byte offset of the string
     uint64_t k0;   // characters [depth, depth + 8)
     uint64_t k1;   // characters [depth + 8, depth + 16)
 };
@@ -41,6 +42,7 @@ __device__ __forceinline__ WElem shfl_xor_welem(const WElem &e, int m) {
     WElem r;
     r.g = __shfl_xor_sync(0xffffffffu, e.g, m);
     r.i = __shfl_xor_sync(0xffffffffu, e.i, m);
+    r.o = __shfl_xor_sync(0xffffffffu, e.o, m);
     r.k0 = __shfl_xor_sync(0xffffffffu, e.k0, m);
     r.k1 = __shfl_xor_sync(0xffffffffu, e.k1, m);
     return r;
@@ -48,14 +50,15 @@ __device__ __forceinline__ WElem shfl_xor_welem(const WElem &e, int m) {
 
 // Sort one group of m <= 32 strings completely with one warp (all 32 lanes
 // call this), 16 characters per round.  Lane l < m holds string index `id`
-// and its 16 characters at `depth`.  Writes perm and lcp of R-local positions
-// out .. out + m - 1 (not the lcp of position `out`, which the caller owns).
-__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t k0,
-                                            uint64_t k1, uint32_t out) {
+// (string offset `off`) and its 16 characters at `depth`.  Writes perm and lcp
+// of R-local positions out .. out + m - 1 (not the lcp of position `out`,
+// which the caller owns).
+__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t off,
+                                            uint64_t k0, uint64_t k1, uint32_t out) {
     const uint32_t lane = threadIdx.x & 31;
     WElem e;
-    if (lane < m) { e.g = 0; e.i = id; e.k0 = k0; e.k1 = k1; }
-    else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.k0 = ~0ull; e.k1 = ~0ull; }
+    if (lane < m) { e.g = 0; e.i = id; e.o = off; e.k0 = k0; e.k1 = k1; }
+    else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.o = 0; e.k0 = ~0ull; e.k1 = ~0ull; }
     uint32_t lcp = 0;
     for (;;) {
         for (int k = 2; k <= 32; k <<= 1) {
@@ -91,7 +94,7 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
         if (lane < m) e.g = sg;
         if (!__any_sync(0xffffffffu, active)) break;
         depth += 16;
-        if (active) load_key2(R, e.i, depth, e.k0, e.k1);
+        if (active) load_key2_o(R, e.i, e.o, depth, e.k0, e.k1);
     }
     if (lane < m) {
         R.perm_out[out + lane] = e.i;
@@ -102,30 +105,30 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
 // Tiny base cases (2..32 strings), one warp each.  The task count is read on
 // the device: the CTA base cases below append groups to the same list.
 __global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, const uint32_t *ntask_dev,
-                                                         const ReqDesc *reqs, const uint32_t *idx0,
-                                                         const uint64_t *key0, const uint32_t *idx1,
-                                                         const uint64_t *key1) {
+                                                         const ReqDesc *reqs, ElemBufs eb) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t ntask = *ntask_dev;
     for (uint32_t tk = gw; tk < ntask; tk += nw) {
         SmallTask t = tasks[tk];
-        const uint32_t *idx = t.parity ? idx1 : idx0;
-        const uint64_t *key = t.parity ? key1 : key0;
+        const uint32_t *idx = eb.idx[t.parity];
+        const uint64_t *soff = eb.soff[t.parity];
+        const uint64_t *key = eb.key[t.parity];
         const ReqDesc &R = reqs[t.req];
         uint32_t id = 0;
-        uint64_t k0 = 0, k1 = 0;
+        uint64_t off = 0, k0 = 0, k1 = 0;
         if (lane < t.size) {
             id = idx[t.begin + lane];
+            off = soff[t.begin + lane];
             if (t.gather) {
-                load_key2(R, id, t.depth, k0, k1);
+                load_key2_o(R, id, off, t.depth, k0, k1);
             } else {
                 k0 = key[t.begin + lane];
-                k1 = has_zero(k0) ? 0ull : load_key(R, id, t.depth + 8);
+                k1 = has_zero(k0) ? 0ull : load_key_o(R, id, off, t.depth + 8);
             }
         }
-        warp_finish(R, t.size, t.depth, id, k0, k1, t.begin - R.base);
+        warp_finish(R, t.size, t.depth, id, off, k0, k1, t.begin - R.base);
     }
 }
 
@@ -258,10 +261,12 @@ struct BaseSmem {
     uint32_t nwl, nws, wbase;   // small groups, their strings, first reserved list slot
 };
 
+// Small groups are handed to the warp kernel through the other parity's
+// buffers: base cases run after the last level, so those positions of the
+// task are free, and no other task reads them.
 template <int NT, int ITEMS>
 __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
-                                                 uint32_t *idx0, const uint64_t *key0, uint32_t *idx1,
-                                                 const uint64_t *key1, SmallTask *tiny, uint32_t tiny_cap,
+                                                 ElemBufs eb, SmallTask *tiny, uint32_t tiny_cap,
                                                  uint32_t *counters) {
     constexpr uint32_t CAP = NT * ITEMS;
     constexpr int NW = NT / 32;
@@ -270,8 +275,11 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (uint32_t tk = blockIdx.x; tk < ntask; tk += gridDim.x) {
         const SmallTask t = tasks[tk];
-        uint32_t *idx = t.parity ? idx1 : idx0;
-        const uint64_t *key = t.parity ? key1 : key0;
+        const uint32_t *idx = eb.idx[t.parity];
+        const uint64_t *soff = eb.soff[t.parity];
+        const uint64_t *key = eb.key[t.parity];
+        uint32_t *idx_hand = eb.idx[t.parity ^ 1];
+        uint64_t *soff_hand = eb.soff[t.parity ^ 1];
         const ReqDesc &R = reqs[t.req];
         const uint32_t m = t.size <= CAP ? t.size : CAP;
         const uint32_t lbase = t.begin - R.base;
@@ -383,7 +391,8 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
                 if (s < M && stays[j]) {
                     uint32_t pos = spos[j];
                     S.ACT[S.MG[s]] = (uint16_t)pos;
-                    S.SK[pos] = load_key(R, S.SI[S.SP[pos]], depth + 8);
+                    uint32_t orig = S.SP[pos];
+                    S.SK[pos] = load_key_o(R, S.SI[orig], soff[t.begin + orig], depth + 8);
                 }
             }
             // groups of 2..32 strings go to the warp kernel: their string indices in
@@ -398,10 +407,14 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
             for (uint32_t w = warp; w < nwl; w += NW) {
                 uint32_t e = S.WL[w];
                 uint32_t s0 = e >> 16, sz = e & 0xFFFFu;
-                if (lane < sz) idx[t.begin + s0 + lane] = S.SI[S.SP[s0 + lane]];
+                if (lane < sz) {
+                    uint32_t orig = S.SP[s0 + lane];
+                    idx_hand[t.begin + s0 + lane] = S.SI[orig];
+                    soff_hand[t.begin + s0 + lane] = soff[t.begin + orig];
+                }
                 if (lane == 0) {
                     uint32_t k = S.wbase + w;
-                    if (k < tiny_cap) tiny[k] = SmallTask{t.begin + s0, sz, depth + 8, t.req, t.parity, 1u};
+                    if (k < tiny_cap) tiny[k] = SmallTask{t.begin + s0, sz, depth + 8, t.req, t.parity ^ 1u, 1u};
                     else set_error(counters, E_SMALL_OVERFLOW, k);
                 }
             }

@@ -76,13 +76,17 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // ------------------------------------------------------------ k_init
 
-__global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t *idx0, uint64_t *key0) {
+// every element starts as (string index, string offset, key at depth 0); the
+// offset travels with the index so later gathers need one random load, not two
+__global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t *idx0, uint64_t *soff0, uint64_t *key0) {
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
         uint32_t r = find_req(reqs, nreq, g);
         const ReqDesc &R = reqs[r];
         uint32_t i = g - R.base;
+        uint64_t off = __ldg(R.offsets + i);
         idx0[g] = i;
-        key0[g] = load_key(R, i, 0);
+        soff0[g] = off;
+        key0[g] = load_key_o(R, i, off, 0);
         if (i == 0) {
             R.lcp_out[0] = 0;
             if (R.n == 1) R.perm_out[0] = 0;
@@ -494,10 +498,11 @@ constexpr int kScatterBatch = 8;   // placements computed, then gathers in fligh
 
 template <int MODE>
 __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32_t nseg, const ReqDesc *reqs,
-                                                      const uint32_t *idx_in, const uint64_t *key_in,
-                                                      const uint16_t *obuf, const uint32_t *scan,
-                                                      const uint64_t *splitters, uint32_t *idx_out,
-                                                      uint64_t *key_out, uint32_t *counters) {
+                                                      const uint32_t *idx_in, const uint64_t *soff_in,
+                                                      const uint64_t *key_in, const uint16_t *obuf,
+                                                      const uint32_t *scan, const uint64_t *splitters,
+                                                      uint32_t *idx_out, uint64_t *soff_out, uint64_t *key_out,
+                                                      uint32_t *counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const uint32_t tile = blockIdx.x;
@@ -581,16 +586,25 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
             continue;
         }
         const ReqDesc &R = *Rp;
-        uint64_t nk[kScatterBatch];
+        uint64_t nk[kScatterBatch], so[kScatterBatch];
 #pragma unroll
         for (int u = 0; u < kScatterBatch; u++) {
             nk[u] = 0;
+            so[u] = 0;
             if (!ok[u]) continue;
             uint32_t info = S.binfo[bk[u]];
             if (info & 16u) continue;   // final: no next key
+            uint32_t p = wbeg + (it + u) * 32 + lane;
+            so[u] = soff_in[p];
+        }
+#pragma unroll
+        for (int u = 0; u < kScatterBatch; u++) {
+            if (!ok[u]) continue;
+            uint32_t info = S.binfo[bk[u]];
+            if (info & 16u) continue;
             uint32_t delta = info & 15u;
             uint32_t p = wbeg + (it + u) * 32 + lane;
-            nk[u] = delta == 0 ? key_in[p] : load_key(R, id[u], sg.depth + delta);
+            nk[u] = delta == 0 ? key_in[p] : load_key_o(R, id[u], so[u], sg.depth + delta);
         }
 #pragma unroll
         for (int u = 0; u < kScatterBatch; u++) {
@@ -604,6 +618,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
                 if ((info & 32u) && q > S.bstart[bk[u]]) R.lcp_out[local] = sg.depth + (info >> 8);
             } else {
                 idx_out[q] = id[u];
+                soff_out[q] = so[u];
                 key_out[q] = nk[u];
             }
         }
@@ -765,6 +780,7 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     Carve c{nullptr, 0};
     c.take<uint32_t>(N); c.take<uint32_t>(N);
     c.take<uint64_t>(N); c.take<uint64_t>(N);
+    c.take<uint64_t>(N); c.take<uint64_t>(N);
     c.take<uint16_t>(N);
     c.take<uint32_t>(caps.counts);
     c.take<uint32_t>(np);
@@ -824,6 +840,9 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     Carve c{(char *)block, 0};
     uint32_t *idx[2] = {c.take<uint32_t>(N), c.take<uint32_t>(N)};
     uint64_t *key[2] = {c.take<uint64_t>(N), c.take<uint64_t>(N)};
+    uint64_t *soff[2] = {c.take<uint64_t>(N), c.take<uint64_t>(N)};
+    ElemBufs eb;
+    for (int p = 0; p < 2; p++) { eb.idx[p] = idx[p]; eb.soff[p] = soff[p]; eb.key[p] = key[p]; }
     uint16_t *obuf = c.take<uint16_t>(N);
     uint32_t *counts = c.take<uint32_t>(caps.counts);
     uint32_t *partial = c.take<uint32_t>(np);
@@ -879,7 +898,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
                 "copy base-case tasks");
     {
         uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
-        SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], key[0]));
+        SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0], key[0]));
         TRY(cudaGetLastError(), "init launch");
     }
     {
@@ -901,7 +920,8 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             TRY(cudaGetLastError(), "classify launch");
             if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) goto done;
             SS_LAUNCH_U("scatter", st, nelems, k_scatter<MODE_SORT><<<ntiles, kThreads, sizeof(ScatterSmem), st>>>(
-                big[cur], nbig, dreqs, idx[cur], key[cur], obuf, counts, splitters, idx[nxt], key[nxt], counters));
+                big[cur], nbig, dreqs, idx[cur], soff[cur], key[cur], obuf, counts, splitters, idx[nxt], soff[nxt],
+                key[nxt], counters));
             TRY(cudaMemsetAsync(counters + C_NBIG, 0, sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_TILES, 0, 3 * sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_ELEMS, 0, sizeof(uint32_t), st), "reset");
@@ -935,21 +955,21 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         if (uint32_t n1 = hc[C_NTASK + 1]) {
             uint32_t grid = std::min<uint32_t>(n1, sms * 32);
             SS_LAUNCH_U("small_cta256", st, hc[C_ETASK + 1], (k_base_cta<32, 8><<<grid, 32, sizeof(BaseSmem<32, 8>), st>>>(
-                L[1], n1, dreqs, idx[0], key[0], idx[1], key[1], L[0], tl.cap[0], counters)));
+                L[1], n1, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (uint32_t n2 = hc[C_NTASK + 2]) {
             uint32_t grid = std::min<uint32_t>(n2, sms * 8);
             SS_LAUNCH_U("small_cta1024", st, hc[C_ETASK + 2], (k_base_cta<128, 8><<<grid, 128, sizeof(BaseSmem<128, 8>), st>>>(
-                L[2], n2, dreqs, idx[0], key[0], idx[1], key[1], L[0], tl.cap[0], counters)));
+                L[2], n2, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (uint32_t n3 = hc[C_NTASK + 3]) {
             uint32_t grid = std::min<uint32_t>(n3, sms * 2);
             SS_LAUNCH_U("small_cta4096", st, hc[C_ETASK + 3], (k_base_cta<512, 8><<<grid, 512, sizeof(BaseSmem<512, 8>), st>>>(
-                L[3], n3, dreqs, idx[0], key[0], idx[1], key[1], L[0], tl.cap[0], counters)));
+                L[3], n3, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (hc[C_NTASK + 0] || hc[C_NTASK + 1] || hc[C_NTASK + 2] || hc[C_NTASK + 3]) {
             uint32_t grid = sms * 8;
-            SS_LAUNCH_U("small_warp", st, hc[C_ETASK + 0], k_small_warp<<<grid, kThreads, 0, st>>>(L[0], counters + C_NTASK + 0, dreqs, idx[0], key[0], idx[1], key[1]));
+            SS_LAUNCH_U("small_warp", st, hc[C_ETASK + 0], k_small_warp<<<grid, kThreads, 0, st>>>(L[0], counters + C_NTASK + 0, dreqs, eb));
         }
         TRY(cudaGetLastError(), "base case launch");
         if (nb) {
@@ -1011,7 +1031,7 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
             if ((e = cudaGetLastError())) break;
             if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) break;
             SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY><<<tiles, kThreads, sizeof(ScatterSmem), st>>>(
-                seg, 1, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, counters));
+                seg, 1, nullptr, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, nullptr, counters));
             if ((e = cudaGetLastError())) break;
             SS_LAUNCH("bucket_begin", st, k_bucket_begin<<<1, 256, 0, st>>>(seg, counts, bucket_begin_out));
         } else {

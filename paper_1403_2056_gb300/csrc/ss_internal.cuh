@@ -86,6 +86,12 @@ enum Counter : int {
     C_NUM = 24
 };
 
+struct ElemBufs {               // per-position element arrays, double buffered by parity
+    uint32_t *idx[2];           // string index (request-local)
+    uint64_t *soff[2];          // byte offset of the string in its request's chars
+    uint64_t *key[2];           // 8 characters at the segment's depth
+};
+
 struct TaskLists {              // base-case task lists by size class
     SmallTask *l[kClasses];
     uint32_t cap[kClasses];
@@ -133,11 +139,10 @@ __device__ __forceinline__ uint32_t lcp8(uint64_t a, uint64_t b) {
     return x ? (uint32_t)(__clzll(x) >> 3) : 8u;
 }
 
-// chars_h: 8 bytes of string i at depth h, big-endian, zero past the end.
-// Reads the aligned word holding byte h, and the next aligned word only when
-// the string continues into it.
-__device__ __forceinline__ uint64_t load_key(const ReqDesc &R, uint32_t i, uint32_t h) {
-    uint64_t off = __ldg(R.offsets + i);
+// chars_h: 8 bytes of string i (starting at byte `off` of chars) at depth h,
+// big-endian, zero past the end.  Reads the aligned word holding byte h, and
+// the next aligned word only when the string continues into it.
+__device__ __forceinline__ uint64_t load_key_o(const ReqDesc &R, uint32_t i, uint64_t off, uint32_t h) {
     uint64_t rem = ~0ULL;   // bytes of the string left from depth h (terminated: unknown)
     if (R.lengths) {
         uint32_t len = __ldg(R.lengths + i);
@@ -174,6 +179,10 @@ __device__ __forceinline__ uint64_t load_key(const ReqDesc &R, uint32_t i, uint3
     return key;
 }
 
+__device__ __forceinline__ uint64_t load_key(const ReqDesc &R, uint32_t i, uint32_t h) {
+    return load_key_o(R, i, __ldg(R.offsets + i), h);
+}
+
 // keep the bytes of a big-endian key before byte k (k in 0..8)
 __device__ __forceinline__ uint64_t keep_bytes(uint64_t key, uint32_t k) {
     return k >= 8 ? key : (k ? key & (~0ULL << (64 - 8 * k)) : 0ULL);
@@ -182,8 +191,8 @@ __device__ __forceinline__ uint64_t keep_bytes(uint64_t key, uint32_t k) {
 // chars_h for 16 characters: k0 = bytes [h, h+8), k1 = [h+8, h+16), zero past
 // the end.  Each further aligned word is read only when the string continues
 // into it, so no read leaves the string and its terminator.
-__device__ __forceinline__ void load_key2(const ReqDesc &R, uint32_t i, uint32_t h, uint64_t &k0, uint64_t &k1) {
-    uint64_t off = __ldg(R.offsets + i);
+__device__ __forceinline__ void load_key2_o(const ReqDesc &R, uint32_t i, uint64_t off, uint32_t h, uint64_t &k0,
+                                            uint64_t &k1) {
     uint64_t rem = ~0ULL;
     if (R.lengths) {
         uint32_t len = __ldg(R.lengths + i);
@@ -227,6 +236,10 @@ __device__ __forceinline__ void load_key2(const ReqDesc &R, uint32_t i, uint32_t
         uint64_t z1 = zero_bytes(k1);
         if (z1) k1 = keep_bytes(k1, (uint32_t)(__clzll(z1) >> 3));
     }
+}
+
+__device__ __forceinline__ void load_key2(const ReqDesc &R, uint32_t i, uint32_t h, uint64_t &k0, uint64_t &k1) {
+    load_key2_o(R, i, __ldg(R.offsets + i), h, k0, k1);
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finaliser

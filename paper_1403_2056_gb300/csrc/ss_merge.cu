@@ -28,11 +28,12 @@ constexpr uint32_t kCoarse = 256;      // outputs per merge-path window
 
 // full comparison of strings a and b from depth h on (both share h characters),
 // 16 characters per round; returns -1/0/+1 and the lcp in *l
-__device__ __forceinline__ int str_cmp_from(const ReqDesc &S, uint32_t a, uint32_t b, uint32_t h, uint32_t *l) {
+__device__ __forceinline__ int str_cmp_from(const ReqDesc &S, uint32_t a, uint64_t oa, uint32_t b, uint64_t ob,
+                                            uint32_t h, uint32_t *l) {
     for (;;) {
         uint64_t a0, a1, b0, b1;
-        load_key2(S, a, h, a0, a1);
-        load_key2(S, b, h, b0, b1);
+        load_key2_o(S, a, oa, h, a0, a1);
+        load_key2_o(S, b, ob, h, b0, b1);
         if (a0 != b0) { *l = h + lcp8(a0, b0); return a0 < b0 ? -1 : 1; }
         if (has_zero(a0)) { *l = h + nulpos(a0); return 0; }
         if (a1 != b1) { *l = h + 8 + lcp8(a1, b1); return a1 < b1 ? -1 : 1; }
@@ -41,16 +42,22 @@ __device__ __forceinline__ int str_cmp_from(const ReqDesc &S, uint32_t a, uint32
     }
 }
 
-// pair (2p, 2p+1) of the round's runs; an unpaired last run has B empty
+// pair (2p, 2p+1) of the round's runs; an unpaired last run has B empty.
+// With a table of string offsets aligned to the runs (Ao/Bo) every string
+// access is one random load; without one the set's offsets are looked up.
 struct PairView {
     uint32_t a0, na, nb, baseA, baseB;
     const uint32_t *Ap, *Bp, *HA, *HB;
+    const uint64_t *Ao, *Bo, *offsets;
     __device__ __forceinline__ uint32_t A(uint32_t k) const { return Ap[k] + baseA; }
     __device__ __forceinline__ uint32_t B(uint32_t k) const { return Bp[k] + baseB; }
+    __device__ __forceinline__ uint64_t OA(uint32_t k) const { return Ao ? Ao[k] : __ldg(offsets + A(k)); }
+    __device__ __forceinline__ uint64_t OB(uint32_t k) const { return Bo ? Bo[k] : __ldg(offsets + B(k)); }
 };
 
-__device__ __forceinline__ PairView pair_view(uint32_t p, const uint32_t *in_perm, const uint32_t *in_lcp,
-                                              const uint32_t *rb, uint32_t R, const uint32_t *rbase) {
+__device__ __forceinline__ PairView pair_view(const ReqDesc &S, uint32_t p, const uint32_t *in_perm,
+                                              const uint32_t *in_lcp, const uint64_t *in_off, const uint32_t *rb,
+                                              uint32_t R, const uint32_t *rbase) {
     PairView v;
     uint32_t a1 = rb[2 * p + 1];
     uint32_t b1 = (2 * p + 1 < R) ? rb[2 * p + 2] : a1;
@@ -61,6 +68,9 @@ __device__ __forceinline__ PairView pair_view(uint32_t p, const uint32_t *in_per
     v.Bp = in_perm + a1;
     v.HA = in_lcp + v.a0;
     v.HB = in_lcp + a1;
+    v.Ao = in_off ? in_off + v.a0 : nullptr;
+    v.Bo = in_off ? in_off + a1 : nullptr;
+    v.offsets = S.offsets;
     // string index of a run entry: entry + the run's index base (first round only)
     v.baseA = rbase ? rbase[2 * p] : 0u;
     v.baseB = (rbase && 2 * p + 1 < R) ? rbase[2 * p + 1] : 0u;
@@ -73,10 +83,39 @@ __device__ __forceinline__ uint32_t path_search(const ReqDesc &S, const PairView
                                                 uint32_t hi, uint32_t h) {
     while (lo < hi) {
         uint32_t mid = (lo + hi) / 2;
-        uint32_t l;
-        if (str_cmp_from(S, v.A(mid), v.B(diag - 1 - mid), h, &l) <= 0) lo = mid + 1; else hi = mid;
+        uint32_t l, bj = diag - 1 - mid;
+        if (str_cmp_from(S, v.A(mid), v.OA(mid), v.B(bj), v.OB(bj), h, &l) <= 0) lo = mid + 1; else hi = mid;
     }
     return lo;
+}
+
+// string offset of every run entry, for the first round
+// Per round, for every run entry: its string offset (first round: looked up
+// and written to off; later rounds: carried in off) and its cached characters
+// ck = the 8 characters at its run LCP (0 for a run's first entry), the
+// distinguishing characters that the caching variant of Section 4.4 keeps so
+// that LCP-Compare's first character comparison needs no string access.
+__global__ void k_run_prep(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R,
+                           const uint32_t *rbase, uint32_t total, int lookup_offsets, uint64_t *off, uint64_t *ck,
+                           uint32_t *ckd) {
+    for (uint32_t p = blockIdx.x * blockDim.x + threadIdx.x; p < total; p += gridDim.x * blockDim.x) {
+        uint32_t lo = 0, hi = R;   // run of position p
+        while (hi - lo > 1) {
+            uint32_t mid = (lo + hi) / 2;
+            if (rb[mid] <= p) lo = mid; else hi = mid;
+        }
+        uint32_t id = in_perm[p] + (rbase ? rbase[lo] : 0u);
+        uint64_t o;
+        if (lookup_offsets) {
+            o = __ldg(S.offsets + id);
+            off[p] = o;
+        } else {
+            o = off[p];
+        }
+        uint32_t d = p == rb[lo] ? 0u : in_lcp[p];
+        ck[p] = load_key_o(S, id, o, d);
+        ckd[p] = d;
+    }
 }
 
 struct Coarse {
@@ -94,13 +133,13 @@ __device__ __forceinline__ uint32_t pair_of_entry(const uint32_t *cbase, uint32_
 }
 
 // window cuts: pair p has entries cbase[p] + k for diagonals min(k kCoarse, na + nb)
-__global__ void k_merge_cuts(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb,
-                             uint32_t R, const uint32_t *rbase, const uint32_t *cbase, uint32_t npairs,
-                             uint32_t nentries, Coarse *C) {
+__global__ void k_merge_cuts(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint64_t *in_off,
+                             const uint32_t *rb, uint32_t R, const uint32_t *rbase, const uint32_t *cbase,
+                             uint32_t npairs, uint32_t nentries, Coarse *C) {
     uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nentries) return;
     uint32_t p = pair_of_entry(cbase, npairs, e);
-    PairView v = pair_view(p, in_perm, in_lcp, rb, R, rbase);
+    PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
     uint32_t len = v.na + v.nb;
     uint32_t diag = min((e - cbase[p]) * kCoarse, len);
     uint32_t lo = diag > v.nb ? diag - v.nb : 0, hi = min(diag, v.na);
@@ -110,23 +149,23 @@ __global__ void k_merge_cuts(ReqDesc S, const uint32_t *in_perm, const uint32_t 
 // characters shared by a whole window: the strings of a window are a
 // contiguous run of the merged order, so they share min(lcp(A_i0, A_i1-1),
 // lcp(B_j0, B_j1-1), lcp(A_i0, B_j0)) characters
-__global__ void k_merge_windows(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb,
-                                uint32_t R, const uint32_t *rbase, const uint32_t *cbase, uint32_t npairs,
-                                uint32_t nentries, Coarse *C) {
+__global__ void k_merge_windows(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint64_t *in_off,
+                                const uint32_t *rb, uint32_t R, const uint32_t *rbase, const uint32_t *cbase,
+                                uint32_t npairs, uint32_t nentries, Coarse *C) {
     uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= nentries) return;
     uint32_t p = pair_of_entry(cbase, npairs, e);
     uint32_t last = (p + 1 < npairs ? cbase[p + 1] : nentries) - 1;
     if (e == last) { C[e].h = 0; return; }
-    PairView v = pair_view(p, in_perm, in_lcp, rb, R, rbase);
+    PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
     uint32_t len = v.na + v.nb;
     uint32_t k = e - cbase[p];
     uint32_t d0 = min(k * kCoarse, len), d1 = min((k + 1) * kCoarse, len);
     uint32_t i0 = C[e].i, i1 = C[e + 1].i, j0 = d0 - i0, j1 = d1 - i1;
     uint32_t h = 0xFFFFFFFFu, l;
-    if (i1 > i0) { str_cmp_from(S, v.A(i0), v.A(i1 - 1), 0, &l); h = min(h, l); }
-    if (j1 > j0) { str_cmp_from(S, v.B(j0), v.B(j1 - 1), 0, &l); h = min(h, l); }
-    if (i1 > i0 && j1 > j0) { str_cmp_from(S, v.A(i0), v.B(j0), 0, &l); h = min(h, l); }
+    if (i1 > i0) { str_cmp_from(S, v.A(i0), v.OA(i0), v.A(i1 - 1), v.OA(i1 - 1), 0, &l); h = min(h, l); }
+    if (j1 > j0) { str_cmp_from(S, v.B(j0), v.OB(j0), v.B(j1 - 1), v.OB(j1 - 1), 0, &l); h = min(h, l); }
+    if (i1 > i0 && j1 > j0) { str_cmp_from(S, v.A(i0), v.OA(i0), v.B(j0), v.OB(j0), 0, &l); h = min(h, l); }
     C[e].h = h == 0xFFFFFFFFu ? 0u : h;
 }
 
@@ -146,7 +185,8 @@ __device__ __forceinline__ uint32_t upper_run(const uint32_t *rb, uint32_t R, ui
 // searches the whole pair from depth 0.
 __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R,
                               const uint32_t *rbase, uint32_t total, uint32_t *out_perm, uint32_t *out_lcp,
-                              const Coarse *C, const uint32_t *cbase) {
+                              const Coarse *C, const uint32_t *cbase, const uint64_t *in_off, uint64_t *out_off,
+                              const uint64_t *ck, const uint32_t *ckd, uint64_t *out_ck, uint32_t *out_ckd) {
     uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
     uint64_t o64 = (uint64_t)t * kMergeItems;
     if (o64 >= total) return;
@@ -155,11 +195,13 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
     while (o < end) {
         uint32_t r = upper_run(rb, R, o);
         uint32_t p = r / 2;
-        const PairView v = pair_view(p, in_perm, in_lcp, rb, R, rbase);
+        const PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
         const uint32_t a0 = v.a0, na = v.na, nb = v.nb;
         const uint32_t *HA = v.HA, *HB = v.HB;
         auto A = [&](uint32_t k) { return v.A(k); };
         auto B = [&](uint32_t k) { return v.B(k); };
+        auto OA = [&](uint32_t k) { return v.OA(k); };
+        auto OB = [&](uint32_t k) { return v.OB(k); };
         const uint32_t pair_end = a0 + na + nb;
         const uint32_t stop = min(end, pair_end);
         uint32_t diag = o - a0;
@@ -201,19 +243,34 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
             else {
                 uint32_t l;
                 uint32_t h0 = (inA(i - 1) && inB(j - 1)) ? hw : 0u;
-                last_is_b = str_cmp_from(S, A(i - 1), B(j - 1), h0, &l) <= 0;   // ties: A then B
+                last_is_b = str_cmp_from(S, A(i - 1), OA(i - 1), B(j - 1), OB(j - 1), h0, &l) <= 0;   // ties: A then B
             }
             uint32_t prev = last_is_b ? B(j - 1) : A(i - 1);
+            uint64_t prev_o = last_is_b ? OB(j - 1) : OA(i - 1);
             bool prev_in = last_is_b ? inB(j - 1) : inA(i - 1);
             if (i < na) {
                 if (!last_is_b) ha = HA[i];
-                else { uint32_t l; str_cmp_from(S, prev, A(i), (prev_in && inA(i)) ? hw : 0u, &l); ha = l; }
+                else { uint32_t l; str_cmp_from(S, prev, prev_o, A(i), OA(i), (prev_in && inA(i)) ? hw : 0u, &l); ha = l; }
             }
             if (j < nb) {
                 if (last_is_b) hb = HB[j];
-                else { uint32_t l; str_cmp_from(S, prev, B(j), (prev_in && inB(j)) ? hw : 0u, &l); hb = l; }
+                else { uint32_t l; str_cmp_from(S, prev, prev_o, B(j), OB(j), (prev_in && inB(j)) ? hw : 0u, &l); hb = l; }
             }
         }
+        // cached characters of the fronts: 8 bytes of the string at depth kd
+        // (kd = ~0: none), refreshed from (ck, ckd) whenever a front advances;
+        // a cache is a fact about its string, so it travels with the string
+        // into the next round
+        uint32_t kdA = ~0u, kdB = ~0u;
+        uint64_t kA = 0, kB = 0;
+        auto cacheA = [&]() {
+            if (ck && i < na) { kdA = ckd[a0 + i]; kA = ck[a0 + i]; } else kdA = ~0u;
+        };
+        auto cacheB = [&]() {
+            if (ck && j < nb) { kdB = ckd[a0 + na + j]; kB = ck[a0 + na + j]; } else kdB = ~0u;
+        };
+        cacheA();
+        cacheB();
         // binary LCP-merge (Algorithm 3) over positions [o, stop)
         for (; o < stop; o++) {
             bool take_b;
@@ -222,8 +279,32 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
             if (!both) {
                 take_b = i >= na;
             } else if (ha == hb) {   // case 1: compare characters from the common LCP on
-                int c = str_cmp_from(S, A(i), B(j), ha, &hp);
-                take_b = c > 0;
+                const uint32_t h = ha;
+                bool decided = false;
+                if (kdA <= h && kdB <= h && h - kdA < 8 && h - kdB < 8) {
+                    // both fronts' cached bytes cover depth h: compare the overlap
+                    const uint32_t sa = h - kdA, sb = h - kdB;
+                    const uint64_t wa = kA << (8 * sa), wb = kB << (8 * sb);
+                    const uint32_t nk = 8 - max(sa, sb);   // bytes known for both from h on
+                    const uint64_t mask = ~0ull << (64 - 8 * nk);
+                    const uint64_t x = (wa ^ wb) & mask;
+                    if (x) {
+                        hp = h + (uint32_t)(__clzll(x) >> 3);
+                        take_b = (wa & mask) > (wb & mask);
+                        decided = true;
+                    } else {
+                        const uint64_t z = zero_bytes(wa) & mask;   // both end inside the overlap: equal
+                        if (z) {
+                            hp = h + (uint32_t)(__clzll(z) >> 3);
+                            take_b = false;
+                            decided = true;
+                        }
+                    }
+                }
+                if (!decided) {
+                    int c = str_cmp_from(S, A(i), OA(i), B(j), OB(j), h, &hp);
+                    take_b = c > 0;
+                }
             } else if (ha < hb) {    // case 2: B is smaller
                 take_b = true;
                 hp = ha;
@@ -233,16 +314,22 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
             }
             if (!take_b) {
                 out_perm[o] = A(i);
+                if (out_off) out_off[o] = OA(i);
+                if (out_ck) { out_ck[o] = kA; out_ckd[o] = kdA; }
                 out_lcp[o] = (o == a0) ? 0u : ha;
                 i++;
                 ha = i < na ? HA[i] : 0;
                 if (both) hb = hp;
+                cacheA();
             } else {
                 out_perm[o] = B(j);
+                if (out_off) out_off[o] = OB(j);
+                if (out_ck) { out_ck[o] = kB; out_ckd[o] = kdB; }
                 out_lcp[o] = (o == a0) ? 0u : hb;
                 j++;
                 hb = j < nb ? HB[j] : 0;
                 if (both) ha = hp;
+                cacheB();
             }
         }
     }
@@ -273,7 +360,8 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
     // window table: at most total / kCoarse + 2 entries per pair
     const size_t max_entries = (size_t)total / kCoarse + 2ull * (K + 1) + 2;
     const size_t a64 = 63;
-    size_t bytes = 2ull * 4 * (((size_t)total + a64) & ~a64) + 4ull * (4 * (K + 2) + 64) + sizeof(Coarse) * max_entries + 4096;
+    const size_t tot64 = ((size_t)total + a64) & ~a64;
+    size_t bytes = 4ull * 8 * tot64 + 4ull * 4 * tot64 + 4ull * (4 * (K + 2) + 64) + sizeof(Coarse) * max_entries + 4096;
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
     if (e) {
@@ -281,9 +369,14 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
         set_error_detail("ss_merge: scratch allocation of %zu bytes failed", bytes);
         return SS_ERR_OOM;
     }
-    uint32_t *tmp_perm = (uint32_t *)block;
-    uint32_t *tmp_lcp = tmp_perm + (((size_t)total + a64) & ~a64);
-    uint32_t *d_rb = tmp_lcp + (((size_t)total + a64) & ~a64);   // rb[R+1], bases[R], cbase[pairs]
+    // string offsets and cached characters (bytes, depth) aligned to the runs,
+    // ping-pong across rounds
+    uint64_t *off_buf[2] = {(uint64_t *)block, (uint64_t *)block + tot64};
+    uint64_t *ck_buf[2] = {off_buf[1] + tot64, off_buf[1] + 2 * tot64};
+    uint32_t *ckd_buf[2] = {(uint32_t *)(ck_buf[1] + tot64), (uint32_t *)(ck_buf[1] + tot64) + tot64};
+    uint32_t *tmp_perm = ckd_buf[1] + tot64;
+    uint32_t *tmp_lcp = tmp_perm + tot64;
+    uint32_t *d_rb = tmp_lcp + tot64;   // rb[R+1], bases[R], cbase[pairs]
     Coarse *d_coarse = (Coarse *)(d_rb + ((4 * (K + 2) + 63) & ~63u));
     int rc = SS_OK;
     uint32_t *stage = (uint32_t *)host_staging(sizeof(uint32_t) * 4 * (K + 2));
@@ -320,13 +413,25 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             if ((e = cudaMemcpyAsync(d_rb, stage, cp, cudaMemcpyHostToDevice, st))) break;
             const uint32_t *bases = round == 1 ? d_rb + (R + 1) : nullptr;
             const uint32_t *d_cb = d_rb + (2 * R + 1);
+            const uint64_t *src_o = off_buf[(round - 1) & 1];
+            uint64_t *dst_o = last ? nullptr : off_buf[round & 1];
+            const uint64_t *src_ck = ck_buf[(round - 1) & 1];
+            const uint32_t *src_ckd = ckd_buf[(round - 1) & 1];
+            uint64_t *dst_ck = last ? nullptr : ck_buf[round & 1];
+            uint32_t *dst_ckd = last ? nullptr : ckd_buf[round & 1];
+            if (round == 1) {
+                uint32_t grid = std::min<uint32_t>((total + 255) / 256, 8192);
+                SS_LAUNCH_U("run_prep", st, total, k_run_prep<<<grid, 256, 0, st>>>(
+                    set, src_p, src_l, d_rb, R, bases, total, 1, off_buf[0], ck_buf[0], ckd_buf[0]));
+            }
             SS_LAUNCH_U("merge_cuts", st, nentries, k_merge_cuts<<<(nentries + 127) / 128, 128, 0, st>>>(
-                set, src_p, src_l, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
+                set, src_p, src_l, src_o, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
             SS_LAUNCH_U("merge_windows", st, nentries, k_merge_windows<<<(nentries + 127) / 128, 128, 0, st>>>(
-                set, src_p, src_l, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
+                set, src_p, src_l, src_o, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
             uint32_t threads = (total + kMergeItems - 1) / kMergeItems;
             SS_LAUNCH_U("merge_round", st, total, k_merge_round<<<(threads + 255) / 256, 256, 0, st>>>(
-                set, src_p, src_l, d_rb, R, bases, total, dst_p, dst_l, d_coarse, d_cb));
+                set, src_p, src_l, d_rb, R, bases, total, dst_p, dst_l, d_coarse, d_cb, src_o, dst_o, src_ck, src_ckd,
+                dst_ck, dst_ckd));
             if ((e = cudaGetLastError())) break;
             // the staging buffer is reused next round: wait for the copy
             if ((e = cudaStreamSynchronize(st))) break;
@@ -445,7 +550,8 @@ static int merge_runs_noalloc(const ReqDesc &set, const uint32_t *run_perm, cons
         SS_LAUNCH("store_run_table", st, k_store_run_table<<<1, 128, 0, st>>>(t, R, d_table));
         uint32_t threads = (total + kMergeItems - 1) / kMergeItems;
         SS_LAUNCH_U("merge_round", st, total, k_merge_round<<<(threads + 255) / 256, 256, 0, st>>>(
-            set, src_p, src_l, d_table, R, d_table + kNoAllocMaxRuns + 1, total, dst_p, dst_l, nullptr, nullptr));
+            set, src_p, src_l, d_table, R, d_table + kNoAllocMaxRuns + 1, total, dst_p, dst_l, nullptr, nullptr,
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr));
         if ((e = cudaGetLastError())) return cuda_fail(e, "ss_merge_noalloc");
         RunTable nt;
         memset(&nt, 0, sizeof(nt));
