@@ -68,6 +68,8 @@ def _load():
             lib.orc_lcp_mergek.restype = C.c_uint64
             lib.orc_lcp_insertion.argtypes = set_args + [_u32p, _u32p, C.c_uint64, C.c_uint64]
             lib.orc_lcp_insertion.restype = C.c_uint64
+            lib.orc_check_sorted.argtypes = set_args + [C.c_uint64, _u32p, _u32p, _u64p]
+            lib.orc_check_sorted.restype = C.c_uint64
             _lib = lib
     return _lib
 
@@ -221,3 +223,15 @@ def lcp_insertion(ss, s, hbar: int = 0):
     h = np.empty(s.shape[0], np.uint32)
     c = lib.orc_lcp_insertion(*a, _p(s, _u32p), _p(h, _u32p), s.shape[0], hbar)
     return s, h, int(c)
+
+
+def check_sorted(ss, perm, lcp):
+    """(failures, first failing position): perm is a permutation, neighbours in
+    order (ties by index), lcp[0] = 0 and lcp[i] the naive LCP, at every position."""
+    lib = _load()
+    keep, a = _set(ss)
+    perm = _c(perm, np.uint32)
+    lcp = _c(lcp, np.uint32)
+    first = C.c_uint64()
+    bad = lib.orc_check_sorted(*a, perm.shape[0], _p(perm, _u32p), _p(lcp, _u32p), C.byref(first))
+    return int(bad), int(first.value)

@@ -528,3 +528,38 @@ uint64_t orc_lcp_insertion(const uint8_t *chars, const uint64_t *offsets, const 
     free(H);
     return ncmp;
 }
+
+/* ------------------------------------------- checks of a claimed output */
+
+/*
+ * Check a claimed sorted order and LCP array against the definitions of
+ * Section 2 at every position: perm is a permutation of 0..n-1, each
+ * neighbouring pair is in order (equal strings by ascending index), lcp[0]
+ * = 0 and lcp[i] is the naive LCP of the neighbours.  Returns the number of
+ * failing positions; *first gets the first one (or n when none fails).
+ */
+uint64_t orc_check_sorted(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths,
+                          uint32_t fixed_len, uint64_t n, const uint32_t *perm, const uint32_t *lcp,
+                          uint64_t *first)
+{
+    orc_set S = {chars, offsets, lengths, fixed_len};
+    uint64_t bad = 0;
+    *first = n;
+    uint8_t *seen = (uint8_t *)calloc(n ? n : 1, 1);
+    for (uint64_t i = 0; i < n; i++) {
+        int ok = perm[i] < n && !seen[perm[i]];
+        if (perm[i] < n) seen[perm[i]] = 1;
+        if (ok && i == 0) ok = lcp[0] == 0;
+        if (ok && i > 0 && perm[i - 1] < n) {
+            int c = str_cmp(&S, perm[i - 1], perm[i]);
+            ok = c < 0 || (c == 0 && perm[i - 1] < perm[i]);
+            if (ok) ok = lcp[i] == str_lcp(&S, perm[i - 1], perm[i]);
+        }
+        if (!ok) {
+            if (*first == n) *first = i;
+            bad++;
+        }
+    }
+    free(seen);
+    return bad;
+}

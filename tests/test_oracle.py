@@ -347,3 +347,32 @@ def test_lcp_mergek(K):
         dL = int(lcp.astype(np.int64).sum()) - sumL_runs
         Kp = 1 << max(0, math.ceil(math.log2(K))) if K > 1 else 1
         assert ncmp <= dL + ss.n * math.log2(Kp) + Kp
+
+
+# ------------------------------------------------ the any-size checker
+
+def test_check_sorted_accepts_oracle_output_and_catches_planted_mistakes():
+    ss = W.url_like(30000, seed=41)
+    perm, lcp = oracle.sort(ss)
+    assert oracle.check_sorted(ss, perm, lcp) == (0, ss.n)
+    rng = np.random.default_rng(1)
+    for _ in range(20):
+        p2, l2 = perm.copy(), lcp.copy()
+        kind = rng.integers(0, 4)
+        i = int(rng.integers(1, ss.n - 1))
+        if kind == 0:     # swap two neighbours
+            p2[i], p2[i + 1] = p2[i + 1], p2[i]
+        elif kind == 1:   # an LCP off by one
+            l2[i] += 1
+        elif kind == 2:   # a duplicated index (not a permutation)
+            p2[i] = p2[i - 1]
+        else:             # nonzero first LCP
+            l2[0] = 1
+        bad, first = oracle.check_sorted(ss, p2, l2)
+        assert bad > 0 and first <= max(i + 1, 1)
+
+
+def test_check_sorted_tie_order():
+    ss = W.from_bytes_list([b"x", b"x", b"a"])
+    assert oracle.check_sorted(ss, np.array([2, 0, 1]), np.array([0, 0, 1])) == (0, 3)
+    assert oracle.check_sorted(ss, np.array([2, 1, 0]), np.array([0, 0, 1]))[0] == 1   # equal strings out of index order
