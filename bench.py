@@ -65,7 +65,68 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-extra", action="store_true", help="skip the DNA 20M and no-LCP 64Mi sorts")
     return ap.parse_args()
+
+
+def other_workloads(P, torch, dev, stream, peak):
+    """One ss_sort of each other full-size workload (device-resident inputs):
+    time, strings/s, whole-sort algorithmic bytes against the HBM peak, and the
+    dominant kernel with its own roofline."""
+    import workloads as W
+    out = {}
+    cases = [
+        ("no_lcp_64Mi", lambda: W.no_lcp(n=64 * 1024 * 1024, seed=5),
+         "n=67,108,864 strings of 16 bytes U[1,255], NUL-terminated, seed 5"),
+        ("dna_windows_20M", lambda: W.dna_windows(n=20_000_000, text_len=400_000_000, window=100, seed=3),
+         "400,000,000-byte text U{A,C,G,T}, n=20,000,000 windows of 100 bytes, seed 3"),
+    ]
+    for name, gen, desc in cases:
+        ss = gen()
+        n = ss.n
+        chars = torch.from_numpy(ss.chars).to(dev)
+        offsets = torch.from_numpy(ss.offsets.view(np.int64)).to(dev)
+        perm = torch.empty(n, dtype=torch.int32, device=dev)
+        lcp = torch.empty(n, dtype=torch.int32, device=dev)
+
+        def run():
+            if ss.fixed_len:
+                P.ss_sort_ex(chars, offsets, None, ss.fixed_len, n, perm, lcp, stream=stream)
+            else:
+                P.ss_sort(chars, offsets, n, perm, lcp, stream=stream)
+
+        for _ in range(2):
+            run()
+        torch.cuda.synchronize(dev)
+        reps = 5
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        P.profile_reset()
+        P.profile_enable(True)
+        run()
+        torch.cuda.synchronize(dev)
+        P.profile_enable(False)
+        prof = P.profile_read()
+        D, balg = d_and_balg(lcp.cpu().numpy().view(np.uint32))
+        dom = max(prof, key=lambda k: prof[k][1])
+        nl, tms, units = prof[dom]
+        bpu = BYTES_PER_UNIT.get(dom)
+        ach = units * bpu / (tms / 1e3) / 1e9 if bpu else None
+        out[name] = {"workload": desc, "n": n, "ms": ms, "strings_per_s": n / (ms / 1e3),
+                     "d_gb_per_s": D / (ms / 1e3) / 1e9,
+                     "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
+                                             "frac": balg / (ms / 1e3) / 1e9 / peak},
+                     "dominant_kernel": {"kernel": dom, "ms": tms, "share": tms / sum(v[1] for v in prof.values()),
+                                         "achieved_gbs": ach, "frac": (ach / peak) if ach else None}}
+        del chars, offsets, perm, lcp
+        torch.cuda.empty_cache()
+    return out
 
 
 def load_peaks():
@@ -371,6 +432,8 @@ def main():
         same = np.array_equal(hp.numpy(), perm.cpu().numpy()) and np.array_equal(hl.numpy(), lcp.cpu().numpy())
         line["e2e"]["equals_device_result"] = bool(same)
 
+    if rank == 0 and not args.no_extra:
+        line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
