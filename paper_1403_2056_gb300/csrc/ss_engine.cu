@@ -36,13 +36,28 @@ namespace ss {
 // --------------------------------------------------------------- helpers
 
 __host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size) {
-    // v + 1 = 2^d about size / 1024 (children near 512 strings), d in [2, 10]
-    uint32_t q = (size + 1023) / 1024;
+    // v + 1 = 2^d about size / kChildTarget, d in [2, 10]
+    uint32_t q = (size + kChildTarget - 1) / kChildTarget;
     uint32_t d = 0;
     while ((1u << d) < q) d++;
     if (d < 2) d = 2;
     if (d > (uint32_t)kMaxD) d = kMaxD;
     return d;
+}
+
+#ifndef SS_MIN_STEP
+#define SS_MIN_STEP 5
+#endif
+// Depth step of the even bucket between splitters x_{r-1} and x_r: its strings
+// share lcp(x_{r-1}, x_r) more characters (0 for the outer buckets).  A step of
+// fewer than SS_MIN_STEP characters is not taken: the bucket keeps its depth
+// and the key it carries, which still holds at least 8 - SS_MIN_STEP + 1
+// unresolved characters, and the random gather of a new key is saved.  Any
+// depth up to the shared prefix gives the same result.
+__device__ __forceinline__ uint32_t even_delta(uint64_t xl, uint64_t xr, uint32_t r, uint32_t v) {
+    if (r == 0 || r == v) return 0u;
+    uint32_t l = lcp8(xl, xr);
+    return l >= (uint32_t)SS_MIN_STEP ? l : 0u;
 }
 
 __host__ __device__ __forceinline__ uint32_t tiles_of(uint32_t size) { return (size + kTile - 1) / kTile; }
@@ -323,8 +338,10 @@ __device__ __forceinline__ uint32_t classify_one(uint64_t c, const uint64_t *t, 
     return 2 * r + ((r < v && x[r] == c) ? 1u : 0u);
 }
 
-__global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *segs, uint32_t nseg, const uint64_t *key,
-                                                       const uint64_t *splitters, uint16_t *obuf, uint32_t *counts) {
+__global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict__ segs, uint32_t nseg,
+                                                       const uint64_t *__restrict__ key,
+                                                       const uint64_t *__restrict__ splitters,
+                                                       uint16_t *__restrict__ obuf, uint32_t *__restrict__ counts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClassifySmem &S = *reinterpret_cast<ClassifySmem *>(smem_raw);
     const uint32_t tile = blockIdx.x;
@@ -332,33 +349,39 @@ __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *segs, uint3
     const BigSeg sg = segs[si];
     const uint32_t tl = tile - sg.tile_base;
     const uint32_t d = sg.d, v = (1u << d) - 1, B = 2 * v + 1;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t seg_end = sg.begin + sg.size;
+    const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
+    // every key of this thread in flight while the tree is staged
+    uint64_t c[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; u++) {
+        uint32_t p = wbeg + u * 32 + lane;
+        c[u] = p < seg_end ? key[p] : 0ull;
+    }
     load_tree(splitters + (size_t)si * kMaxV, d, S.t, S.x);
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) S.cnt[b] = 0;
     __syncthreads();
 
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const uint32_t seg_end = sg.begin + sg.size;
-    const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
     // four interleaved descents per thread (Section 3.3: unrolled, interleaved loops)
-    for (uint32_t it = 0; it < (uint32_t)kItems; it += 4) {
-        uint64_t c[4];
+#pragma unroll
+    for (int it = 0; it < kItems; it += 4) {
         uint32_t p[4], node[4];
         bool ok[4];
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             p[u] = wbeg + (it + u) * 32 + lane;
             ok[u] = p[u] < seg_end;
-            c[u] = ok[u] ? key[p[u]] : 0ull;
             node[u] = 1;
         }
         for (uint32_t l = 0; l < d; l++) {
 #pragma unroll
-            for (int u = 0; u < 4; u++) node[u] = 2 * node[u] + (c[u] > S.t[node[u]] ? 1u : 0u);
+            for (int u = 0; u < 4; u++) node[u] = 2 * node[u] + (c[it + u] > S.t[node[u]] ? 1u : 0u);
         }
 #pragma unroll
         for (int u = 0; u < 4; u++) {
             uint32_t r = node[u] - (v + 1);
-            uint32_t b = 2 * r + ((r < v && S.x[r] == c[u]) ? 1u : 0u);
+            uint32_t b = 2 * r + ((r < v && S.x[r] == c[it + u]) ? 1u : 0u);
             if (ok[u]) obuf[p[u]] = (uint16_t)b;
             uint32_t key_b = ok[u] ? b : 0xFFFFu;
             uint32_t peers = __match_any_sync(0xffffffffu, key_b);
@@ -477,10 +500,16 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(uint32_t *a, const uint3
 // ------------------------------------------------------------ k_scatter
 
 struct ScatterSmem {
-    uint32_t tbase[kMaxB + 1];          // global position of each bucket's first string from this tile
-    uint32_t bstart[kMaxB + 1];         // global start of each bucket
-    uint32_t binfo[kMaxB + 1];          // delta | final << 4 | done << 5 | nulpos << 8
-    uint16_t wpos[kWarps][kMaxB + 1];   // per warp: count, then running offset inside the tile's bucket
+    uint32_t tbase[kMaxB + 1];   // global position of each bucket's first string from this tile
+    uint32_t lbase[kMaxB + 1];   // tile-local start of each bucket (exclusive scan of the tile's counts)
+    uint32_t binfo[kMaxB + 1];   // delta | final << 4 | done << 5 | first tile << 6 | nulpos << 8
+    union {
+        uint16_t wpos[kWarps][kMaxB + 1];   // per warp: count, then running offset inside the tile's bucket
+        uint64_t stage[kTile];              // one payload array in tile-local bucket order
+        uint32_t stage32[kTile];
+    } u;
+    uint16_t slot_b[kTile];      // bucket of each tile-local slot
+    uint32_t wsum[kWarps];
 };
 
 enum { MODE_SORT = 0, MODE_CLASSIFY = 1 };
@@ -494,15 +523,30 @@ __device__ __forceinline__ uint32_t bucket_start(const BigSeg &sg, const uint32_
     return b < B ? tile_pos(sg, scan, b, 0) : sg.begin + sg.size;
 }
 
-constexpr int kScatterBatch = 8;   // placements computed, then gathers in flight, per step
+#ifndef SS_SCATTER_BATCH
+#define SS_SCATTER_BATCH 4
+#endif
+#ifndef SS_SCATTER_MINB
+#define SS_SCATTER_MINB 3
+#endif
+constexpr int kScatterBatch = SS_SCATTER_BATCH;   // elements whose reads are in flight together, per thread
 
+// Stable out-of-place redistribution of one tile (Section 3.3, the second hot
+// loop).  Each element's rank inside the tile is fixed first (lanes in order
+// inside a warp, warps in order inside the tile); then each payload array in
+// turn is reordered through shared memory into tile-local bucket order, so that
+// consecutive threads write the consecutive positions of a bucket's run.
 template <int MODE>
-__global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32_t nseg, const ReqDesc *reqs,
-                                                      const uint32_t *idx_in, const uint64_t *soff_in,
-                                                      const uint64_t *key_in, const uint16_t *obuf,
-                                                      const uint32_t *scan, const uint64_t *splitters,
-                                                      uint32_t *idx_out, uint64_t *soff_out, uint64_t *key_out,
-                                                      uint32_t *counters) {
+__global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const BigSeg *__restrict__ segs, uint32_t nseg,
+                                                      const ReqDesc *__restrict__ reqs,
+                                                      const uint32_t *__restrict__ idx_in,
+                                                      const uint64_t *__restrict__ soff_in,
+                                                      const uint64_t *__restrict__ key_in,
+                                                      const uint16_t *__restrict__ obuf,
+                                                      const uint32_t *__restrict__ scan,
+                                                      const uint64_t *__restrict__ splitters,
+                                                      uint32_t *__restrict__ idx_out, uint64_t *__restrict__ soff_out,
+                                                      uint64_t *__restrict__ key_out, uint32_t *counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
     const uint32_t tile = blockIdx.x;
@@ -512,115 +556,195 @@ __global__ void __launch_bounds__(kThreads) k_scatter(const BigSeg *segs, uint32
     const uint32_t d = sg.d, v = (1u << d) - 1, B = 2 * v + 1;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t seg_end = sg.begin + sg.size;
-    const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
+    const uint32_t tbeg = sg.begin + tl * kTile;
+    const uint32_t tcount = min((uint32_t)kTile, seg_end - tbeg);
+    const uint32_t wbeg = tbeg + warp * kWarpSpan;
     const uint64_t *xs = splitters + (size_t)si * kMaxV;
 
+    // every bucket id of this thread in flight at once; kept in registers
+    uint32_t bk[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; u++) {
+        uint32_t p = wbeg + u * 32 + lane;
+        bk[u] = p < seg_end ? (uint32_t)obuf[p] : 0xFFFFu;
+    }
     for (uint32_t k = threadIdx.x; k < kWarps * (kMaxB + 1) / 2; k += blockDim.x)
-        reinterpret_cast<uint32_t *>(&S.wpos[0][0])[k] = 0;
+        reinterpret_cast<uint32_t *>(&S.u.wpos[0][0])[k] = 0;
     __syncthreads();
     // phase A: per-warp bucket counts of its contiguous span
-    for (uint32_t it = 0; it < (uint32_t)kItems; it++) {
-        uint32_t p = wbeg + it * 32 + lane;
-        bool ok = p < seg_end;
-        uint32_t b = ok ? obuf[p] : 0xFFFFu;
-        uint32_t peers = __match_any_sync(0xffffffffu, b);
-        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][b] += (uint16_t)__popc(peers);
+#pragma unroll
+    for (int u = 0; u < kItems; u++) {
+        uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
+        if (bk[u] != 0xFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) S.u.wpos[warp][bk[u]] += (uint16_t)__popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // phase B: each warp's offset inside the tile's part of every bucket; bucket facts
-    for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) {
-        uint32_t run = 0;
+    // phase B: each warp's offset inside the tile's part of every bucket, the
+    // tile's count of every bucket (in lbase for now) and the bucket facts.  The
+    // counter and splitter reads of a half of this thread's buckets go out together.
+    constexpr int kHalf = (kMaxB + 1) / kThreads / 2;
 #pragma unroll
-        for (int w = 0; w < kWarps; w++) {
-            uint32_t c = S.wpos[w][b];
-            S.wpos[w][b] = (uint16_t)run;
-            run += c;
-        }
-        S.tbase[b] = tile_pos(sg, scan, b, tl);
-        if (MODE == MODE_SORT) {
-            uint32_t st = bucket_start(sg, scan, b, B);
-            uint32_t en = bucket_start(sg, scan, b + 1, B);
-            uint32_t r = b >> 1;
-            uint32_t delta, done = 0, np = 0;
-            if (b & 1) {
-                uint64_t xr = xs[r];
-                np = nulpos(xr);
-                done = np < 8;   // equal keys that hold the end of the string: all equal
-                delta = 8;
-            } else {
-                delta = (r == 0 || r == v) ? 0u : lcp8(xs[r - 1], xs[r]);
+    for (int half = 0; half < 2; half++) {
+        uint32_t tb[kHalf], st[kHalf], en[kHalf];
+        uint64_t xr[kHalf], xl[kHalf];
+#pragma unroll
+        for (int k = 0; k < kHalf; k++) {
+            uint32_t b = threadIdx.x + (half * kHalf + k) * kThreads;
+            bool in = b < B;
+            tb[k] = in ? tile_pos(sg, scan, b, tl) : 0u;
+            if (MODE == MODE_SORT) {
+                uint32_t r = b >> 1;
+                st[k] = in ? bucket_start(sg, scan, b, B) : 0u;
+                en[k] = in ? bucket_start(sg, scan, b + 1, B) : 0u;
+                xr[k] = (in && r < v) ? xs[r] : 0ull;
+                xl[k] = (in && !(b & 1) && r > 0 && r < v) ? xs[r - 1] : 0ull;
             }
-            uint32_t fin = (en - st == 1) || done;
-            S.bstart[b] = st;
-            S.binfo[b] = delta | (fin << 4) | (done << 5) | (np << 8);
+        }
+#pragma unroll
+        for (int k = 0; k < kHalf; k++) {
+            uint32_t b = threadIdx.x + (half * kHalf + k) * kThreads;
+            uint32_t run = 0;
+            if (b < B) {
+#pragma unroll
+                for (int w = 0; w < kWarps; w++) {
+                    uint32_t c = S.u.wpos[w][b];
+                    S.u.wpos[w][b] = (uint16_t)run;
+                    run += c;
+                }
+                S.tbase[b] = tb[k];
+                if (MODE == MODE_SORT) {
+                    uint32_t r = b >> 1;
+                    uint32_t delta, done = 0, np = 0;
+                    if (b & 1) {
+                        np = nulpos(xr[k]);
+                        done = np < 8;   // equal keys that hold the end of the string: all equal
+                        delta = 8;
+                    } else {
+                        delta = even_delta(xl[k], xr[k], r, v);
+                    }
+                    uint32_t fin = (en[k] - st[k] == 1) || done;
+                    uint32_t first = tb[k] == st[k];
+                    S.binfo[b] = delta | (fin << 4) | (done << 5) | (first << 6) | (np << 8);
+                }
+            }
+            S.lbase[b] = run;
         }
     }
     __syncthreads();
-    // phase C: stable placement; lanes in order inside the warp, warps in order inside the tile
-    const ReqDesc *Rp = MODE == MODE_SORT ? reqs + sg.req : nullptr;
-    for (uint32_t it = 0; it < (uint32_t)kItems; it += kScatterBatch) {
-        uint32_t pos[kScatterBatch], id[kScatterBatch], bk[kScatterBatch];
-        bool ok[kScatterBatch];
+    // tile-local bucket starts: exclusive scan of the counts, 8 contiguous buckets per thread
+    {
+        constexpr int kPer = (kMaxB + 1) / kThreads;
+        uint32_t c[kPer], sum = 0;
 #pragma unroll
-        for (int u = 0; u < kScatterBatch; u++) {
-            uint32_t p = wbeg + (it + u) * 32 + lane;
-            ok[u] = p < seg_end;
-            bk[u] = ok[u] ? obuf[p] : 0xFFFFu;
-            id[u] = ok[u] ? (MODE == MODE_SORT ? idx_in[p] : p - sg.begin) : 0u;
-        }
+        for (int k = 0; k < kPer; k++) { c[k] = S.lbase[threadIdx.x * kPer + k]; sum += c[k]; }
+        uint32_t incl = sum;
 #pragma unroll
-        for (int u = 0; u < kScatterBatch; u++) {
-            uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
-            uint32_t rank = __popc(peers & lanemask_lt());
-            uint32_t off = ok[u] ? S.wpos[warp][bk[u]] : 0u;
-            pos[u] = ok[u] ? S.tbase[bk[u]] + off + rank : 0u;
-            __syncwarp();
-            if (ok[u] && lane == (uint32_t)(__ffs(peers) - 1)) S.wpos[warp][bk[u]] = (uint16_t)(off + __popc(peers));
-            __syncwarp();
+        for (int o = 1; o < 32; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= (uint32_t)o) incl += y;
         }
-        if (MODE == MODE_CLASSIFY) {
+        if (lane == 31) S.wsum[warp] = incl;
+        __syncthreads();
+        uint32_t base = incl - sum;
+        for (uint32_t w = 0; w < warp; w++) base += S.wsum[w];
+#pragma unroll
+        for (int k = 0; k < kPer; k++) { S.lbase[threadIdx.x * kPer + k] = base; base += c[k]; }
+    }
+    __syncthreads();
+    // ranks: tile-local slot of every element
+    uint32_t lp[kItems];
+#pragma unroll
+    for (int u = 0; u < kItems; u++) {
+        const uint32_t b = bk[u];
+        const bool ok = b != 0xFFFFu;
+        uint32_t peers = __match_any_sync(0xffffffffu, b);
+        uint32_t rank = __popc(peers & lanemask_lt());
+        uint32_t off = ok ? S.u.wpos[warp][b] : 0u;
+        lp[u] = ok ? S.lbase[b] + off + rank : 0u;
+        __syncwarp();
+        if (ok && lane == (uint32_t)(__ffs(peers) - 1)) S.u.wpos[warp][b] = (uint16_t)(off + __popc(peers));
+        __syncwarp();
+        if (ok) S.slot_b[lp[u]] = (uint16_t)b;
+    }
+    __syncthreads();   // wpos is dead from here: its space holds the staged payload
+
+    if (MODE == MODE_SORT) {
+        const ReqDesc &R = reqs[sg.req];
+        // keys: the carried key, or the gather at the new depth
+#pragma unroll
+        for (int it = 0; it < kItems; it += kScatterBatch) {
+            uint32_t id[kScatterBatch], info[kScatterBatch];
+            uint64_t so[kScatterBatch], nk[kScatterBatch];
+#pragma unroll
+            for (int u = 0; u < kScatterBatch; u++) {
+                const uint32_t b = bk[it + u];
+                const uint32_t p = wbeg + (it + u) * 32 + lane;
+                info[u] = b != 0xFFFFu ? S.binfo[b] : 16u;
+                const bool carry = !(info[u] & 16u);
+                const bool gather = carry && (info[u] & 15u) != 0;
+                id[u] = gather ? idx_in[p] : 0u;
+                so[u] = gather ? soff_in[p] : 0ull;
+                nk[u] = (carry && !gather) ? key_in[p] : 0ull;
+            }
 #pragma unroll
             for (int u = 0; u < kScatterBatch; u++)
-                if (ok[u]) idx_out[pos[u] - sg.begin] = id[u];
+                if (!(info[u] & 16u) && (info[u] & 15u) != 0) nk[u] = load_key_o(R, id[u], so[u], sg.depth + (info[u] & 15u));
+#pragma unroll
+            for (int u = 0; u < kScatterBatch; u++)
+                if (!(info[u] & 16u)) S.u.stage[lp[it + u]] = nk[u];
+        }
+        __syncthreads();
+        for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
+            const uint32_t b = S.slot_b[s];
+            if (S.binfo[b] & 16u) continue;
+            const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
+            if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
+            key_out[q] = S.u.stage[s];
+        }
+        __syncthreads();
+        // string offsets
+#pragma unroll
+        for (int u = 0; u < kItems; u++) {
+            const uint32_t b = bk[u];
+            const uint32_t p = wbeg + u * 32 + lane;
+            if (b != 0xFFFFu && !(S.binfo[b] & 16u)) S.u.stage[lp[u]] = soff_in[p];
+        }
+        __syncthreads();
+        for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
+            const uint32_t b = S.slot_b[s];
+            if (S.binfo[b] & 16u) continue;
+            const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
+            if (q < sg.begin || q >= seg_end) continue;
+            soff_out[q] = S.u.stage[s];
+        }
+        __syncthreads();
+    }
+    // string indices; finished strings go straight to the output
+#pragma unroll
+    for (int u = 0; u < kItems; u++) {
+        const uint32_t p = wbeg + u * 32 + lane;
+        if (bk[u] != 0xFFFFu) S.u.stage32[lp[u]] = MODE == MODE_SORT ? idx_in[p] : p - sg.begin;
+    }
+    __syncthreads();
+    for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
+        const uint32_t b = S.slot_b[s];
+        const uint32_t lo = s - S.lbase[b];
+        const uint32_t q = S.tbase[b] + lo;
+        if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
+        const uint32_t id = S.u.stage32[s];
+        if (MODE == MODE_CLASSIFY) {
+            idx_out[q - sg.begin] = id;
             continue;
         }
-        const ReqDesc &R = *Rp;
-        uint64_t nk[kScatterBatch], so[kScatterBatch];
-#pragma unroll
-        for (int u = 0; u < kScatterBatch; u++) {
-            nk[u] = 0;
-            so[u] = 0;
-            if (!ok[u]) continue;
-            uint32_t info = S.binfo[bk[u]];
-            if (info & 16u) continue;   // final: no next key
-            uint32_t p = wbeg + (it + u) * 32 + lane;
-            so[u] = soff_in[p];
-        }
-#pragma unroll
-        for (int u = 0; u < kScatterBatch; u++) {
-            if (!ok[u]) continue;
-            uint32_t info = S.binfo[bk[u]];
-            if (info & 16u) continue;
-            uint32_t delta = info & 15u;
-            uint32_t p = wbeg + (it + u) * 32 + lane;
-            nk[u] = delta == 0 ? key_in[p] : load_key_o(R, id[u], so[u], sg.depth + delta);
-        }
-#pragma unroll
-        for (int u = 0; u < kScatterBatch; u++) {
-            if (!ok[u]) continue;
-            uint32_t info = S.binfo[bk[u]];
-            uint32_t q = pos[u];
-            if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
-            if (info & 16u) {
-                uint32_t local = q - R.base;
-                R.perm_out[local] = id[u];
-                if ((info & 32u) && q > S.bstart[bk[u]]) R.lcp_out[local] = sg.depth + (info >> 8);
-            } else {
-                idx_out[q] = id[u];
-                soff_out[q] = so[u];
-                key_out[q] = nk[u];
-            }
+        const uint32_t info = S.binfo[b];
+        if (info & 16u) {
+            const ReqDesc &R = reqs[sg.req];
+            const uint32_t local = q - R.base;
+            R.perm_out[local] = id;
+            // all equal and complete: every string but the bucket's first has the whole key in common
+            if ((info & 32u) && (!(info & 64u) || lo > 0)) R.lcp_out[local] = sg.depth + (info >> 8);
+        } else {
+            idx_out[q] = id;
         }
     }
 }
@@ -661,7 +785,7 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
         if (has_zero(xs[r])) return;   // all equal and complete: placed by k_scatter
         delta = 8;
     } else {
-        delta = (r == 0 || r == v) ? 0u : lcp8(xs[r - 1], xs[r]);
+        delta = even_delta(r > 0 ? xs[r - 1] : 0ull, r < v ? xs[r] : 0ull, r, v);
     }
     uint32_t depth = sg.depth + delta;
     if (size > kSmallMax) {

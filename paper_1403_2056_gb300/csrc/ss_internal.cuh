@@ -20,13 +20,26 @@ namespace ss {
 // ---------------------------------------------------------------- tunables
 constexpr int kThreads = 256;                  // CTA size of the tile kernels
 constexpr int kWarps = kThreads / 32;
-constexpr int kItems = 16;                     // elements per thread in a tile
+#ifndef SS_ITEMS
+#define SS_ITEMS 16
+#endif
+#ifndef SS_MAX_D
+#define SS_MAX_D 10
+#endif
+constexpr int kItems = SS_ITEMS;               // elements per thread in a tile
 constexpr int kTile = kThreads * kItems;       // 4096 elements per tile
 constexpr int kWarpSpan = kTile / kWarps;      // 512 contiguous elements per warp
-constexpr int kMaxD = 10;                      // tree depth: v = 2^d - 1 <= 1023
+constexpr int kMaxD = SS_MAX_D;                // tree depth: v = 2^d - 1 <= 1023
 constexpr int kMaxV = (1 << kMaxD) - 1;
 constexpr int kMaxB = 2 * kMaxV + 1;           // 2047 buckets
-constexpr uint32_t kSmallMax = 4096;           // segments up to this size are base cases
+#ifndef SS_SMALL_MAX
+#define SS_SMALL_MAX 4096
+#endif
+#ifndef SS_CHILD_TARGET
+#define SS_CHILD_TARGET 1024
+#endif
+constexpr uint32_t kSmallMax = SS_SMALL_MAX;   // segments up to this size are base cases
+constexpr uint32_t kChildTarget = SS_CHILD_TARGET;   // tree depth aims at children of about this size
 constexpr uint32_t kTinyMax = 32;              // base cases handled by one warp
 // base-case size classes: class 0 (2..32 strings) one warp; classes 1..3 one
 // CTA of 32, 128, 512 threads holding up to 256, 1024, 4096 strings
@@ -156,18 +169,15 @@ __device__ __forceinline__ uint64_t load_key_o(const ReqDesc &R, uint32_t i, uin
     uintptr_t a = (uintptr_t)p;
     const uint64_t *w = (const uint64_t *)(a & ~(uintptr_t)7);
     uint32_t sh = (uint32_t)(a & 7) * 8;
+    // a known length decides the second word before the first arrives: both in flight
+    const bool known = rem != ~0ULL;
+    uint64_t w1 = (sh && known && rem > (uint64_t)(8 - (a & 7))) ? __ldg(w + 1) : 0ull;
     uint64_t w0 = __ldg(w);
     uint64_t v = w0 >> sh;   // memory bytes p[0 .. 8 - (a&7)) in the low bytes
     if (sh) {
-        bool need;
-        if (rem == ~0ULL) {
-            // terminated: continue only if no 0 byte among the valid bytes
-            uint64_t valid = v | (~0ULL << (64 - sh));
-            need = !has_zero(valid);
-        } else {
-            need = rem > (uint64_t)(8 - (a & 7));
-        }
-        if (need) v |= __ldg(w + 1) << (64 - sh);
+        // terminated: continue only if no 0 byte among the valid bytes
+        if (!known && !has_zero(v | (~0ULL << (64 - sh)))) w1 = __ldg(w + 1);
+        v |= w1 << (64 - sh);
     }
     uint64_t key = bswap64(v);
     if (rem < 8) key &= ~0ULL << (8 * (8 - rem));
