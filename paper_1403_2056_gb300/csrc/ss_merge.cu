@@ -3,14 +3,19 @@
 //
 // The paper merges K runs with one LCP-aware tournament tree per job and
 // splits jobs by LCP minima (Section 4.3).  On the GPU the K-way merge is
-// ceil(log2 K) rounds of pairwise merges; inside a round the output of every
-// pair is cut into fixed chunks of kMergeItems strings by merge path (binary
-// search on the cross diagonal, full string comparisons), and each thread
-// runs the binary LCP-merge over its chunk.  The LCPs that start a chunk are
-// recomputed at the cut: one side's is the run's own LCP entry, the other is
-// one string comparison.  After that, comparisons whose LCPs differ cost no
-// string access at all (cases 2 and 3 of LCP-Compare); only equal LCPs read
-// characters, 8 at a time from the known common prefix on.
+// ceil(log2 K) rounds of pairwise merges.  Inside a round the output of every
+// pair is cut by merge path (binary search on the cross diagonal, full string
+// comparisons) at every kCoarse outputs, with the characters each window's
+// strings share; then every chunk of kMergeItems outputs gets its start (the
+// search inside its window, from the shared prefix, and the LCPs of both
+// fronts with the string before the chunk: one side's is the run's own LCP
+// entry, the other is one string comparison).  The merge proper runs per CTA
+// window of kMergeTile outputs: the window's LCPs and cached characters are
+// staged in shared memory, each thread runs the binary LCP-merge over its
+// chunk there, and the CTA writes the outputs with coalesced stores.
+// Comparisons whose LCPs differ cost no string access at all (cases 2 and 3
+// of LCP-Compare); equal LCPs first try the cached characters, and only then
+// read characters, 8 at a time from the known common prefix on.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -23,7 +28,10 @@
 
 namespace ss {
 
-constexpr uint32_t kMergeItems = 16;   // outputs per thread
+#ifndef SS_MERGE_ITEMS
+#define SS_MERGE_ITEMS 16
+#endif
+constexpr uint32_t kMergeItems = SS_MERGE_ITEMS;   // outputs per thread
 constexpr uint32_t kCoarse = 256;      // outputs per merge-path window
 
 // full comparison of strings a and b from depth h on (both share h characters),
@@ -41,6 +49,7 @@ __device__ __forceinline__ int str_cmp_from(const ReqDesc &S, uint32_t a, uint64
         h += 16;
     }
 }
+
 
 // pair (2p, 2p+1) of the round's runs; an unpaired last run has B empty.
 // With a table of string offsets aligned to the runs (Ao/Bo) every string
@@ -335,6 +344,218 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
     }
 }
 
+#ifndef SS_MERGE_TILE_THREADS
+#define SS_MERGE_TILE_THREADS 128
+#endif
+constexpr uint32_t kMergeTileThreads = SS_MERGE_TILE_THREADS;
+constexpr uint32_t kMergeTile = kMergeTileThreads * kMergeItems;   // outputs per CTA window
+static_assert(kMergeTile % kCoarse == 0, "a CTA window is a whole number of merge-path windows");
+static_assert(kMergeTile <= 65536, "tile-local sources are 16-bit");
+
+struct MergeStart {   // where a thread's outputs start: strings taken from A, front LCPs
+    uint32_t i, ha, hb, pad;
+};
+
+// window w of pair p: outputs [d0, d1) of the pair, C entries k0 .. k1
+struct MergeWindow {
+    uint32_t p, d0, d1, k0, k1;
+};
+
+__device__ __forceinline__ MergeWindow merge_window(const uint32_t *wbase, uint32_t npairs, uint32_t len_of_pair,
+                                                    uint32_t p, uint32_t w) {
+    MergeWindow mw;
+    mw.p = p;
+    mw.d0 = w * kMergeTile;
+    mw.d1 = min(mw.d0 + kMergeTile, len_of_pair);
+    const uint32_t nent = (len_of_pair + kCoarse - 1) / kCoarse;   // C holds diagonals min(k kCoarse, len), k = 0..nent
+    mw.k0 = mw.d0 / kCoarse;
+    mw.k1 = mw.d1 == len_of_pair ? nent : mw.d1 / kCoarse;
+    return mw;
+}
+
+// Start of every thread's kMergeItems outputs, one thread per chunk of a
+// window (same grid shape as k_merge_tile): the merge-path search inside the
+// kCoarse window of its diagonal, from the window's shared prefix, and the
+// LCPs of both fronts with the string output just before the chunk.  These are
+// the string accesses of a round; they run here at full occupancy, apart from
+// the staged merge.
+__global__ void __launch_bounds__(kMergeTileThreads) k_merge_starts(
+    ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R, const uint32_t *rbase,
+    const uint32_t *wbase, uint32_t npairs, const Coarse *C, const uint32_t *cbase, const uint64_t *in_off,
+    MergeStart *starts) {
+    const uint32_t p = pair_of_entry(wbase, npairs, blockIdx.x);
+    const PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
+    const uint32_t na = v.na, nb = v.nb, len = na + nb;
+    const MergeWindow mw = merge_window(wbase, npairs, len, p, blockIdx.x - wbase[p]);
+    const uint32_t diag = mw.d0 + threadIdx.x * kMergeItems;
+    if (diag >= mw.d1) return;
+    uint32_t lo = diag > nb ? diag - nb : 0, hi = min(diag, na);
+    const uint32_t k = diag / kCoarse, e = cbase[p] + k, dc = k * kCoarse;
+    const uint32_t i0 = C[e].i, j0 = dc - i0;
+    uint32_t i1 = na, j1 = nb, hw = 0, i;
+    bool win = true;
+    if (dc == diag) {
+        i = i0;
+        win = false;   // exact cut: no search, no shared prefix needed
+    } else {
+        const uint32_t dce = min(dc + kCoarse, len);
+        i1 = C[e + 1].i;
+        j1 = dce - i1;
+        hw = C[e].h;
+        lo = max(lo, max(i0, diag > j1 ? diag - j1 : 0u));
+        hi = min(hi, min(i1, diag - j0));
+        i = path_search(S, v, diag, lo, hi, hw);
+    }
+    const uint32_t j = diag - i;
+    auto inA = [&](uint32_t x) { return win && x >= i0 && x < i1; };
+    auto inB = [&](uint32_t y) { return win && y >= j0 && y < j1; };
+    uint32_t ha = 0, hb = 0;
+    if (diag > 0) {
+        bool last_is_b;
+        if (i == 0) last_is_b = true;
+        else if (j == 0) last_is_b = false;
+        else {
+            uint32_t l;
+            uint32_t h0 = (inA(i - 1) && inB(j - 1)) ? hw : 0u;
+            last_is_b = str_cmp_from(S, v.A(i - 1), v.OA(i - 1), v.B(j - 1), v.OB(j - 1), h0, &l) <= 0;   // ties: A then B
+        }
+        const uint32_t prev = last_is_b ? v.B(j - 1) : v.A(i - 1);
+        const uint64_t prev_o = last_is_b ? v.OB(j - 1) : v.OA(i - 1);
+        const bool prev_in = last_is_b ? inB(j - 1) : inA(i - 1);
+        if (i < na) {
+            if (!last_is_b) ha = v.HA[i];
+            else { uint32_t l; str_cmp_from(S, prev, prev_o, v.A(i), v.OA(i), (prev_in && inA(i)) ? hw : 0u, &l); ha = l; }
+        }
+        if (j < nb) {
+            if (last_is_b) hb = v.HB[j];
+            else { uint32_t l; str_cmp_from(S, prev, prev_o, v.B(j), v.OB(j), (prev_in && inB(j)) ? hw : 0u, &l); hb = l; }
+        }
+    }
+    starts[blockIdx.x * kMergeTileThreads + threadIdx.x] = MergeStart{i, ha, hb, 0u};
+}
+
+struct MergeTileSmem {
+    uint32_t lcp[kMergeTile];    // the window's run entries: A's, then B's
+    uint64_t ck[kMergeTile];
+    uint32_t ckd[kMergeTile];
+    uint32_t olcp[kMergeTile];   // per output: LCP with the output before it
+    uint16_t src[kMergeTile];    // per output: which staged entry it is
+};
+
+// One round of pairwise merges, one CTA per window of kMergeTile outputs of a
+// pair (windows do not straddle pairs; wbase[p] = first window of pair p).  The
+// window's run entries (LCPs and cached characters) are staged in shared memory
+// with coalesced reads; from its start (k_merge_starts) each thread runs the
+// binary LCP-merge (Algorithm 3) over kMergeItems outputs out of shared memory
+// and records which entry each output is; the CTA then writes all outputs with
+// coalesced stores.  Only the case-1 comparisons that the cached characters
+// leave open read strings here.
+__global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
+    ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R, const uint32_t *rbase,
+    const uint32_t *wbase, uint32_t npairs, uint32_t *out_perm, uint32_t *out_lcp, const Coarse *C,
+    const uint32_t *cbase, const MergeStart *starts, const uint64_t *in_off, uint64_t *out_off, const uint64_t *ck,
+    const uint32_t *ckd, uint64_t *out_ck, uint32_t *out_ckd) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    MergeTileSmem &T = *reinterpret_cast<MergeTileSmem *>(smem_raw);
+    const uint32_t p = pair_of_entry(wbase, npairs, blockIdx.x);
+    const PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
+    const uint32_t a0 = v.a0, na = v.na, nb = v.nb, len = na + nb;
+    const MergeWindow mw = merge_window(wbase, npairs, len, p, blockIdx.x - wbase[p]);
+    const uint32_t d0 = mw.d0, d1 = mw.d1;
+    const uint32_t I0 = C[cbase[p] + mw.k0].i, I1 = C[cbase[p] + mw.k1].i;
+    const uint32_t J0 = d0 - I0, J1 = d1 - I1;
+    const uint32_t nA = I1 - I0, nW = d1 - d0;
+    const uint32_t dl = threadIdx.x * kMergeItems;
+    MergeStart ms{0u, 0u, 0u, 0u};
+    if (dl < nW) ms = starts[blockIdx.x * kMergeTileThreads + threadIdx.x];
+    // stage the window's entries
+    for (uint32_t x = threadIdx.x; x < nW; x += kMergeTileThreads) {
+        const uint32_t g = x < nA ? a0 + I0 + x : a0 + na + J0 + (x - nA);   // run-aligned position
+        T.lcp[x] = in_lcp[g];
+        T.ck[x] = ck ? ck[g] : 0ull;
+        T.ckd[x] = ck ? ckd[g] : ~0u;
+    }
+    __syncthreads();
+    if (dl < nW) {
+        const uint32_t diag = d0 + dl;
+        const uint32_t stop = min(dl + kMergeItems, nW);
+        uint32_t i = ms.i, j = diag - ms.i, ha = ms.ha, hb = ms.hb;
+        // fronts' cached characters (depth kd, ~0: none)
+        uint32_t kdA = ~0u, kdB = ~0u;
+        uint64_t kA = 0, kB = 0;
+        if (i < I1) { kdA = T.ckd[i - I0]; kA = T.ck[i - I0]; }
+        if (j < J1) { kdB = T.ckd[nA + j - J0]; kB = T.ck[nA + j - J0]; }
+        for (uint32_t s = dl; s < stop; s++) {
+            // the window holds exactly the entries its outputs take: a side past
+            // its part of the window is exhausted here
+            const bool hasA = i < I1, hasB = j < J1;
+            bool take_b;
+            uint32_t hp = 0;
+            const bool both = hasA && hasB;
+            if (!both) {
+                take_b = !hasA;
+            } else if (ha == hb) {   // case 1: compare characters from the common LCP on
+                const uint32_t h = ha;
+                bool decided = false;
+                if (kdA <= h && kdB <= h && h - kdA < 8 && h - kdB < 8) {
+                    const uint32_t sa = h - kdA, sb = h - kdB;
+                    const uint64_t wa = kA << (8 * sa), wb = kB << (8 * sb);
+                    const uint32_t nk = 8 - max(sa, sb);   // bytes known for both from h on
+                    const uint64_t mask = ~0ull << (64 - 8 * nk);
+                    const uint64_t x = (wa ^ wb) & mask;
+                    if (x) {
+                        hp = h + (uint32_t)(__clzll(x) >> 3);
+                        take_b = (wa & mask) > (wb & mask);
+                        decided = true;
+                    } else {
+                        const uint64_t z = zero_bytes(wa) & mask;   // both end inside the overlap: equal
+                        if (z) {
+                            hp = h + (uint32_t)(__clzll(z) >> 3);
+                            take_b = false;
+                            decided = true;
+                        }
+                    }
+                }
+                if (!decided) take_b = str_cmp_from(S, v.A(i), v.OA(i), v.B(j), v.OB(j), h, &hp) > 0;
+            } else if (ha < hb) {    // case 2: B is smaller
+                take_b = true;
+                hp = ha;
+            } else {                 // case 3: A is smaller
+                take_b = false;
+                hp = hb;
+            }
+            if (!take_b) {
+                T.src[s] = (uint16_t)(i - I0);
+                T.olcp[s] = diag + (s - dl) == 0 ? 0u : ha;
+                i++;
+                ha = i < I1 ? T.lcp[i - I0] : 0u;
+                if (both) hb = hp;
+                if (i < I1) { kdA = T.ckd[i - I0]; kA = T.ck[i - I0]; } else kdA = ~0u;
+            } else {
+                T.src[s] = (uint16_t)(nA + j - J0);
+                T.olcp[s] = diag + (s - dl) == 0 ? 0u : hb;
+                j++;
+                hb = j < J1 ? T.lcp[nA + j - J0] : 0u;
+                if (both) ha = hp;
+                if (j < J1) { kdB = T.ckd[nA + j - J0]; kB = T.ck[nA + j - J0]; } else kdB = ~0u;
+            }
+        }
+    }
+    __syncthreads();
+    // coalesced write of the window's outputs
+    for (uint32_t s = threadIdx.x; s < nW; s += kMergeTileThreads) {
+        const uint32_t x = T.src[s];
+        const bool fromA = x < nA;
+        const uint32_t g = fromA ? a0 + I0 + x : a0 + na + J0 + (x - nA);
+        const uint32_t o = a0 + d0 + s;
+        const uint32_t id = in_perm[g] + (fromA ? v.baseA : v.baseB);
+        out_perm[o] = id;
+        out_lcp[o] = T.olcp[s];
+        if (out_off) out_off[o] = in_off ? in_off[g] : __ldg(S.offsets + id);
+        if (out_ck) { out_ck[o] = T.ck[x]; out_ckd[o] = T.ckd[x]; }
+    }
+}
+
 // a single run: copy with its index base added; its first LCP becomes 0
 __global__ void k_copy_run(const uint32_t *in_perm, const uint32_t *in_lcp, uint32_t base, uint32_t total,
                            uint32_t *out_perm, uint32_t *out_lcp) {
@@ -361,7 +582,10 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
     const size_t max_entries = (size_t)total / kCoarse + 2ull * (K + 1) + 2;
     const size_t a64 = 63;
     const size_t tot64 = ((size_t)total + a64) & ~a64;
-    size_t bytes = 4ull * 8 * tot64 + 4ull * 4 * tot64 + 4ull * (4 * (K + 2) + 64) + sizeof(Coarse) * max_entries + 4096;
+    // thread starts: one per kMergeItems outputs, at most one partial window per pair
+    const size_t max_starts = ((size_t)total / kMergeTile + K + 2) * kMergeTileThreads;
+    size_t bytes = 4ull * 8 * tot64 + 4ull * 4 * tot64 + 4ull * (4 * (K + 2) + 64) + sizeof(Coarse) * max_entries +
+                   sizeof(MergeStart) * max_starts + 4096;
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
     if (e) {
@@ -378,6 +602,7 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
     uint32_t *tmp_lcp = tmp_perm + tot64;
     uint32_t *d_rb = tmp_lcp + tot64;   // rb[R+1], bases[R], cbase[pairs]
     Coarse *d_coarse = (Coarse *)(d_rb + ((4 * (K + 2) + 63) & ~63u));
+    MergeStart *d_starts = (MergeStart *)(d_coarse + ((max_entries + 63) & ~(size_t)63));
     int rc = SS_OK;
     uint32_t *stage = (uint32_t *)host_staging(sizeof(uint32_t) * 4 * (K + 2));
     do {
@@ -403,16 +628,20 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             memcpy(stage, rb.data(), sizeof(uint32_t) * (R + 1));
             if (round == 1) memcpy(stage + (R + 1), rbase.data(), sizeof(uint32_t) * R);
             uint32_t *cb = stage + (2 * R + 1);
-            uint32_t nentries = 0;
+            uint32_t *wb = cb + npairs;
+            uint32_t nentries = 0, nwin = 0;
             for (uint32_t p = 0; p < npairs; p++) {
                 uint32_t len = rb[std::min(2 * p + 2, R)] - rb[2 * p];
                 cb[p] = nentries;
                 nentries += (len + kCoarse - 1) / kCoarse + 1;
+                wb[p] = nwin;
+                nwin += (len + kMergeTile - 1) / kMergeTile;
             }
-            size_t cp = sizeof(uint32_t) * (2 * R + 1 + npairs);
+            size_t cp = sizeof(uint32_t) * (2 * R + 1 + 2 * npairs);
             if ((e = cudaMemcpyAsync(d_rb, stage, cp, cudaMemcpyHostToDevice, st))) break;
             const uint32_t *bases = round == 1 ? d_rb + (R + 1) : nullptr;
             const uint32_t *d_cb = d_rb + (2 * R + 1);
+            const uint32_t *d_wb = d_cb + npairs;
             const uint64_t *src_o = off_buf[(round - 1) & 1];
             uint64_t *dst_o = last ? nullptr : off_buf[round & 1];
             const uint64_t *src_ck = ck_buf[(round - 1) & 1];
@@ -428,10 +657,11 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
                 set, src_p, src_l, src_o, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
             SS_LAUNCH_U("merge_windows", st, nentries, k_merge_windows<<<(nentries + 127) / 128, 128, 0, st>>>(
                 set, src_p, src_l, src_o, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
-            uint32_t threads = (total + kMergeItems - 1) / kMergeItems;
-            SS_LAUNCH_U("merge_round", st, total, k_merge_round<<<(threads + 255) / 256, 256, 0, st>>>(
-                set, src_p, src_l, d_rb, R, bases, total, dst_p, dst_l, d_coarse, d_cb, src_o, dst_o, src_ck, src_ckd,
-                dst_ck, dst_ckd));
+            SS_LAUNCH_U("merge_starts", st, total, k_merge_starts<<<nwin, kMergeTileThreads, 0, st>>>(
+                set, src_p, src_l, d_rb, R, bases, d_wb, npairs, d_coarse, d_cb, src_o, d_starts));
+            SS_LAUNCH_U("merge_round", st, total, k_merge_tile<<<nwin, kMergeTileThreads, sizeof(MergeTileSmem), st>>>(
+                set, src_p, src_l, d_rb, R, bases, d_wb, npairs, dst_p, dst_l, d_coarse, d_cb, d_starts, src_o, dst_o,
+                src_ck, src_ckd, dst_ck, dst_ckd));
             if ((e = cudaGetLastError())) break;
             // the staging buffer is reused next round: wait for the copy
             if ((e = cudaStreamSynchronize(st))) break;
