@@ -39,14 +39,19 @@ METRIC = "strings/s and D-GB/s vs HBM roofline (bit-exact); batched p50/p99 vs p
 BYTES_PER_UNIT = {
     "init": 8 + 8 + 4 + 8,           # offset read, key gather, index + key write
     "classify": 8 + 2,               # key read, bucket write
-    "scatter": 2 + 4 + 8 + 4 + 8,    # bucket + index read, next-key gather, index + key write
+    # bucket id, index, string offset, carried key read; index, offset, key written
+    # (the gather of a key at a new depth is extra: it is counted in the whole-sort B_alg)
+    "scatter": 2 + 4 + 8 + 8 + 4 + 8 + 8,
     "small_warp": 4 + 8 + 4 + 4,     # index + key read, perm + lcp write
     "small_cta256": 4 + 8 + 4 + 4,
     "small_cta1024": 4 + 8 + 4 + 4,
     "small_cta4096": 4 + 8 + 4 + 4,
     "boundary": 4 + 4 + 8 + 8 + 4,   # two perm reads, two key gathers, lcp write
-    "merge_round": 4 + 4 + 8 + 4 + 4 + 8,   # perm + lcp + offset read, perm + lcp + offset write
-    "run_prep": 4 + 4 + 8 + 8 + 8,   # perm + lcp read, offset gather, offset + cached-key write
+    # per output: perm, lcp, offset, cached key + its depth read (28 B); written again in a
+    # round that feeds another (28 B), perm + lcp only in the last round (8 B): mean of the
+    # two rounds of a 4-way merge
+    "merge_round": (28 + 28 + 28 + 8) / 2,
+    "run_prep": 4 + 4 + 8 + 8 + 8 + 4,   # perm + lcp read, offset gather, offset + cached key + depth write
     "copy_run": 16,
     "scan_reduce": 4,
     "scan_down": 8,
@@ -375,8 +380,8 @@ def main():
         try:
             with open(tp) as f:
                 tj = json.load(f)
-            if tj.get("kernel") == dom and tj.get("source_hash") == _source_hash():
-                traffic = tj.get("bytes_per_launch")
+            if tj.get("source_hash") == _source_hash():
+                traffic = tj.get("bytes_per_launch", {}).get(dom)
         except Exception:
             traffic = None
     roofline = None
