@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-extra", action="store_true", help="skip the DNA 20M and no-LCP 64Mi sorts")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
+    ap.add_argument("--batched-requests", type=int, default=4096)
     return ap.parse_args()
 
 
@@ -131,6 +133,86 @@ def other_workloads(P, torch, dev, stream, peak):
                                          "achieved_gbs": ach, "frac": (ach / peak) if ach else None}}
         del chars, offsets, perm, lcp
         torch.cuda.empty_cache()
+    return out
+
+
+def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
+    """The batched configuration: nreq independent requests of log-uniform sizes
+    1,000..1,000,000 strings, generators random / URL-like / DNA-like by request
+    number mod 3, all arriving at once.  Batched = one ss_sort_batch call for all
+    of them; plain = one ss_sort call per request, in arrival order.  Latency of a
+    request = its completion time from the common arrival (the batch completes
+    every request at its end).  Each request is a contiguous slice of a seeded
+    pool of its generator (own offsets, shared bytes)."""
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    pools = [W.random_lower(2_000_000, seed=seed * 10 + 0), W.url_like(2_000_000, seed=seed * 10 + 1),
+             W.dna_windows(2_000_000, 40_000_000, 100, seed=seed * 10 + 2)]
+    dpools = [(torch.from_numpy(p.chars).to(dev), torch.from_numpy(p.offsets.view(np.int64)).to(dev), p) for p in pools]
+    sizes = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(1e6), nreq))).astype(np.int64)
+    starts = [int(rng.integers(0, pools[r % 3].n - int(sizes[r]) + 1)) for r in range(nreq)]
+    total = int(sizes.sum())
+    base = np.concatenate([[0], np.cumsum(sizes)])
+    perm_b = torch.empty(total, dtype=torch.int32, device=dev)
+    lcp_b = torch.empty(total, dtype=torch.int32, device=dev)
+    perm_p = torch.empty(total, dtype=torch.int32, device=dev)
+    lcp_p = torch.empty(total, dtype=torch.int32, device=dev)
+
+    def req(r, perm, lcp):
+        chars, offs, pool = dpools[r % 3]
+        n = int(sizes[r])
+        return dict(chars=chars, offsets=offs[starts[r]:starts[r] + n], lengths=None, fixed_len=pool.fixed_len, n=n,
+                    perm_out=perm[int(base[r]):int(base[r + 1])], lcp_out=lcp[int(base[r]):int(base[r + 1])])
+
+    breqs = [req(r, perm_b, lcp_b) for r in range(nreq)]
+    preqs = [req(r, perm_p, lcp_p) for r in range(nreq)]
+    P.ss_sort_batch(breqs, stream=stream)   # warm-up (pool growth, attributes)
+    torch.cuda.synchronize(dev)
+    bt = []
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.ss_sort_batch(breqs, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        bt.append(e0.elapsed_time(e1))
+    for r in range(0, nreq, 97):   # warm-up of the one-request path
+        q = preqs[r]
+        if q["fixed_len"]:
+            P.ss_sort_ex(q["chars"], q["offsets"], None, q["fixed_len"], q["n"], q["perm_out"], q["lcp_out"], stream=stream)
+        else:
+            P.ss_sort(q["chars"], q["offsets"], q["n"], q["perm_out"], q["lcp_out"], stream=stream)
+    torch.cuda.synchronize(dev)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(nreq + 1)]
+    ev[0].record(stream)
+    for r in range(nreq):
+        q = preqs[r]
+        if q["fixed_len"]:
+            P.ss_sort_ex(q["chars"], q["offsets"], None, q["fixed_len"], q["n"], q["perm_out"], q["lcp_out"], stream=stream)
+        else:
+            P.ss_sort(q["chars"], q["offsets"], q["n"], q["perm_out"], q["lcp_out"], stream=stream)
+        ev[r + 1].record(stream)
+    torch.cuda.synchronize(dev)
+    done = np.array([ev[0].elapsed_time(ev[r + 1]) for r in range(nreq)])
+    service = np.diff(np.concatenate([[0.0], done]))
+    equal = bool(torch.equal(perm_b, perm_p) and torch.equal(lcp_b, lcp_p))
+    tb = float(np.median(bt))
+    tp = float(done[-1])
+    out = {
+        "workload": f"{nreq} requests, sizes log-uniform 1,000..1,000,000 strings, generators random/URL-like/DNA-like by request mod 3, seed {seed}; all arrive at once",
+        "requests": nreq, "strings": total,
+        "batched": {"ms": tb, "strings_per_s": total / (tb / 1e3), "latency_p50_ms": tb, "latency_p99_ms": tb,
+                    "launches": "one ss_sort_batch call"},
+        "plain": {"ms": tp, "strings_per_s": total / (tp / 1e3),
+                  "latency_p50_ms": float(np.percentile(done, 50)), "latency_p99_ms": float(np.percentile(done, 99)),
+                  "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
+                  "launches": "one ss_sort per request, in arrival order"},
+        "speedup": tp / tb,
+        "outputs_equal": equal,
+    }
+    del perm_b, lcp_b, perm_p, lcp_p, dpools
+    torch.cuda.empty_cache()
     return out
 
 
@@ -439,6 +521,8 @@ def main():
 
     if rank == 0 and not args.no_extra:
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)
+    if rank == 0 and not args.no_batched:
+        line["batched"] = batched_vs_plain(P, torch, dev, stream, nreq=args.batched_requests)
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
