@@ -216,6 +216,19 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
     return out
 
 
+def aggregate(dist, ms, units, device):
+    """Replicas (one process per GPU, no collective on the data path): the job's
+    time is the slowest rank's, its work the sum of all ranks' units."""
+    if dist is None:
+        return ms, units
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(round(u.item()))
+
+
 def load_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -433,15 +446,11 @@ def main():
     ck = clocks.stop()
     P.profile_enable(False)
     prof = P.profile_read()
-    ms = ev0.elapsed_time(ev1) / args.steps
-    if dist is not None:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms, job_strings = aggregate(dist, ev0.elapsed_time(ev1) / args.steps, n, dev)
 
     lcp_h = lcp.cpu().numpy().view(np.uint32)
     D, balg = d_and_balg(lcp_h)
-    value = n * world / (ms / 1e3)
+    value = job_strings / (ms / 1e3)
 
     # dominant kernel and its roofline
     peak, peak_kind = load_peaks()
@@ -481,7 +490,7 @@ def main():
         "config": {"workload": workload_name(n, K), "n": n, "N_bytes": int(ss.chars.nbytes),
                    "mean_len": ss.meta.get("mean_len"), "runs": K, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (chars 0.5 GB + offsets 80 MB per step)"},
-        "d_gb_per_s": D * world / (ms / 1e3) / 1e9, "D": D,
+        "d_gb_per_s": D * (job_strings // n) / (ms / 1e3) / 1e9, "D": D,
         "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
                                 "frac": balg / (ms / 1e3) / 1e9 / peak},
         "sort_only": {"ms": ms_sort, "value": n / (ms_sort / 1e3), "unit": "strings/s",
@@ -508,12 +517,8 @@ def main():
         for _ in range(reps):
             P.ss_sort_host(hc, ho, None, 0, hp, hl, runs=K, stream=stream)
         torch.cuda.synchronize(dev)
-        e2e_ms = (time.perf_counter() - t0) / reps * 1e3
-        if dist is not None:
-            t = torch.tensor([e2e_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms = float(t.item())
-        line["e2e"] = {"value": n * world / (e2e_ms / 1e3), "unit": "strings/s",
+        e2e_ms, e2e_strings = aggregate(dist, (time.perf_counter() - t0) / reps * 1e3, n, dev)
+        line["e2e"] = {"value": e2e_strings / (e2e_ms / 1e3), "unit": "strings/s",
                        "h2d_bytes_per_step": int(ss.chars.nbytes + 8 * n), "d2h_bytes_per_step": int(8 * n),
                        "ms_per_step": e2e_ms}
         same = np.array_equal(hp.numpy(), perm.cpu().numpy()) and np.array_equal(hl.numpy(), lcp.cpu().numpy())
