@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-extra", action="store_true", help="skip the DNA 20M and no-LCP 64Mi sorts")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batched-requests", type=int, default=4096)
+    ap.add_argument("--no-serving", action="store_true", help="skip the served-vs-plain measurement")
+    ap.add_argument("--serving-requests", type=int, default=2000)
     return ap.parse_args()
 
 
@@ -214,6 +216,89 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
     del perm_b, lcp_b, perm_p, lcp_p, dpools
     torch.cuda.empty_cache()
     return out
+
+
+def serving_vs_plain(P, torch, dev, url_chars, url_offsets, capacity_sps, nreq=2000, load=0.7, seed=5, workers=3):
+    """The serving configuration: requests of log-uniform sizes 1,000..4,000,000
+    strings (generators random / URL-like / DNA-like by request mod 3) arrive as
+    a Poisson stream whose offered load is `load` times the batched capacity
+    measured before (strings/s), plus one no-LCP job of 64 Mi strings in the
+    middle.  Served = the continuous-batching server (`workers` streams, 120 GB
+    budget); plain = the same stream through a server with one worker and
+    batches of one request (one request per launch sequence).  Latency =
+    completion - arrival, on the server's clock."""
+    import threading
+    import workloads as W
+    rng = np.random.default_rng(seed)
+    lower = W.random_lower(4_000_000, seed=seed * 10)
+    dna = W.dna_windows(4_000_000, 80_000_000, 100, seed=seed * 10 + 2)
+    nolcp = W.no_lcp(n=64 * 1024 * 1024, seed=5)
+    pools = [(torch.from_numpy(lower.chars).to(dev), torch.from_numpy(lower.offsets.view(np.int64)).to(dev), 0,
+              lower.n),
+             (url_chars, url_offsets, 0, int(url_offsets.shape[0])),
+             (torch.from_numpy(dna.chars).to(dev), torch.from_numpy(dna.offsets.view(np.int64)).to(dev), 100, dna.n)]
+    big = (torch.from_numpy(nolcp.chars).to(dev), torch.from_numpy(nolcp.offsets.view(np.int64)).to(dev), 0, nolcp.n)
+    sizes = np.floor(np.exp(rng.uniform(np.log(1e3), np.log(4e6), nreq))).astype(np.int64)
+    src = [pools[r % 3] for r in range(nreq)]
+    starts = [int(rng.integers(0, src[r][3] - int(sizes[r]) + 1)) for r in range(nreq)]
+    mid = nreq // 2
+    sizes = np.insert(sizes, mid, big[3])
+    src.insert(mid, big)
+    starts.insert(mid, 0)
+    nall = len(sizes)
+    total = int(sizes.sum())
+    rate = load * capacity_sps / float(sizes.mean())   # requests per second
+    gaps = rng.exponential(1.0 / rate, nall)
+    base = np.concatenate([[0], np.cumsum(sizes)])
+
+    def run(workers_, max_batch):
+        perm = torch.empty(total, dtype=torch.int32, device=dev)
+        lcp = torch.empty(total, dtype=torch.int32, device=dev)
+        reqs = []
+        for r in range(nall):
+            chars, offs, fixed, _ = src[r]
+            n = int(sizes[r])
+            reqs.append(dict(chars=chars, offsets=offs[starts[r]:starts[r] + n], lengths=None, fixed_len=fixed, n=n,
+                             perm_out=perm[int(base[r]):int(base[r + 1])], lcp_out=lcp[int(base[r]):int(base[r + 1])]))
+        torch.cuda.synchronize(dev)
+        tickets = [None] * nall
+        with P.Server(120 << 30, workers=workers_, max_batch=max_batch) as srv:
+            def producer():
+                t_next = time.perf_counter()
+                for r in range(nall):
+                    t_next += float(gaps[r])
+                    d = t_next - time.perf_counter()
+                    if d > 0:
+                        time.sleep(d)
+                    tickets[r] = srv.submit(reqs[r])
+            th = threading.Thread(target=producer)
+            th.start()
+            th.join()
+            res = [srv.wait(t) for t in tickets]
+        st = [s_ for s_, _ in res]
+        tm = np.array([t_ for _, t_ in res])
+        lat = tm[:, 2] - tm[:, 0]
+        span = float(tm[:, 2].max() - tm[:, 0].min())
+        out = {"makespan_ms": span, "strings_per_s": total / (span / 1e3),
+               "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
+               "latency_64Mi_job_ms": float(lat[mid]), "errors": int(sum(1 for x in st if x != 0)),
+               "batches": int(len(set(tm[:, 1].tolist())))}
+        return out, perm, lcp
+
+    served, perm_s, lcp_s = run(workers, 0)
+    plain, perm_p, lcp_p = run(1, 1)
+    equal = bool(torch.equal(perm_s, perm_p) and torch.equal(lcp_s, lcp_p))
+    del perm_s, lcp_s, perm_p, lcp_p, pools, big
+    torch.cuda.empty_cache()
+    return {
+        "workload": (f"{nreq} requests, sizes log-uniform 1,000..4,000,000 strings, generators random/URL-like/DNA-like "
+                     f"by request mod 3, Poisson arrivals at {load:.1f} x the batched capacity, plus one no-LCP job of "
+                     f"64 Mi strings in the middle; seed {seed}"),
+        "requests": nall, "strings": total, "arrival_rate_per_s": rate, "budget_bytes": 120 << 30,
+        "served": dict(served, workers=workers, batching="continuous: every idle worker takes all admitted waiting requests"),
+        "plain": dict(plain, workers=1, batching="one request per launch sequence, first come first served"),
+        "outputs_equal": equal,
+    }
 
 
 def aggregate(dist, ms, units, device):
@@ -528,6 +613,10 @@ def main():
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_vs_plain(P, torch, dev, stream, nreq=args.batched_requests)
+        if not args.no_serving:
+            line["serving"] = serving_vs_plain(P, torch, dev, chars, offsets,
+                                               capacity_sps=line["batched"]["batched"]["strings_per_s"],
+                                               nreq=args.serving_requests)
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()

@@ -211,6 +211,43 @@ int ss_classify(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, uin
                 uint16_t *bucket_out_dev, uint32_t *bucket_begin_out_dev, uint32_t *order_out_dev,
                 ss_stream_t stream);
 
+/*
+ * Sort server -- continuous batching of independent requests (the paper's
+ * job queue of independent subproblems, Section 3.5, one level up: requests
+ * arriving over time).  The server admits submitted requests in arrival order
+ * while the scratch memory of the admitted, unfinished ones fits
+ * budget_bytes; each of `workers` host threads drives its own CUDA stream and,
+ * when idle, takes every admitted request waiting at that moment (at most
+ * max_batch, 0 = no limit) as one batch with the launches of ss_sort_batch.
+ * Batches formed while others run overlap on the device.  Results equal those
+ * of one ss_sort_ex per request.
+ *
+ * Ownership: the caller keeps every buffer a request points to alive and
+ * unchanged (the strings) or untouched (the outputs) until ss_server_wait has
+ * returned for its ticket.  Pointers are device pointers, as for ss_request.
+ *
+ * ss_server_create: budget_bytes > 0, 1 <= workers <= 64; *out receives the
+ *   server (SS_ERR_INVALID otherwise; SS_ERR_CUDA if a stream cannot be made).
+ *   The server works on the device current at creation.
+ * ss_server_submit: queues one request without blocking and returns its
+ *   ticket.  SS_ERR_TOO_LARGE if the request alone needs more scratch than the
+ *   budget (ss_scratch_bytes); SS_ERR_INVALID for NULL pointers with n > 0 or
+ *   after ss_server_destroy has begun.
+ * ss_server_wait: blocks until the ticket's request is done, then writes its
+ *   status (an ss_status) and, if times_ms_out is not NULL, three times in ms
+ *   on the server's clock: submitted, batch started, batch finished.  Each
+ *   ticket is waited for once; an unknown ticket gives SS_ERR_INVALID.
+ * ss_server_destroy: finishes every submitted request, stops the workers and
+ *   frees the server.
+ * ss_scratch_bytes: scratch bytes one request of n strings is charged.
+ */
+typedef struct ss_server ss_server;
+int ss_server_create(uint64_t budget_bytes, uint32_t workers, uint32_t max_batch, ss_server **out);
+int ss_server_submit(ss_server *server, const ss_request *req, uint64_t *ticket_out);
+int ss_server_wait(ss_server *server, uint64_t ticket, int32_t *status_out, double *times_ms_out);
+int ss_server_destroy(ss_server *server);
+uint64_t ss_scratch_bytes(uint32_t n);
+
 /* Kernel timing: when enabled, the library records CUDA events around each of
  * its kernel launches (on the launch stream) and accumulates per-kernel time.
  * ss_profile_read fills up to `cap` entries: name (NUL-terminated, 48 bytes

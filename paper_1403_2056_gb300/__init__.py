@@ -69,8 +69,15 @@ def lib():
     L.ss_launch_count.restype = u64
     L.ss_last_error_detail.argtypes = [C.c_char_p, C.c_size_t]
     L.ss_version.restype = i32
+    L.ss_server_create.argtypes = [u64, u32, u32, C.POINTER(vp)]
+    L.ss_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
+    L.ss_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
+    L.ss_server_destroy.argtypes = [vp]
+    L.ss_scratch_bytes.argtypes = [u32]
+    L.ss_scratch_bytes.restype = u64
     for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
-                 "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read"):
+                 "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
+                 "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -168,6 +175,74 @@ def ss_sort_batch(requests, stream=None):
                          _dev(q["perm_out"], "int32", "perm_out"), _dev(q["lcp_out"], "int32", "lcp_out"),
                          _dev(q.get("status_out"), "int32", "status_out"))
     _check(lib().ss_sort_batch(C.cast(arr, C.c_void_p), len(requests), _stream(stream)))
+
+
+def _request(q):
+    return Request(_dev(q["chars"], "uint8", "chars"), _off(q["offsets"]),
+                   _dev(q.get("lengths"), "int32", "lengths"), int(q.get("fixed_len", 0)), int(q["n"]),
+                   _dev(q["perm_out"], "int32", "perm_out"), _dev(q["lcp_out"], "int32", "lcp_out"),
+                   _dev(q.get("status_out"), "int32", "status_out"))
+
+
+def ss_scratch_bytes(n: int) -> int:
+    return int(lib().ss_scratch_bytes(int(n)))
+
+
+def ss_server_create(budget_bytes: int, workers: int = 2, max_batch: int = 0):
+    h = C.c_void_p()
+    _check(lib().ss_server_create(int(budget_bytes), int(workers), int(max_batch), C.byref(h)))
+    return h
+
+
+def ss_server_submit(server, q) -> int:
+    t = C.c_uint64()
+    _check(lib().ss_server_submit(server, C.byref(_request(q)), C.byref(t)))
+    return t.value
+
+
+def ss_server_wait(server, ticket: int):
+    st = C.c_int32()
+    tm = (C.c_double * 3)()
+    _check(lib().ss_server_wait(server, int(ticket), C.byref(st), tm))
+    return int(st.value), (tm[0], tm[1], tm[2])
+
+
+def ss_server_destroy(server):
+    _check(lib().ss_server_destroy(server))
+
+
+class Server:
+    """Continuous-batching sort server (ss_server_* of the C ABI).  submit()
+    queues a request dict (keys as for ss_sort_batch) and returns its ticket;
+    wait(ticket) blocks until it is done and returns (status, (t_submit,
+    t_start, t_done)) in ms on the server's clock.  The caller keeps the
+    request's tensors alive until wait() has returned."""
+
+    def __init__(self, budget_bytes: int, workers: int = 2, max_batch: int = 0):
+        self._h = ss_server_create(budget_bytes, workers, max_batch)
+        self._keep = {}
+
+    def submit(self, q) -> int:
+        t = ss_server_submit(self._h, q)
+        self._keep[t] = q
+        return t
+
+    def wait(self, ticket: int):
+        r = ss_server_wait(self._h, ticket)
+        self._keep.pop(ticket, None)
+        return r
+
+    def close(self):
+        if self._h:
+            ss_server_destroy(self._h)
+            self._h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
 
 
 def ss_merge(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,

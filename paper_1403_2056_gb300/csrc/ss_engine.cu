@@ -26,6 +26,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <vector>
 
 #include "ss_internal.cuh"
@@ -844,17 +846,17 @@ __global__ void k_bucket_begin(const BigSeg *seg, const uint32_t *scan, uint32_t
 // ------------------------------------------------------------ host side
 
 static int sm_count() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0;
+    static const int n = [] {
+        int dev = 0, c = 0;
         cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-        if (n <= 0) n = 1;
-    }
+        cudaDeviceGetAttribute(&c, cudaDevAttrMultiProcessorCount, dev);
+        return c > 0 ? c : 1;
+    }();
     return n;
 }
 
-static bool g_attrs_done[64];
+static std::atomic<bool> g_attrs_done[64];
+static std::mutex g_attrs_mu;
 
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
@@ -864,7 +866,8 @@ static cudaError_t set_smem(K kernel, size_t bytes) {
 static cudaError_t ensure_attrs() {
     int dev = 0;
     cudaGetDevice(&dev);
-    if (dev < 64 && g_attrs_done[dev]) return cudaSuccess;
+    if (dev < 64 && g_attrs_done[dev].load()) return cudaSuccess;
+    std::lock_guard<std::mutex> lk(g_attrs_mu);
     cudaError_t e;
     if ((e = set_smem(k_build_trees, sizeof(TreeSmem)))) return e;
     if ((e = set_smem(k_pick_only, sizeof(TreeSmem)))) return e;
@@ -890,6 +893,14 @@ struct Carve {
         return p;
     }
 };
+
+static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np);
+
+size_t engine_scratch_bytes(size_t N, uint32_t nreq) {
+    Caps caps;
+    size_t np;
+    return carve_size(N, nreq, caps, np);
+}
 
 static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     caps.big = (uint32_t)(N / (kSmallMax + 1) + nreq + 1);

@@ -280,6 +280,7 @@ void *host_staging(size_t bytes);
 
 // engine entry points (ss_engine.cu)
 int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream);
+size_t engine_scratch_bytes(size_t N, uint32_t nreq);
 int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
                     uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t stream);
 int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t stream);
