@@ -855,6 +855,38 @@ static int sm_count() {
     return n;
 }
 
+#ifndef SS_C1_NT
+#define SS_C1_NT 64     // threads of the CTA base case for 33..256 strings
+#endif
+#ifndef SS_C2_NT
+#define SS_C2_NT 256    // .. for 257..1024 strings
+#endif
+#ifndef SS_C3_NT
+#define SS_C3_NT 512    // .. for 1025..4096 strings
+#endif
+#ifndef SS_BASE_CONCURRENT
+#define SS_BASE_CONCURRENT 1
+#endif
+
+// Two side streams and three events per host thread (a server's workers each
+// get their own), made on first use.
+struct AuxStreams {
+    bool ok = false;
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    AuxStreams() {
+        ok = cudaStreamCreateWithFlags(&s[0], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaStreamCreateWithFlags(&s[1], cudaStreamNonBlocking) == cudaSuccess;
+        for (int k = 0; k < 3 && ok; k++) ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
+        if (!ok) cudaGetLastError();
+    }
+};
+
+static AuxStreams &aux_streams() {
+    static thread_local AuxStreams a;
+    return a;
+}
+
 static std::atomic<bool> g_attrs_done[64];
 static std::mutex g_attrs_mu;
 
@@ -874,9 +906,9 @@ static cudaError_t ensure_attrs() {
     if ((e = set_smem(k_classify, sizeof(ClassifySmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_SORT>, sizeof(ScatterSmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_CLASSIFY>, sizeof(ScatterSmem)))) return e;
-    if ((e = set_smem(k_base_cta<32, 8>, sizeof(BaseSmem<32, 8>)))) return e;
-    if ((e = set_smem(k_base_cta<128, 8>, sizeof(BaseSmem<128, 8>)))) return e;
-    if ((e = set_smem(k_base_cta<512, 8>, sizeof(BaseSmem<512, 8>)))) return e;
+    if ((e = set_smem(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>)))) return e;
+    if ((e = set_smem(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>)))) return e;
+    if ((e = set_smem(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>)))) return e;
     if (dev < 64) g_attrs_done[dev] = true;
     return cudaSuccess;
 }
@@ -1087,20 +1119,39 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         // CTA base cases first: they append their small equal-key groups to the
         // class-0 list, which the warp kernel then drains (count read on the device)
         SmallTask *const *L = tl.l;
-        if (uint32_t n1 = hc[C_NTASK + 1]) {
-            uint32_t grid = std::min<uint32_t>(n1, sms * 32);
-            SS_LAUNCH_U("small_cta256", st, hc[C_ETASK + 1], (k_base_cta<32, 8><<<grid, 32, sizeof(BaseSmem<32, 8>), st>>>(
-                L[1], n1, dreqs, eb, L[0], tl.cap[0], counters)));
-        }
-        if (uint32_t n2 = hc[C_NTASK + 2]) {
-            uint32_t grid = std::min<uint32_t>(n2, sms * 8);
-            SS_LAUNCH_U("small_cta1024", st, hc[C_ETASK + 2], (k_base_cta<128, 8><<<grid, 128, sizeof(BaseSmem<128, 8>), st>>>(
-                L[2], n2, dreqs, eb, L[0], tl.cap[0], counters)));
+        // the three CTA classes are independent: on side streams they overlap
+        // each other's last waves; the warp kernel waits for all of them
+        AuxStreams &ax = aux_streams();
+        const bool fork = SS_BASE_CONCURRENT && ax.ok;
+        cudaStream_t s1 = fork ? ax.s[0] : st, s2 = fork ? ax.s[1] : st;
+        if (fork) {
+            TRY(cudaEventRecord(ax.ev[0], st), "fork");
+            TRY(cudaStreamWaitEvent(s1, ax.ev[0], 0), "fork");
+            TRY(cudaStreamWaitEvent(s2, ax.ev[0], 0), "fork");
         }
         if (uint32_t n3 = hc[C_NTASK + 3]) {
-            uint32_t grid = std::min<uint32_t>(n3, sms * 2);
-            SS_LAUNCH_U("small_cta4096", st, hc[C_ETASK + 3], (k_base_cta<512, 8><<<grid, 512, sizeof(BaseSmem<512, 8>), st>>>(
+            constexpr int NT = SS_C3_NT, IT = (int)(kSmallMax / SS_C3_NT);
+            uint32_t grid = std::min<uint32_t>(n3, sms * 2);   // two CTAs per SM fit in shared memory
+            SS_LAUNCH_U("small_cta4096", st, hc[C_ETASK + 3], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), st>>>(
                 L[3], n3, dreqs, eb, L[0], tl.cap[0], counters)));
+        }
+        if (uint32_t n2 = hc[C_NTASK + 2]) {
+            constexpr int NT = SS_C2_NT, IT = (int)(1024 / SS_C2_NT);
+            uint32_t grid = std::min<uint32_t>(n2, sms * 8);
+            SS_LAUNCH_U("small_cta1024", s1, hc[C_ETASK + 2], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s1>>>(
+                L[2], n2, dreqs, eb, L[0], tl.cap[0], counters)));
+        }
+        if (uint32_t n1 = hc[C_NTASK + 1]) {
+            constexpr int NT = SS_C1_NT, IT = (int)(256 / SS_C1_NT);
+            uint32_t grid = std::min<uint32_t>(n1, sms * 32);
+            SS_LAUNCH_U("small_cta256", s2, hc[C_ETASK + 1], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s2>>>(
+                L[1], n1, dreqs, eb, L[0], tl.cap[0], counters)));
+        }
+        if (fork) {
+            TRY(cudaEventRecord(ax.ev[1], s1), "join");
+            TRY(cudaEventRecord(ax.ev[2], s2), "join");
+            TRY(cudaStreamWaitEvent(st, ax.ev[1], 0), "join");
+            TRY(cudaStreamWaitEvent(st, ax.ev[2], 0), "join");
         }
         if (hc[C_NTASK + 0] || hc[C_NTASK + 1] || hc[C_NTASK + 2] || hc[C_NTASK + 3]) {
             uint32_t grid = sms * 8;
