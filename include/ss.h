@@ -244,6 +244,27 @@ int ss_classify(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, uin
 typedef struct ss_server ss_server;
 int ss_server_create(uint64_t budget_bytes, uint32_t workers, uint32_t max_batch, ss_server **out);
 int ss_server_submit(ss_server *server, const ss_request *req, uint64_t *ticket_out);
+
+/*
+ * A request on host buffers: the arguments of ss_sort_host.  The server runs
+ * it alone on one worker (copies in, the sort, the merge of `runs` runs when
+ * runs > 1, copies out), so its copies overlap the sorts of other workers:
+ * a stream of host requests through a 2-worker server overlaps the transfers
+ * of one with the sort of the next.  Pinned host buffers copy faster.  It is
+ * charged its device copies, outputs and scratch against the budget.
+ */
+typedef struct {
+    const uint8_t *chars;
+    uint64_t chars_len;
+    const uint64_t *offsets;
+    const uint32_t *lengths;
+    uint32_t fixed_len;
+    uint32_t n;
+    uint32_t runs;
+    uint32_t *perm_out;
+    uint32_t *lcp_out;
+} ss_host_request;
+int ss_server_submit_host(ss_server *server, const ss_host_request *req, uint64_t *ticket_out);
 int ss_server_wait(ss_server *server, uint64_t ticket, int32_t *status_out, double *times_ms_out);
 int ss_server_destroy(ss_server *server);
 uint64_t ss_scratch_bytes(uint32_t n);

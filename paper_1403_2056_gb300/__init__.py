@@ -72,15 +72,23 @@ def lib():
     L.ss_server_create.argtypes = [u64, u32, u32, C.POINTER(vp)]
     L.ss_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
     L.ss_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
+    L.ss_server_submit_host.argtypes = [vp, vp, C.POINTER(u64)]
     L.ss_server_destroy.argtypes = [vp]
     L.ss_scratch_bytes.argtypes = [u32]
     L.ss_scratch_bytes.restype = u64
     for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
-                 "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy"):
+                 "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
+                 "ss_server_submit_host"):
         getattr(L, name).restype = i32
     _lib = L
     return L
+
+
+class HostRequest(C.Structure):
+    _fields_ = [("chars", C.c_void_p), ("chars_len", C.c_uint64), ("offsets", C.c_void_p), ("lengths", C.c_void_p),
+                ("fixed_len", C.c_uint32), ("n", C.c_uint32), ("runs", C.c_uint32), ("perm_out", C.c_void_p),
+                ("lcp_out", C.c_void_p)]
 
 
 class Request(C.Structure):
@@ -200,6 +208,17 @@ def ss_server_submit(server, q) -> int:
     return t.value
 
 
+def ss_server_submit_host(server, chars, offsets, lengths, fixed_len, perm_out, lcp_out, runs=1) -> int:
+    """Host arrays (numpy, or pinned CPU tensors), as for ss_sort_host."""
+    n = int(offsets.shape[0])
+    nbytes = int(chars.nbytes) if isinstance(chars, np.ndarray) else int(chars.numel() * chars.element_size())
+    q = HostRequest(_ptr(chars), nbytes, _ptr(offsets), _ptr(lengths), int(fixed_len), n, int(runs), _ptr(perm_out),
+                    _ptr(lcp_out))
+    t = C.c_uint64()
+    _check(lib().ss_server_submit_host(server, C.byref(q), C.byref(t)))
+    return t.value
+
+
 def ss_server_wait(server, ticket: int):
     st = C.c_int32()
     tm = (C.c_double * 3)()
@@ -225,6 +244,11 @@ class Server:
     def submit(self, q) -> int:
         t = ss_server_submit(self._h, q)
         self._keep[t] = q
+        return t
+
+    def submit_host(self, chars, offsets, lengths, fixed_len, perm_out, lcp_out, runs=1) -> int:
+        t = ss_server_submit_host(self._h, chars, offsets, lengths, fixed_len, perm_out, lcp_out, runs)
+        self._keep[t] = (chars, offsets, lengths, perm_out, lcp_out)
         return t
 
     def wait(self, ticket: int):

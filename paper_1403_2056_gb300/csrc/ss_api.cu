@@ -189,55 +189,12 @@ static int check_req(const ReqDesc &r, const char *who) {
     return SS_OK;
 }
 
-extern "C" {
+namespace ss {
 
-int ss_version(void) { return 100; }
-
-int ss_last_error_detail(char *buf, size_t len) {
-    const std::string &d = t_detail;
-    if (buf && len) {
-        size_t k = d.size() < len - 1 ? d.size() : len - 1;
-        memcpy(buf, d.data(), k);
-        buf[k] = 0;
-    }
-    return (int)d.size();
-}
-
-int ss_sort_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len, uint32_t n,
-               uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
-    t_detail.clear();
-    ReqDesc r = make_req(chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, nullptr);
-    int rc = check_req(r, "ss_sort_ex");
-    if (rc != SS_OK || n == 0) return rc;
-    return engine_sort(&r, 1, as_stream(stream));
-}
-
-int ss_sort(const uint8_t *chars, const uint64_t *offsets, uint32_t n, uint32_t *perm_out, uint32_t *lcp_out,
-            ss_stream_t stream) {
-    return ss_sort_ex(chars, offsets, nullptr, 0, n, perm_out, lcp_out, stream);
-}
-
-int ss_sort_batch(const ss_request *reqs, uint32_t count, ss_stream_t stream) {
-    t_detail.clear();
-    if (count == 0) return SS_OK;
-    if (!reqs) {
-        set_error_detail("ss_sort_batch: NULL request array");
-        return SS_ERR_INVALID;
-    }
-    std::vector<ReqDesc> v(count);
-    for (uint32_t i = 0; i < count; i++) {
-        const ss_request &q = reqs[i];
-        v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
-        int rc = check_req(v[i], "ss_sort_batch");
-        if (rc != SS_OK) return rc;
-    }
-    return engine_sort(v.data(), count, as_stream(stream));
-}
-
-int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host,
-                 const uint32_t *lengths_host, uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host,
-                 uint32_t *lcp_host, ss_stream_t stream) {
-    t_detail.clear();
+// Host buffers in, host buffers out: copies, the sort (runs > 1: index-contiguous
+// runs sorted together, then the LCP merge), copies back; returns when done.
+int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host, const uint32_t *lengths_host,
+              uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host, uint32_t *lcp_host, cudaStream_t st) {
     if (n == 0) return SS_OK;
     if (!chars_host || !offsets_host || !perm_host || !lcp_host || chars_len == 0) {
         set_error_detail("ss_sort_host: NULL pointer or empty chars with n = %u", n);
@@ -246,7 +203,6 @@ int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *
     if (n == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
     if (runs == 0) runs = 1;
     if (runs > n) runs = n;
-    cudaStream_t st = as_stream(stream);
     const size_t A = 255;
     size_t cbytes = (chars_len + 15) & ~(size_t)15;   // aligned words past the end stay inside
     size_t nb4 = (4ull * n + A) & ~A, nb8 = (8ull * n + A) & ~A;
@@ -305,6 +261,61 @@ int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *
     if (e && rc == SS_OK) rc = cuda_fail(e, "ss_sort_host");
     scratch_free(block, st);
     return rc;
+}
+
+}  // namespace ss
+
+extern "C" {
+
+int ss_version(void) { return 100; }
+
+int ss_last_error_detail(char *buf, size_t len) {
+    const std::string &d = t_detail;
+    if (buf && len) {
+        size_t k = d.size() < len - 1 ? d.size() : len - 1;
+        memcpy(buf, d.data(), k);
+        buf[k] = 0;
+    }
+    return (int)d.size();
+}
+
+int ss_sort_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len, uint32_t n,
+               uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
+    t_detail.clear();
+    ReqDesc r = make_req(chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, nullptr);
+    int rc = check_req(r, "ss_sort_ex");
+    if (rc != SS_OK || n == 0) return rc;
+    return engine_sort(&r, 1, as_stream(stream));
+}
+
+int ss_sort(const uint8_t *chars, const uint64_t *offsets, uint32_t n, uint32_t *perm_out, uint32_t *lcp_out,
+            ss_stream_t stream) {
+    return ss_sort_ex(chars, offsets, nullptr, 0, n, perm_out, lcp_out, stream);
+}
+
+int ss_sort_batch(const ss_request *reqs, uint32_t count, ss_stream_t stream) {
+    t_detail.clear();
+    if (count == 0) return SS_OK;
+    if (!reqs) {
+        set_error_detail("ss_sort_batch: NULL request array");
+        return SS_ERR_INVALID;
+    }
+    std::vector<ReqDesc> v(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const ss_request &q = reqs[i];
+        v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
+        int rc = check_req(v[i], "ss_sort_batch");
+        if (rc != SS_OK) return rc;
+    }
+    return engine_sort(v.data(), count, as_stream(stream));
+}
+
+int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host,
+                 const uint32_t *lengths_host, uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host,
+                 uint32_t *lcp_host, ss_stream_t stream) {
+    t_detail.clear();
+    return host_sort(chars_host, chars_len, offsets_host, lengths_host, fixed_len, n, runs, perm_host, lcp_host,
+                     as_stream(stream));
 }
 
 int ss_merge(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,

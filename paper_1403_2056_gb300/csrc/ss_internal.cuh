@@ -281,6 +281,8 @@ void *host_staging(size_t bytes);
 // engine entry points (ss_engine.cu)
 int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream);
 size_t engine_scratch_bytes(size_t N, uint32_t nreq);
+int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host, const uint32_t *lengths_host,
+              uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host, uint32_t *lcp_host, cudaStream_t st);
 int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
                     uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t stream);
 int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t stream);

@@ -29,8 +29,19 @@
 
 namespace ss {
 
+struct HostArgs {      // a request on host buffers (ss_server_submit_host)
+    const uint8_t *chars;
+    uint64_t chars_len;
+    const uint64_t *offsets;
+    const uint32_t *lengths;
+    uint32_t fixed_len, n, runs;
+    uint32_t *perm, *lcp;
+};
+
 struct ServerJob {
     uint64_t ticket;
+    bool host;           // host buffers: runs alone, with its copies, on the worker's stream
+    HostArgs ha;
     ReqDesc req;
     size_t bytes;        // admission charge: scratch of the request alone
     double t_submit, t_start, t_done;
@@ -66,12 +77,34 @@ struct Server {
         while (!waiting.empty() && b.size() < max_batch) {
             ServerJob &j = jobs[waiting.front()];
             if (used + j.bytes > budget && !(used == 0 && b.empty())) break;
+            // a host-buffer job runs alone (its copies overlap other workers' sorts)
+            if (!b.empty() && (j.host || jobs[b.front()].host)) break;
             used += j.bytes;
             b.push_back(waiting.front());
             waiting.pop_front();
         }
         in_use = used;
         return b;
+    }
+
+    int enqueue(ServerJob &j, uint32_t n, uint64_t *ticket_out) {
+        std::lock_guard<std::mutex> lk(mu);
+        if (stop) {
+            set_error_detail("ss_server_submit: the server is shutting down");
+            return SS_ERR_INVALID;
+        }
+        if (j.bytes > budget) {
+            set_error_detail("ss_server_submit: request of %u strings needs %zu bytes, above the budget %llu", n, j.bytes,
+                             (unsigned long long)budget);
+            return SS_ERR_TOO_LARGE;
+        }
+        j.ticket = next_ticket++;
+        j.t_submit = now_ms();
+        *ticket_out = j.ticket;
+        jobs.emplace(j.ticket, j);
+        waiting.push_back(j.ticket);
+        cv_work.notify_one();
+        return SS_OK;
     }
 
     void work(cudaStream_t st) {
@@ -96,8 +129,12 @@ struct Server {
                 reqs.push_back(j.req);
                 charged += j.bytes;
             }
+            const bool host = jobs[batch.front()].host;
+            const HostArgs ha = jobs[batch.front()].ha;
             lk.unlock();
-            int rc = engine_sort(reqs.data(), (uint32_t)reqs.size(), st);
+            int rc = host ? host_sort(ha.chars, ha.chars_len, ha.offsets, ha.lengths, ha.fixed_len, ha.n, ha.runs, ha.perm,
+                                      ha.lcp, st)
+                          : engine_sort(reqs.data(), (uint32_t)reqs.size(), st);
             const double td = now_ms();
             lk.lock();
             in_use -= charged;
@@ -161,6 +198,8 @@ int ss_server_submit(ss_server *server, const ss_request *q, uint64_t *ticket_ou
         return SS_ERR_TOO_LARGE;
     }
     ServerJob j;
+    j.host = false;
+    memset(&j.ha, 0, sizeof(j.ha));
     memset(&j.req, 0, sizeof(j.req));
     j.req.chars = q->chars;
     j.req.offsets = q->offsets;
@@ -174,23 +213,37 @@ int ss_server_submit(ss_server *server, const ss_request *q, uint64_t *ticket_ou
     j.t_start = j.t_done = 0;
     j.status = SS_OK;
     j.done = false;
-    std::lock_guard<std::mutex> lk(s->mu);
-    if (s->stop) {
-        set_error_detail("ss_server_submit: the server is shutting down");
+    return s->enqueue(j, q->n, ticket_out);
+}
+
+int ss_server_submit_host(ss_server *server, const ss_host_request *q, uint64_t *ticket_out) {
+    Server *s = reinterpret_cast<Server *>(server);
+    if (!s || !q || !ticket_out) {
+        set_error_detail("ss_server_submit_host: NULL argument");
         return SS_ERR_INVALID;
     }
-    if (j.bytes > s->budget) {
-        set_error_detail("ss_server_submit: request of %u strings needs %zu scratch bytes, above the budget %llu", q->n,
-                         j.bytes, (unsigned long long)s->budget);
+    if (q->n && (!q->chars || !q->offsets || !q->perm_out || !q->lcp_out || q->chars_len == 0)) {
+        set_error_detail("ss_server_submit_host: NULL pointer or empty chars with n = %u", q->n);
+        return SS_ERR_INVALID;
+    }
+    if (q->n == 0xFFFFFFFFu) {
+        set_error_detail("ss_server_submit_host: n = 2^32 - 1 is beyond the limit 2^32 - 2");
         return SS_ERR_TOO_LARGE;
     }
-    j.ticket = s->next_ticket++;
-    j.t_submit = s->now_ms();
-    *ticket_out = j.ticket;
-    s->jobs.emplace(j.ticket, j);
-    s->waiting.push_back(j.ticket);
-    s->cv_work.notify_one();
-    return SS_OK;
+    ServerJob j;
+    j.host = true;
+    memset(&j.req, 0, sizeof(j.req));
+    j.ha = HostArgs{q->chars, q->chars_len, q->offsets, q->lengths, q->lengths ? 0u : q->fixed_len, q->n,
+                    q->runs ? q->runs : 1u, q->perm_out, q->lcp_out};
+    // device copies of the input, the output, the runs and the merge's buffers, and the sort's scratch
+    const uint64_t n = q->n;
+    j.bytes = q->n ? (size_t)(q->chars_len + 32 + 8 * n + (q->lengths ? 4 * n : 0) + 16 * n +
+                              (j.ha.runs > 1 ? 8 * n + 56 * n : 0) + engine_scratch_bytes(q->n, j.ha.runs))
+                   : 0;
+    j.t_start = j.t_done = 0;
+    j.status = SS_OK;
+    j.done = false;
+    return s->enqueue(j, q->n, ticket_out);
 }
 
 int ss_server_wait(ss_server *server, uint64_t ticket, int32_t *status_out, double *times_ms_out) {

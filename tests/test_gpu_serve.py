@@ -117,3 +117,31 @@ def test_server_refuses_oversize_request():
         with pytest.raises(P.SortError) as e:
             srv.submit(q)
         assert e.value.status == -5
+
+
+def test_server_host_requests_equal_sort_host():
+    """Host-buffer requests (copies in, sort of runs + merge, copies out) on a
+    2-worker server, several in flight: each equals ss_sort_host's result."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    sets = [W.url_like(150_000, seed=21), W.dna_windows(120_000, 2_400_100, 100, seed=22),
+            W.random_lower(90_000, seed=23), W.url_like(60_000, seed=24)]
+    with P.Server(8 << 30, workers=2) as srv:
+        jobs = []
+        for k, ss in enumerate(sets):
+            hp = np.full(ss.n, 0xFFFFFFFF, np.uint32)
+            hl = np.full(ss.n, 0xFFFFFFFF, np.uint32)
+            runs = 1 + k % 3
+            t = srv.submit_host(ss.chars, ss.offsets, None, ss.fixed_len, hp, hl, runs=runs)
+            jobs.append((ss, runs, hp, hl, t))
+        for ss, runs, hp, hl, t in jobs:
+            status, _ = srv.wait(t)
+            assert status == 0
+            wp = np.full(ss.n, 0xFFFFFFFF, np.uint32)
+            wl = np.full(ss.n, 0xFFFFFFFF, np.uint32)
+            P.ss_sort_host(ss.chars, ss.offsets, None, ss.fixed_len, wp, wl, runs=runs)
+            assert np.array_equal(hp, wp), ss.name
+            assert np.array_equal(hl, wl), ss.name
+            want_perm, want_lcp = oracle.sort(ss)
+            assert np.array_equal(hp, want_perm), ss.name
+            assert np.array_equal(hl, want_lcp), ss.name
