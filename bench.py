@@ -347,12 +347,15 @@ def d_and_balg(lcp: np.ndarray):
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi samples (every 20 ms, time-stamped) around the timed region;
+    the summary keeps the samples that fall inside it (the nearest one if the
+    region is shorter than the sampling interval)."""
 
     def __init__(self, index):
         self.proc = None
         self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
         self.index = index
+        self.t0 = self.t1 = None
 
     def start(self):
         try:
@@ -360,39 +363,55 @@ class Clocks:
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}",
-                 "--query-gpu=index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "--query-gpu=timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap",
-                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                 "--format=csv,noheader,nounits", "-lms", "20"], stdout=self.f, stderr=subprocess.DEVNULL)
+            deadline = time.time() + 10.0   # wait for the first sample: the sampler is up
+            while time.time() < deadline and os.path.getsize(self.path) == 0:
+                time.sleep(0.02)
         except Exception:
             self.proc = None
+
+    def mark(self, begin):
+        if begin:
+            self.t0 = time.time()
+        else:
+            self.t1 = time.time()
 
     def stop(self):
         if not self.proc:
             return None
+        time.sleep(0.05)
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except Exception:
             self.proc.kill()
         self.f.close()
-        sm, mx, reasons = [], 0.0, set()
+        import datetime
+        rows = []
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for line in open(self.path):
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
             try:
-                sm.append(float(parts[1]))
-                mx = max(mx, float(parts[2]))
+                ts = datetime.datetime.strptime(parts[0], "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                rows.append((ts, float(parts[1]), float(parts[2]),
+                             {nm for k, nm in enumerate(names) if parts[5 + k].lower() == "active"}))
             except ValueError:
                 continue
-            for k, nm in enumerate(names):
-                if parts[5 + k].lower() == "active":
-                    reasons.add(nm)
-        if not sm:
+        if not rows:
             return None
-        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+        inside = [r for r in rows if self.t0 is not None and self.t0 <= r[0] <= (self.t1 or r[0])]
+        if not inside and self.t0 is not None:
+            mid = 0.5 * (self.t0 + (self.t1 or self.t0))
+            inside = [min(rows, key=lambda r: abs(r[0] - mid))]
+        sm = [r[1] for r in inside]
+        reasons = set().union(*[r[3] for r in inside]) if inside else set()
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": max(r[2] for r in inside), "reasons": sorted(reasons),
+                "samples": len(inside), "interval_ms": 20}
 
 
 def cpu_baseline(ss, seconds):
@@ -511,27 +530,42 @@ def main():
         step()
     torch.cuda.synchronize(dev)
 
-    # timed region: K steps, kernel events on the launch stream, clocks sampled
+    # timed region: exactly K steps between a barrier and a synchronize on both
+    # sides, CUDA events on the launch stream, clocks sampled
     clocks = Clocks(local)
-    P.profile_reset()
-    P.profile_enable(True)
+    clocks.start()
     barrier()
     torch.cuda.synchronize(dev)
-    clocks.start()
     launches0 = P.launch_count()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
+    clocks.mark(True)
     ev0.record(stream)
     for _ in range(args.steps):
         step()
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    clocks.mark(False)
     barrier()
     launches = P.launch_count() - launches0
     ck = clocks.stop()
+    ms, job_strings = aggregate(dist, ev0.elapsed_time(ev1) / args.steps, n, dev)
+
+    # per-kernel times: the same K steps again with the library's launch events on
+    # (the base-case size classes then run one after another, so every kernel's
+    # time is its own)
+    P.profile_reset()
+    P.profile_enable(True)
+    pe0 = torch.cuda.Event(enable_timing=True)
+    pe1 = torch.cuda.Event(enable_timing=True)
+    pe0.record(stream)
+    for _ in range(args.steps):
+        step()
+    pe1.record(stream)
+    torch.cuda.synchronize(dev)
     P.profile_enable(False)
     prof = P.profile_read()
-    ms, job_strings = aggregate(dist, ev0.elapsed_time(ev1) / args.steps, n, dev)
+    profiled_ms = pe0.elapsed_time(pe1) / args.steps
 
     lcp_h = lcp.cpu().numpy().view(np.uint32)
     D, balg = d_and_balg(lcp_h)
@@ -585,6 +619,9 @@ def main():
         "gpu_launches": int(launches),
         "clocks": ck,
         "kernels": kernels,
+        "kernels_pass": {"ms_per_step": profiled_ms,
+                         "what": "the per-kernel table and the roofline come from a second pass of the same K steps "
+                                 "with launch events on and the base-case classes serialised"},
     }
 
     # end to end through the host-buffer API: H2D, sort runs + merge, D2H

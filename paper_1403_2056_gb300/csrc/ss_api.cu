@@ -137,6 +137,8 @@ static void prof_flush() {
     t_pending.clear();
 }
 
+bool prof_on() { return g_prof_on.load() != 0; }
+
 void prof_begin(const char *name, cudaStream_t s) {
     (void)name;
     g_launches++;

@@ -1120,9 +1120,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         // class-0 list, which the warp kernel then drains (count read on the device)
         SmallTask *const *L = tl.l;
         // the three CTA classes are independent: on side streams they overlap
-        // each other's last waves; the warp kernel waits for all of them
+        // each other's last waves; the warp kernel waits for all of them.  With
+        // per-launch timing on they run one after another, so each kernel's time
+        // is its own.
         AuxStreams &ax = aux_streams();
-        const bool fork = SS_BASE_CONCURRENT && ax.ok;
+        const bool fork = SS_BASE_CONCURRENT && ax.ok && !prof_on();
         cudaStream_t s1 = fork ? ax.s[0] : st, s2 = fork ? ax.s[1] : st;
         if (fork) {
             TRY(cudaEventRecord(ax.ev[0], st), "fork");

@@ -268,6 +268,7 @@ void set_error_detail(const char *fmt, ...);
 int cuda_fail(cudaError_t e, const char *what);
 
 // launch bookkeeping (profiling): begin/end around each library kernel launch
+bool prof_on();   // per-launch timing is enabled
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(const char *name, cudaStream_t s, uint64_t units);
 
