@@ -868,21 +868,14 @@ static int sm_count() {
 #define SS_BASE_CONCURRENT 1
 #endif
 
-// Two side streams and three events per host thread (a server's workers each
-// get their own), made on first use.
-struct AuxStreams {
-    bool ok = false;
-    cudaStream_t s[2] = {nullptr, nullptr};
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
-    AuxStreams() {
-        ok = cudaStreamCreateWithFlags(&s[0], cudaStreamNonBlocking) == cudaSuccess &&
-             cudaStreamCreateWithFlags(&s[1], cudaStreamNonBlocking) == cudaSuccess;
-        for (int k = 0; k < 3 && ok; k++) ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
-        if (!ok) cudaGetLastError();
-    }
-};
+AuxStreams::AuxStreams() {
+    ok = cudaStreamCreateWithFlags(&s[0], cudaStreamNonBlocking) == cudaSuccess &&
+         cudaStreamCreateWithFlags(&s[1], cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; k < 3 && ok; k++) ok = cudaEventCreateWithFlags(&ev[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) cudaGetLastError();
+}
 
-static AuxStreams &aux_streams() {
+AuxStreams &aux_streams() {
     static thread_local AuxStreams a;
     return a;
 }

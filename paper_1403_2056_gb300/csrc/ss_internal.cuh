@@ -269,6 +269,16 @@ int cuda_fail(cudaError_t e, const char *what);
 
 // launch bookkeeping (profiling): begin/end around each library kernel launch
 bool prof_on();   // per-launch timing is enabled
+
+// Two side streams and three events per host thread (a server's workers each
+// get their own), made on first use, for independent launches that may overlap.
+struct AuxStreams {
+    bool ok = false;
+    cudaStream_t s[2] = {nullptr, nullptr};
+    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    AuxStreams();
+};
+AuxStreams &aux_streams();
 void prof_begin(const char *name, cudaStream_t s);
 void prof_end(const char *name, cudaStream_t s, uint64_t units);
 
