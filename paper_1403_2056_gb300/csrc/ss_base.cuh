@@ -148,14 +148,25 @@ __device__ __forceinline__ bool gk_less(uint64_t ka, uint32_t ga, uint64_t kb, u
 // bijection mod 32), so the blocked stores and loads below are conflict-free.
 __device__ __forceinline__ uint32_t padx(uint32_t x) { return x + (x >> 3); }
 
-template <int ITEMS>
+// The order of the sort: (group, key, original index), or the key alone when
+// every slot is in one group and the slots start in original-index order (the
+// first sort of a segment): the sort below is stable, so equal keys keep that
+// order and the result is the same.  The key-only order needs no group word in
+// the comparisons.
+template <bool KEYONLY>
+__device__ __forceinline__ bool sort_less(uint64_t ka, uint32_t ga, uint64_t kb, uint32_t gb) {
+    return KEYONLY ? ka < kb : gk_less(ka, ga, kb, gb);
+}
+
+template <int ITEMS, bool KEYONLY>
 __device__ __forceinline__ void reg_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITEMS]) {
-    // odd-even transposition network, fully unrolled
+    // odd-even transposition network, fully unrolled; it swaps only strictly
+    // smaller neighbours forward, so it is stable
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
 #pragma unroll
         for (int j = r & 1; j + 1 < ITEMS; j += 2) {
-            if (gk_less(k[j + 1], g[j + 1], k[j], g[j])) {
+            if (sort_less<KEYONLY>(k[j + 1], g[j + 1], k[j], g[j])) {
                 uint64_t tk = k[j]; k[j] = k[j + 1]; k[j + 1] = tk;
                 uint32_t tg = g[j]; g[j] = g[j + 1]; g[j + 1] = tg;
             }
@@ -167,10 +178,10 @@ __device__ __forceinline__ void reg_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITE
 // (thread t holds slots t*ITEMS ..) through the padded shared buffers MK / MG
 // (sized for padx(P)).  On return each thread holds its ITEMS slots of the
 // sorted sequence.
-template <int NT, int ITEMS>
+template <int NT, int ITEMS, bool KEYONLY>
 __device__ __forceinline__ void block_merge_sort(uint64_t (&k)[ITEMS], uint32_t (&g)[ITEMS], uint32_t P, uint64_t *MK,
                                                  uint32_t *MG) {
-    reg_sort<ITEMS>(k, g);
+    reg_sort<ITEMS, KEYONLY>(k, g);
     const uint32_t o = threadIdx.x * ITEMS;
     for (uint32_t L = ITEMS; L < P; L <<= 1) {
         if (o < P) {
@@ -185,14 +196,15 @@ __device__ __forceinline__ void block_merge_sort(uint64_t (&k)[ITEMS], uint32_t 
             while (lo < hi) {   // merge path: A[mid] goes first unless B[d-1-mid] < A[mid]
                 uint32_t mid = (lo + hi) >> 1;
                 uint32_t bi = padx(b + d - 1 - mid), ai = padx(a + mid);
-                if (!gk_less(MK[bi], MG[bi], MK[ai], MG[ai])) lo = mid + 1; else hi = mid;
+                if (!sort_less<KEYONLY>(MK[bi], KEYONLY ? 0u : MG[bi], MK[ai], KEYONLY ? 0u : MG[ai])) lo = mid + 1;
+                else hi = mid;
             }
             uint32_t i = lo, jj = d - lo;
             uint64_t ka = i < L ? MK[padx(a + i)] : 0, kb = jj < L ? MK[padx(b + jj)] : 0;
             uint32_t ga = i < L ? MG[padx(a + i)] : 0, gb = jj < L ? MG[padx(b + jj)] : 0;
 #pragma unroll
             for (int q = 0; q < ITEMS; q++) {
-                bool takeA = jj >= L || (i < L && !gk_less(kb, gb, ka, ga));
+                bool takeA = jj >= L || (i < L && !sort_less<KEYONLY>(kb, gb, ka, ga));
                 if (takeA) {
                     k[q] = ka; g[q] = ga; i++;
                     if (i < L) { ka = MK[padx(a + i)]; ga = MG[padx(a + i)]; }
@@ -324,7 +336,9 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
             if (__syncthreads_or(differ)) {
                 uint32_t P = ITEMS;
                 while (P < M) P <<= 1;
-                block_merge_sort<NT, ITEMS>(k, g, P, S.SK, S.MG);
+                // first round: one group, slots in original order (key-only order)
+                if (depth == t.depth) block_merge_sort<NT, ITEMS, true>(k, g, P, S.SK, S.MG);
+                else block_merge_sort<NT, ITEMS, false>(k, g, P, S.SK, S.MG);
 #pragma unroll
                 for (int j = 0; j < ITEMS; j++) {
                     uint32_t s = tid * ITEMS + j;
