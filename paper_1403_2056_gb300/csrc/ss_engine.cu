@@ -111,6 +111,53 @@ __global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t 
     }
 }
 
+// ------------------------------------------------- shared prefix of a request
+// The strings of a large request may all share their first characters (a
+// common scheme or host prefix); the first level's splitters would spend
+// those.  The characters all of them share are the minimum over its strings
+// of the lcp with its first string (one coalesced pass over the depth-0 keys,
+// per chunk of a request's segment); the request's segment then starts that
+// deep, with its keys reloaded there in input order.
+
+constexpr uint32_t kPrefChunk = 8192;   // strings per CTA of the two passes below
+
+__global__ void __launch_bounds__(256) k_shared_prefix(const uint4 *chunks, const ReqDesc *reqs, const uint64_t *key0,
+                                                       uint32_t *shared) {
+    __shared__ uint32_t wmin[8];
+    const uint4 c = chunks[blockIdx.x];   // begin, end, request
+    const uint64_t first = key0[reqs[c.z].base];
+    uint32_t b = 8;
+    for (uint32_t g = c.x + threadIdx.x; g < c.y; g += blockDim.x) {
+        const uint64_t key = key0[g];
+        const uint32_t l = key == first ? (has_zero(key) ? nulpos(key) : 8u) : lcp8(key, first);
+        b = min(b, l);
+        if (b == 0) break;   // nothing shared: the rest cannot lower it
+    }
+    b = __reduce_min_sync(0xffffffffu, b);
+    if ((threadIdx.x & 31) == 0) wmin[threadIdx.x >> 5] = b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < 8; w++) b = min(b, wmin[w]);
+        if (b < ((volatile uint32_t *)shared)[c.z]) atomicMin(shared + c.z, b);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_skip_prefix(const uint4 *chunks, const ReqDesc *reqs, const uint64_t *soff0,
+                                                     uint64_t *key0, const uint32_t *shared) {
+    const uint4 c = chunks[blockIdx.x];
+    const uint32_t b = shared[c.z];
+    if (b == 0 || b > 8) return;
+    const ReqDesc &R = reqs[c.z];
+    for (uint32_t g = c.x + threadIdx.x; g < c.y; g += blockDim.x) key0[g] = load_key_o(R, g - R.base, soff0[g], b);
+}
+
+__global__ void k_start_depth(BigSeg *big, uint32_t nbig, const uint32_t *shared) {
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nbig; k += gridDim.x * blockDim.x) {
+        const uint32_t b = shared[big[k].req];
+        if (b > 0 && b <= 8) big[k].depth = b;
+    }
+}
+
 // ------------------------------------------------------ k_setup_big
 // Exclusive prefix sums over the big list: tile_base, cnt_base, bkt_base,
 // scan_base, from each segment's tree depth as k_build_trees chose it.  The
@@ -950,6 +997,8 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     c.take<Boundary>(caps.bound);
     c.take<uint32_t>(C_NUM);
     c.take<ReqDesc>(nreq);
+    c.take<uint32_t>(nreq);
+    c.take<uint4>(N / kPrefChunk + caps.big + 1);
     return c.off + 256;
 }
 
@@ -1016,12 +1065,15 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     Boundary *bounds = c.take<Boundary>(caps.bound);
     uint32_t *counters = c.take<uint32_t>(C_NUM);
     ReqDesc *dreqs = c.take<ReqDesc>(nreq);
+    uint32_t *shared = c.take<uint32_t>(nreq);   // characters shared by all strings of each large request
+    uint4 *pchunks = c.take<uint4>(N / kPrefChunk + caps.big + 1);
 
     int rc = SS_OK;
     uint32_t *hc = (uint32_t *)host_staging(sizeof(uint32_t) * C_NUM + 64);
     // initial segments: one per request
     std::vector<BigSeg> big0;
     std::vector<SmallTask> s_task[kClasses];
+    std::vector<uint4> pchunk_host;
     uint32_t tiles0 = 0, counts0 = 0, pairs0 = 0;
     for (uint32_t r = 0; r < nreq; r++) {
         const ReqDesc &q = reqs[r];
@@ -1059,6 +1111,17 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     {
         uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
         SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0], key[0]));
+        if (!big0.empty()) {
+            for (const BigSeg &b : big0)
+                for (uint32_t x = 0; x < b.size; x += kPrefChunk)
+                    pchunk_host.push_back(make_uint4(b.begin + x, b.begin + std::min(b.size, x + kPrefChunk), b.req, 0));
+            const uint32_t nch = (uint32_t)pchunk_host.size();
+            TRY(cudaMemcpyAsync(pchunks, pchunk_host.data(), sizeof(uint4) * nch, cudaMemcpyHostToDevice, st), "copy chunks");
+            TRY(cudaMemsetAsync(shared, 0xFF, sizeof(uint32_t) * nreq, st), "reset shared prefix");
+            SS_LAUNCH_U("shared_prefix", st, elems0, k_shared_prefix<<<nch, 256, 0, st>>>(pchunks, dreqs, key[0], shared));
+            SS_LAUNCH_U("skip_prefix", st, elems0, k_skip_prefix<<<nch, 256, 0, st>>>(pchunks, dreqs, soff[0], key[0], shared));
+            SS_LAUNCH_U("start_depth", st, big0.size(), k_start_depth<<<1, 256, 0, st>>>(big[0], (uint32_t)big0.size(), shared));
+        }
         TRY(cudaGetLastError(), "init launch");
     }
     {
