@@ -42,10 +42,10 @@ BYTES_PER_UNIT = {
     # bucket id, index, string offset, carried key read; index, offset, key written
     # (the gather of a key at a new depth is extra: it is counted in the whole-sort B_alg)
     "scatter": 2 + 4 + 8 + 8 + 4 + 8 + 8,
-    "small_warp": 4 + 8 + 4 + 4,     # index + key read, perm + lcp write
-    "small_cta256": 4 + 8 + 4 + 4,
-    "small_cta1024": 4 + 8 + 4 + 4,
-    "small_cta4096": 4 + 8 + 4 + 4,
+    "base_warp": 4 + 8 + 4 + 4,      # index + key read, perm + lcp write
+    "base_c1": 4 + 8 + 4 + 4,
+    "base_c2": 4 + 8 + 4 + 4,
+    "base_c3": 4 + 8 + 4 + 4,
     "boundary": 4 + 4 + 8 + 8 + 4,   # two perm reads, two key gathers, lcp write
     # per output: perm, lcp, offset, cached key + its depth read (28 B); written again in a
     # round that feeds another (28 B), perm + lcp only in the last round (8 B): mean of the

@@ -909,7 +909,7 @@ static int sm_count() {
 #define SS_C2_NT 256    // .. for 257..1024 strings
 #endif
 #ifndef SS_C3_NT
-#define SS_C3_NT 512    // .. for 1025..4096 strings
+#define SS_C3_NT 256    // .. for 1025..kSmallMax strings
 #endif
 #ifndef SS_BASE_CONCURRENT
 #define SS_BASE_CONCURRENT 1
@@ -1189,20 +1189,20 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         }
         if (uint32_t n3 = hc[C_NTASK + 3]) {
             constexpr int NT = SS_C3_NT, IT = (int)(kSmallMax / SS_C3_NT);
-            uint32_t grid = std::min<uint32_t>(n3, sms * 2);   // two CTAs per SM fit in shared memory
-            SS_LAUNCH_U("small_cta4096", st, hc[C_ETASK + 3], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), st>>>(
+            uint32_t grid = std::min<uint32_t>(n3, sms * (uint32_t)(4096 / kSmallMax) * 2);   // CTAs that fit in shared memory
+            SS_LAUNCH_U("base_c3", st, hc[C_ETASK + 3], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), st>>>(
                 L[3], n3, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (uint32_t n2 = hc[C_NTASK + 2]) {
             constexpr int NT = SS_C2_NT, IT = (int)(1024 / SS_C2_NT);
             uint32_t grid = std::min<uint32_t>(n2, sms * 8);
-            SS_LAUNCH_U("small_cta1024", s1, hc[C_ETASK + 2], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s1>>>(
+            SS_LAUNCH_U("base_c2", s1, hc[C_ETASK + 2], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s1>>>(
                 L[2], n2, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (uint32_t n1 = hc[C_NTASK + 1]) {
             constexpr int NT = SS_C1_NT, IT = (int)(256 / SS_C1_NT);
             uint32_t grid = std::min<uint32_t>(n1, sms * 32);
-            SS_LAUNCH_U("small_cta256", s2, hc[C_ETASK + 1], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s2>>>(
+            SS_LAUNCH_U("base_c1", s2, hc[C_ETASK + 1], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s2>>>(
                 L[1], n1, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (fork) {
@@ -1213,7 +1213,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         }
         if (hc[C_NTASK + 0] || hc[C_NTASK + 1] || hc[C_NTASK + 2] || hc[C_NTASK + 3]) {
             uint32_t grid = sms * 8;
-            SS_LAUNCH_U("small_warp", st, hc[C_ETASK + 0], k_small_warp<<<grid, kThreads, 0, st>>>(L[0], counters + C_NTASK + 0, dreqs, eb));
+            SS_LAUNCH_U("base_warp", st, hc[C_ETASK + 0], k_small_warp<<<grid, kThreads, 0, st>>>(L[0], counters + C_NTASK + 0, dreqs, eb));
         }
         TRY(cudaGetLastError(), "base case launch");
         if (nb) {

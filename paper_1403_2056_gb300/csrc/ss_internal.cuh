@@ -33,16 +33,16 @@ constexpr int kMaxD = SS_MAX_D;                // tree depth: v = 2^d - 1 <= 102
 constexpr int kMaxV = (1 << kMaxD) - 1;
 constexpr int kMaxB = 2 * kMaxV + 1;           // 2047 buckets
 #ifndef SS_SMALL_MAX
-#define SS_SMALL_MAX 4096
+#define SS_SMALL_MAX 2048
 #endif
 #ifndef SS_CHILD_TARGET
-#define SS_CHILD_TARGET 1024
+#define SS_CHILD_TARGET 512
 #endif
 constexpr uint32_t kSmallMax = SS_SMALL_MAX;   // segments up to this size are base cases
 constexpr uint32_t kChildTarget = SS_CHILD_TARGET;   // tree depth aims at children of about this size
 constexpr uint32_t kTinyMax = 32;              // base cases handled by one warp
 // base-case size classes: class 0 (2..32 strings) one warp; classes 1..3 one
-// CTA of 32, 128, 512 threads holding up to 256, 1024, 4096 strings
+// CTA each, holding up to 256, 1024 and kSmallMax strings
 constexpr int kClasses = 4;
 __host__ __device__ __forceinline__ uint32_t class_max(int c) {
     return c == 0 ? 32u : c == 1 ? 256u : c == 2 ? 1024u : kSmallMax;

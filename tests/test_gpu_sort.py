@@ -62,7 +62,7 @@ def test_empty_and_single():
     P.ss_sort(chars, offsets, 0, out, out)   # n = 0: no-op
 
 
-@pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 4095, 4096,
+@pytest.mark.parametrize("n", [2, 3, 31, 32, 33, 255, 256, 257, 511, 512, 513, 1023, 1024, 1025, 2047, 2048, 2049, 4095, 4096,
                                4097, 8191, 8192, 8193, 20000])
 def test_threshold_sizes(n):
     _check(W.random_lower(n, seed=n, min_len=0, max_len=12))
