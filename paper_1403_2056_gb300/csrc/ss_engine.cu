@@ -95,7 +95,8 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // every element starts as (string index, string offset, key at depth 0); the
 // offset travels with the index so later gathers need one random load, not two
-__global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t *idx0, uint64_t *soff0, uint64_t *key0) {
+__global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t *idx0, uint64_t *soff0, uint64_t *key0,
+                       uint64_t *next0) {
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
         uint32_t r = find_req(reqs, nreq, g);
         const ReqDesc &R = reqs[r];
@@ -103,7 +104,12 @@ __global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t 
         uint64_t off = __ldg(R.offsets + i);
         idx0[g] = i;
         soff0[g] = off;
-        key0[g] = load_key_o(R, i, off, 0);
+        // characters 0..15: the second word serves the shared-prefix step below
+        // (it lives in the other parity's key buffer until the first scatter)
+        uint64_t k0, k1;
+        load_key2_o(R, i, off, 0, k0, k1);
+        key0[g] = k0;
+        next0[g] = k1;
         if (i == 0) {
             R.lcp_out[0] = 0;
             if (R.n == 1) R.perm_out[0] = 0;
@@ -142,13 +148,14 @@ __global__ void __launch_bounds__(256) k_shared_prefix(const uint4 *chunks, cons
     }
 }
 
-__global__ void __launch_bounds__(256) k_skip_prefix(const uint4 *chunks, const ReqDesc *reqs, const uint64_t *soff0,
-                                                     uint64_t *key0, const uint32_t *shared) {
+__global__ void __launch_bounds__(256) k_skip_prefix(const uint4 *chunks, const uint64_t *next0, uint64_t *key0,
+                                                     const uint32_t *shared) {
     const uint4 c = chunks[blockIdx.x];
     const uint32_t b = shared[c.z];
     if (b == 0 || b > 8) return;
-    const ReqDesc &R = reqs[c.z];
-    for (uint32_t g = c.x + threadIdx.x; g < c.y; g += blockDim.x) key0[g] = load_key_o(R, g - R.base, soff0[g], b);
+    // the key at depth b from characters 0..15 (zero past the end of a string)
+    for (uint32_t g = c.x + threadIdx.x; g < c.y; g += blockDim.x)
+        key0[g] = b == 8 ? next0[g] : (key0[g] << (8 * b)) | (next0[g] >> (64 - 8 * b));
 }
 
 __global__ void k_start_depth(BigSeg *big, uint32_t nbig, const uint32_t *shared) {
@@ -1110,7 +1117,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
                 "copy base-case tasks");
     {
         uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
-        SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0], key[0]));
+        SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0], key[0], key[1]));
         if (!big0.empty()) {
             for (const BigSeg &b : big0)
                 for (uint32_t x = 0; x < b.size; x += kPrefChunk)
@@ -1119,7 +1126,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             TRY(cudaMemcpyAsync(pchunks, pchunk_host.data(), sizeof(uint4) * nch, cudaMemcpyHostToDevice, st), "copy chunks");
             TRY(cudaMemsetAsync(shared, 0xFF, sizeof(uint32_t) * nreq, st), "reset shared prefix");
             SS_LAUNCH_U("shared_prefix", st, elems0, k_shared_prefix<<<nch, 256, 0, st>>>(pchunks, dreqs, key[0], shared));
-            SS_LAUNCH_U("skip_prefix", st, elems0, k_skip_prefix<<<nch, 256, 0, st>>>(pchunks, dreqs, soff[0], key[0], shared));
+            SS_LAUNCH_U("skip_prefix", st, elems0, k_skip_prefix<<<nch, 256, 0, st>>>(pchunks, key[1], key[0], shared));
             SS_LAUNCH_U("start_depth", st, big0.size(), k_start_depth<<<1, 256, 0, st>>>(big[0], (uint32_t)big0.size(), shared));
         }
         TRY(cudaGetLastError(), "init launch");
