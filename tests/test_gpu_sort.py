@@ -249,3 +249,62 @@ def test_batch_runs_then_merge_with_bases(K):
         want_perm, want_lcp = oracle.sort(ss)
         assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
         assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
+
+
+# ------------------------------------------- requests sharing a prefix
+def _prefixed(n, prefix, seed, terminated=True, dup_every=0):
+    rng = np.random.default_rng(seed)
+    tails = [bytes(rng.integers(97, 100, int(rng.integers(0, 14))).astype(np.uint8)) for _ in range(n)]
+    strs = [prefix + t for t in tails]
+    if dup_every:
+        for k in range(dup_every, n, dup_every):
+            strs[k] = strs[k - dup_every]
+    return W.from_bytes_list(strs, name=f"prefix{len(prefix)}", terminated=terminated)
+
+
+@pytest.mark.parametrize("plen", [1, 5, 7, 8, 9, 12, 20])
+def test_shared_prefix_large_request(plen):
+    """Every string of a request above the base-case limit starts with the same
+    plen characters (tails over 3 letters, some empty, some duplicates): the
+    request starts its first level that deep."""
+    _check(_prefixed(30_000, b"q" * (plen - 1) + b"/", seed=plen, dup_every=97))
+
+
+def test_shared_prefix_explicit_lengths():
+    """The same with explicit lengths (bytes 0x01..0xFF, no terminators)."""
+    _check(_prefixed(25_000, b"ab\xffcd\x01", seed=3, terminated=False, dup_every=31))
+
+
+def test_shared_prefix_fixed_length():
+    """Fixed-length windows of a text that repeats a 6-character motif with
+    rare changes: long shared prefixes inside one request."""
+    rng = np.random.default_rng(9)
+    text = np.frombuffer(b"ACGTAC" * 200_000, dtype=np.uint8).copy()
+    flip = rng.integers(0, text.size, 3000)
+    text[flip] = rng.choice(np.frombuffer(b"ACGT", dtype=np.uint8), flip.size)
+    offs = (rng.integers(0, (text.size - 40) // 6, 20_000) * 6).astype(np.uint64)
+    ss = W.StringSet(chars=text, offsets=offs, lengths=None, fixed_len=40, name="motif40", meta={})
+    _check(ss)
+
+
+def test_batch_with_different_shared_prefixes():
+    """Large and small requests in one batch, each with its own shared prefix:
+    each request equals the oracle."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    sets = [_prefixed(9_000, b"http://", seed=1), _prefixed(3_000, b"x", seed=2), _prefixed(12_000, b"", seed=3),
+            _prefixed(6_000, b"0123456789", seed=4, dup_every=5), W.random_lower(20_000, seed=5)]
+    reqs, outs = [], []
+    for ss in sets:
+        chars, offsets, lengths = to_device(ss)
+        perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=ss.n,
+                         perm_out=perm, lcp_out=lcp))
+        outs.append((perm, lcp))
+    P.ss_sort_batch(reqs)
+    torch.cuda.synchronize()
+    for ss, (perm, lcp) in zip(sets, outs):
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm), ss.name
+        assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp), ss.name
