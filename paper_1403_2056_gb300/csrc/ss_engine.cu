@@ -1,8 +1,11 @@
 // Super scalar string sample sort (S5) on one GB300, level-synchronous.
 //
-// Every recursion level of the paper's S5 (Algorithm 1, applied recursively
-// as in Section 3.5) runs as a handful of kernels over ALL segments that are
-// still larger than the base-case threshold, whatever request they belong to:
+// k_init gives every string its index, byte offset and first characters;
+// a large request whose strings all share a prefix starts that deep
+// (k_shared_prefix, k_skip_prefix).  Then every recursion level of the
+// paper's S5 (Algorithm 1, applied recursively as in Section 3.5) runs as a
+// handful of kernels over ALL segments that are still larger than the
+// base-case threshold, whatever request they belong to:
 //
 //   k_build_trees  sample (alpha = 2), sort, pick splitters with the
 //                  skip-equal-samples recursion (Section 3.4)      one CTA / segment
@@ -10,8 +13,9 @@
 //                  bucket buffer, per-tile histogram (Alg. 1 loops)  one CTA / tile
 //   k_scan_*       exclusive prefix sum over the bucket-major
 //                  (segment, bucket, tile) counters (Theorem 1)
-//   k_scatter      stable out-of-place redistribution of (index, next key),
-//                  final placement of singletons and all-equal buckets
+//   k_scatter      stable out-of-place redistribution of (index, offset,
+//                  next key) through shared memory, final placement of
+//                  singletons and all-equal buckets
 //   k_buckets      child segments: big ones to the next level, small ones to
 //                  the base case; bucket boundaries recorded for LCPs
 //
