@@ -125,6 +125,38 @@ typedef struct {
 int ss_sort_batch(const ss_request *reqs_host, uint32_t count, ss_stream_t stream);
 
 /*
+ * Tuning of one request (0 fields: the library's defaults).  child_target:
+ * the segment size the splitter tree aims its children at (a power of two in
+ * [32, 65536]; the tree has about size / child_target leaves, at most 1024);
+ * min_step: the smallest depth step an even bucket takes (in [1, 9]; 9: it
+ * never steps and keeps its key).  Neither changes any result.
+ */
+typedef struct {
+    uint32_t child_target;
+    uint32_t min_step;
+} ss_tuning;
+
+/*
+ * ss_sort_batch_tuned -- ss_sort_batch with one tuning per request
+ * (tunings_host: `count` entries, or NULL for the defaults).  SS_ERR_INVALID
+ * for a tuning outside the ranges above.
+ */
+int ss_sort_batch_tuned(const ss_request *reqs_host, const ss_tuning *tunings_host, uint32_t count,
+                        ss_stream_t stream);
+
+/*
+ * ss_autotune -- picks a tuning for inputs like `req`'s: sorts its first
+ * min(n, sample_n) strings (sample_n = 0: 2,000,000) with each of 16
+ * candidate tunings (child_target 256..2048 x min_step 1, 3, 5, 9), once to
+ * warm and once timed with CUDA events on `stream`, into scratch it
+ * allocates (req's outputs are not touched), and writes the fastest to
+ * *best_out and its time in ms to *best_ms_out (may be NULL).  Returns when
+ * done.
+ */
+int ss_autotune(const ss_request *req_host, uint32_t sample_n, ss_tuning *best_out, double *best_ms_out,
+                ss_stream_t stream);
+
+/*
  * ss_merge -- LCP-aware merge of K sorted runs of one string set
  * (Sections 4.1-4.3: LCP-Compare, Algorithm 2; binary LCP-merge,
  * Algorithm 3; the K-way merge is done as ceil(log2 K) rounds of pairwise

@@ -73,13 +73,15 @@ def lib():
     L.ss_server_submit.argtypes = [vp, vp, C.POINTER(u64)]
     L.ss_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
     L.ss_server_submit_host.argtypes = [vp, vp, C.POINTER(u64)]
+    L.ss_sort_batch_tuned.argtypes = [vp, vp, u32, vp]
+    L.ss_autotune.argtypes = [vp, u32, C.POINTER(Tuning), C.POINTER(C.c_double), vp]
     L.ss_server_destroy.argtypes = [vp]
     L.ss_scratch_bytes.argtypes = [u32]
     L.ss_scratch_bytes.restype = u64
     for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
                  "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
-                 "ss_server_submit_host"):
+                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_autotune"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -89,6 +91,10 @@ class HostRequest(C.Structure):
     _fields_ = [("chars", C.c_void_p), ("chars_len", C.c_uint64), ("offsets", C.c_void_p), ("lengths", C.c_void_p),
                 ("fixed_len", C.c_uint32), ("n", C.c_uint32), ("runs", C.c_uint32), ("perm_out", C.c_void_p),
                 ("lcp_out", C.c_void_p)]
+
+
+class Tuning(C.Structure):
+    _fields_ = [("child_target", C.c_uint32), ("min_step", C.c_uint32)]
 
 
 class Request(C.Structure):
@@ -190,6 +196,28 @@ def _request(q):
                    _dev(q.get("lengths"), "int32", "lengths"), int(q.get("fixed_len", 0)), int(q["n"]),
                    _dev(q["perm_out"], "int32", "perm_out"), _dev(q["lcp_out"], "int32", "lcp_out"),
                    _dev(q.get("status_out"), "int32", "status_out"))
+
+
+def ss_sort_batch_tuned(requests, tunings=None, stream=None):
+    """As ss_sort_batch, with one (child_target, min_step) pair per request (0: default)."""
+    arr = (Request * max(1, len(requests)))()
+    for k, q in enumerate(requests):
+        arr[k] = _request(q)
+    tarr = None
+    if tunings is not None:
+        tarr = (Tuning * max(1, len(requests)))()
+        for k, t in enumerate(tunings):
+            tarr[k] = Tuning(int(t[0]), int(t[1]))
+    _check(lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
+                                      len(requests), _stream(stream)))
+
+
+def ss_autotune(q, sample_n: int = 0, stream=None):
+    """((child_target, min_step), ms) fastest on the first sample_n strings of request q."""
+    t = Tuning()
+    ms = C.c_double()
+    _check(lib().ss_autotune(C.byref(_request(q)), int(sample_n), C.byref(t), C.byref(ms), _stream(stream)))
+    return (t.child_target, t.min_step), ms.value
 
 
 def ss_scratch_bytes(n: int) -> int:

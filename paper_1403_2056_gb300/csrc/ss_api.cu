@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <algorithm>
 #include <atomic>
 #include <map>
 #include <mutex>
@@ -310,6 +311,101 @@ int ss_sort_batch(const ss_request *reqs, uint32_t count, ss_stream_t stream) {
         if (rc != SS_OK) return rc;
     }
     return engine_sort(v.data(), count, as_stream(stream));
+}
+
+// tuning of one request, packed as in ReqDesc::tune
+static int pack_tuning(const ss_tuning &t, uint32_t &out, const char *who) {
+    uint32_t s = 0;
+    if (t.child_target) {
+        if (t.child_target < 32 || t.child_target > 65536 || (t.child_target & (t.child_target - 1))) {
+            set_error_detail("%s: child_target must be 0 or a power of two in [32, 65536], got %u", who, t.child_target);
+            return SS_ERR_INVALID;
+        }
+        while ((1u << s) < t.child_target) s++;
+    }
+    if (t.min_step > 9) {
+        set_error_detail("%s: min_step must be in [0, 9], got %u", who, t.min_step);
+        return SS_ERR_INVALID;
+    }
+    out = s | (t.min_step << 8);
+    return SS_OK;
+}
+
+int ss_sort_batch_tuned(const ss_request *reqs, const ss_tuning *tunings, uint32_t count, ss_stream_t stream) {
+    t_detail.clear();
+    if (count == 0) return SS_OK;
+    if (!reqs) {
+        set_error_detail("ss_sort_batch_tuned: NULL request array");
+        return SS_ERR_INVALID;
+    }
+    std::vector<ReqDesc> v(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const ss_request &q = reqs[i];
+        v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
+        int rc = check_req(v[i], "ss_sort_batch_tuned");
+        if (rc == SS_OK && tunings) rc = pack_tuning(tunings[i], v[i].tune, "ss_sort_batch_tuned");
+        if (rc != SS_OK) return rc;
+    }
+    return engine_sort(v.data(), count, as_stream(stream));
+}
+
+int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, double *best_ms_out, ss_stream_t stream) {
+    t_detail.clear();
+    if (!req || !best_out) {
+        set_error_detail("ss_autotune: NULL argument");
+        return SS_ERR_INVALID;
+    }
+    ReqDesc r = make_req(req->chars, req->offsets, req->lengths, req->fixed_len, req->n, req->perm_out, req->lcp_out,
+                         nullptr);
+    int rc = check_req(r, "ss_autotune");
+    if (rc != SS_OK) return rc;
+    const uint32_t n = std::min<uint32_t>(req->n, sample_n ? sample_n : 2000000u);
+    best_out->child_target = 0;
+    best_out->min_step = 0;
+    if (best_ms_out) *best_ms_out = 0;
+    if (n < 2) return SS_OK;
+    cudaStream_t st = as_stream(stream);
+    void *block = nullptr;
+    const size_t nb = ((size_t)n * 4 + 255) & ~(size_t)255;
+    cudaError_t e = scratch_alloc(&block, 2 * nb, st);
+    if (e) {
+        cudaGetLastError();
+        set_error_detail("ss_autotune: scratch allocation failed");
+        return SS_ERR_OOM;
+    }
+    r.n = n;
+    r.perm_out = (uint32_t *)block;
+    r.lcp_out = (uint32_t *)((char *)block + nb);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double best = -1;
+    const uint32_t targets[] = {256, 512, 1024, 2048};
+    const uint32_t steps[] = {1, 3, 5, 9};
+    do {
+        if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) break;
+        for (uint32_t ct : targets) {
+            for (uint32_t ms : steps) {
+                ss_tuning t{ct, ms};
+                if ((rc = pack_tuning(t, r.tune, "ss_autotune")) != SS_OK) break;
+                if ((rc = engine_sort(&r, 1, st)) != SS_OK) break;   // warm: pool, caches
+                if ((e = cudaEventRecord(e0, st))) break;
+                if ((rc = engine_sort(&r, 1, st)) != SS_OK) break;
+                if ((e = cudaEventRecord(e1, st)) || (e = cudaEventSynchronize(e1))) break;
+                float msec = 0;
+                if ((e = cudaEventElapsedTime(&msec, e0, e1))) break;
+                if (best < 0 || msec < best) {
+                    best = msec;
+                    *best_out = t;
+                }
+            }
+            if (rc != SS_OK || e) break;
+        }
+    } while (0);
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    scratch_free(block, st);
+    if (e && rc == SS_OK) rc = cuda_fail(e, "ss_autotune");
+    if (rc == SS_OK && best_ms_out) *best_ms_out = best;
+    return rc;
 }
 
 int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host,

@@ -41,9 +41,9 @@ namespace ss {
 
 // --------------------------------------------------------------- helpers
 
-__host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size) {
-    // v + 1 = 2^d about size / kChildTarget, d in [2, 10]
-    uint32_t q = (size + kChildTarget - 1) / kChildTarget;
+__host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size, uint32_t target) {
+    // v + 1 = 2^d about size / target, d in [2, 10]
+    uint32_t q = (size + target - 1) / target;
     uint32_t d = 0;
     while ((1u << d) < q) d++;
     if (d < 2) d = 2;
@@ -51,19 +51,16 @@ __host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size) {
     return d;
 }
 
-#ifndef SS_MIN_STEP
-#define SS_MIN_STEP 5
-#endif
 // Depth step of the even bucket between splitters x_{r-1} and x_r: its strings
 // share lcp(x_{r-1}, x_r) more characters (0 for the outer buckets).  A step of
-// fewer than SS_MIN_STEP characters is not taken: the bucket keeps its depth
-// and the key it carries, which still holds at least 8 - SS_MIN_STEP + 1
-// unresolved characters, and the random gather of a new key is saved.  Any
-// depth up to the shared prefix gives the same result.
-__device__ __forceinline__ uint32_t even_delta(uint64_t xl, uint64_t xr, uint32_t r, uint32_t v) {
+// fewer than min_step characters is not taken: the bucket keeps its depth and
+// the key it carries, which still holds at least 8 - min_step + 1 unresolved
+// characters, and the random gather of a new key is saved.  Any depth up to
+// the shared prefix gives the same result.
+__device__ __forceinline__ uint32_t even_delta(uint64_t xl, uint64_t xr, uint32_t r, uint32_t v, uint32_t min_step) {
     if (r == 0 || r == v) return 0u;
     uint32_t l = lcp8(xl, xr);
-    return l >= (uint32_t)SS_MIN_STEP ? l : 0u;
+    return l >= min_step ? l : 0u;
 }
 
 __host__ __device__ __forceinline__ uint32_t tiles_of(uint32_t size) { return (size + kTile - 1) / kTile; }
@@ -324,12 +321,13 @@ struct TreeSmem {
 // segment whose sample holds 27 distinct keys gets 31 splitters, not 1023.
 // The chosen depth is stored in the segment record; k_setup_big lays out the
 // counters from it.
-__global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const uint64_t *key, uint64_t *splitters) {
+__global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const ReqDesc *reqs, const uint64_t *key,
+                                                           uint64_t *splitters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TreeSmem &S = *reinterpret_cast<TreeSmem *>(smem_raw);
     __shared__ uint32_t distinct;
     BigSeg sg = segs[blockIdx.x];
-    const uint32_t dmax = choose_d(sg.size);
+    const uint32_t dmax = choose_d(sg.size, req_child_target(reqs[sg.req]));
     uint32_t v = (1u << dmax) - 1;
     uint32_t a = 2 * v + 1;            // alpha * v + alpha - 1 with alpha = 2
     uint32_t P = a + 1;
@@ -680,7 +678,7 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
                         done = np < 8;   // equal keys that hold the end of the string: all equal
                         delta = 8;
                     } else {
-                        delta = even_delta(xl[k], xr[k], r, v);
+                        delta = even_delta(xl[k], xr[k], r, v, req_min_step(reqs[sg.req]));
                     }
                     uint32_t fin = (en[k] - st[k] == 1) || done;
                     uint32_t first = tb[k] == st[k];
@@ -818,7 +816,8 @@ __device__ __forceinline__ void push_small(const TaskLists &tl, uint32_t *counte
     if (k < tl.cap[c]) tl.l[c][k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
 }
 
-__global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32_t nseg, const uint32_t *npairs_dev,
+__global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32_t nseg, const ReqDesc *reqs,
+                                                      const uint32_t *npairs_dev,
                                                       const uint32_t *scan, const uint64_t *splitters,
                                                       uint32_t next_parity, BigSeg *next_big, TaskLists tl,
                                                       Boundary *bounds, Caps caps, uint32_t *counters) {
@@ -845,7 +844,7 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
         if (has_zero(xs[r])) return;   // all equal and complete: placed by k_scatter
         delta = 8;
     } else {
-        delta = even_delta(r > 0 ? xs[r - 1] : 0ull, r < v ? xs[r] : 0ull, r, v);
+        delta = even_delta(r > 0 ? xs[r - 1] : 0ull, r < v ? xs[r] : 0ull, r, v, req_min_step(reqs[sg.req]));
     }
     uint32_t depth = sg.depth + delta;
     if (size > kSmallMax) {
@@ -854,7 +853,7 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
             BigSeg c{};
             c.begin = st; c.size = size; c.depth = depth; c.req = sg.req;
             next_big[k] = c;
-            uint32_t d = choose_d(size), t = tiles_of(size), Bc = buckets_of(d);
+            uint32_t d = choose_d(size, req_child_target(reqs[sg.req])), t = tiles_of(size), Bc = buckets_of(d);
             atomicAdd(counters + C_TILES, t);
             atomicAdd(counters + C_COUNTS, Bc * t);
             atomicAdd(counters + C_PAIRS, Bc);
@@ -1093,7 +1092,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             BigSeg s{};
             s.begin = q.base; s.size = q.n; s.depth = 0; s.req = r;
             big0.push_back(s);
-            uint32_t d = choose_d(q.n), t = tiles_of(q.n), B = buckets_of(d);
+            uint32_t d = choose_d(q.n, req_child_target(q)), t = tiles_of(q.n), B = buckets_of(d);
             tiles0 += t; counts0 += B * t; pairs0 += B;
         } else {
             SmallTask t{q.base, q.n, 0, r, 0, 0};
@@ -1148,7 +1147,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             }
             uint32_t nxt = cur ^ 1;
             // trees first: each chooses its depth; then the counter layout follows
-            SS_LAUNCH_U("build_trees", st, nbig, k_build_trees<<<nbig, kThreads, sizeof(TreeSmem), st>>>(big[cur], key[cur], splitters));
+            SS_LAUNCH_U("build_trees", st, nbig, k_build_trees<<<nbig, kThreads, sizeof(TreeSmem), st>>>(big[cur], dreqs, key[cur], splitters));
             SS_LAUNCH_U("setup_big", st, nbig, k_setup_big<<<1, 1024, 0, st>>>(big[cur], nbig, counters + C_LVL_COUNTS));
             SS_LAUNCH_U("classify", st, nelems, k_classify<<<ntiles, kThreads, sizeof(ClassifySmem), st>>>(big[cur], nbig, key[cur], splitters, obuf, counts));
             TRY(cudaGetLastError(), "classify launch");
@@ -1160,7 +1159,8 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             TRY(cudaMemsetAsync(counters + C_TILES, 0, 3 * sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_ELEMS, 0, sizeof(uint32_t), st), "reset");
             SS_LAUNCH_U("buckets", st, npairs, k_buckets<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(
-                big[cur], nbig, counters + C_LVL_PAIRS, counts, splitters, nxt, big[nxt], tl, bounds, caps, counters));
+                big[cur], nbig, dreqs, counters + C_LVL_PAIRS, counts, splitters, nxt, big[nxt], tl, bounds, caps,
+                counters));
             TRY(cudaGetLastError(), "level launch");
             TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
             TRY(cudaStreamSynchronize(st), "level sync");

@@ -35,6 +35,9 @@ constexpr int kMaxB = 2 * kMaxV + 1;           // 2047 buckets
 #ifndef SS_SMALL_MAX
 #define SS_SMALL_MAX 2048
 #endif
+#ifndef SS_MIN_STEP
+#define SS_MIN_STEP 5
+#endif
 #ifndef SS_CHILD_TARGET
 #define SS_CHILD_TARGET 512
 #endif
@@ -59,11 +62,22 @@ struct ReqDesc {
     uint32_t fixed_len;
     uint32_t n;
     uint32_t base;             // global position of the request's first element
-    uint32_t pad;
+    uint32_t tune;             // log2 child target (bits 0..7) | minimum depth step (bits 8..15); 0: defaults
     uint32_t *perm_out;
     uint32_t *lcp_out;
     int32_t *status_out;
 };
+
+// Per-request tuning: the segment size the tree depth aims at for children,
+// and the smallest depth step an even bucket takes (0 fields: the defaults).
+__host__ __device__ __forceinline__ uint32_t req_child_target(const ReqDesc &r) {
+    const uint32_t s = r.tune & 0xFFu;
+    return s ? (1u << s) : kChildTarget;
+}
+__host__ __device__ __forceinline__ uint32_t req_min_step(const ReqDesc &r) {
+    const uint32_t m = (r.tune >> 8) & 0xFFu;
+    return m ? m : (uint32_t)SS_MIN_STEP;
+}
 
 struct BigSeg {                 // a segment sorted by one multi-CTA S5 step
     uint32_t begin, size, depth, req;

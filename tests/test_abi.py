@@ -60,3 +60,16 @@ def test_product_path_does_not_touch_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "oracle" not in re.sub(r"#.*|//.*", "", txt).replace("oracle array", ""), f
+
+
+def test_tuning_ranges_checked_on_the_host():
+    """Out-of-range tunings are refused before any device work."""
+    import ctypes as C
+    import paper_1403_2056_gb300 as P
+    q = P.Request(1, 1, None, 0, 5, 1, 1, None)   # pointers are never dereferenced: the check fails first
+    arr = (P.Request * 1)(q)
+    for bad in [(48, 0), (16, 0), (1 << 17, 0), (0, 10)]:
+        t = (P.Tuning * 1)(P.Tuning(*bad))
+        rc = P.lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), C.cast(t, C.c_void_p), 1, None)
+        assert rc == -1, bad
+        assert b"ss_sort_batch_tuned" in P._detail().encode()

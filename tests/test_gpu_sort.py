@@ -308,3 +308,40 @@ def test_batch_with_different_shared_prefixes():
         want_perm, want_lcp = oracle.sort(ss)
         assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm), ss.name
         assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp), ss.name
+
+
+# ------------------------------------------------------------- tuning
+@pytest.mark.parametrize("tuning", [(256, 1), (2048, 9), (32, 3), (65536, 5), (0, 0)])
+def test_tunings_do_not_change_results(tuning):
+    """Any tuning gives the same order and LCPs (the oracle's)."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    sets = [W.url_like(60_000, seed=41), W.dna_windows(60_000, 1_200_100, 100, seed=42), W.random_lower(60_000, seed=43)]
+    reqs, outs = [], []
+    for ss in sets:
+        chars, offsets, lengths = to_device(ss)
+        perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=ss.n,
+                         perm_out=perm, lcp_out=lcp))
+        outs.append((perm, lcp))
+    P.ss_sort_batch_tuned(reqs, [tuning] * len(reqs))
+    torch.cuda.synchronize()
+    for ss, (perm, lcp) in zip(sets, outs):
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm), (ss.name, tuning)
+        assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp), (ss.name, tuning)
+
+
+def test_autotune_picks_a_candidate_and_leaves_outputs():
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = W.url_like(300_000, seed=44)
+    chars, offsets, _ = to_device(ss)
+    perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    (ct, ms_step), ms = P.ss_autotune(dict(chars=chars, offsets=offsets, lengths=None, fixed_len=0, n=ss.n,
+                                           perm_out=perm, lcp_out=lcp), sample_n=200_000)
+    assert ct in (256, 512, 1024, 2048) and ms_step in (1, 3, 5, 9) and ms > 0
+    torch.cuda.synchronize()
+    assert int((perm != -1).sum().item()) == 0 and int((lcp != -1).sum().item()) == 0
