@@ -168,6 +168,14 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
 
     breqs = [req(r, perm_b, lcp_b) for r in range(nreq)]
     preqs = [req(r, perm_p, lcp_p) for r in range(nreq)]
+    # one tuning per generator, picked by the library's autotuner on a 1 M sample of its pool
+    tuned = []
+    for g in range(3):
+        chars, offs, pool = dpools[g]
+        q = dict(chars=chars, offsets=offs, lengths=None, fixed_len=pool.fixed_len, n=pool.n, perm_out=perm_b,
+                 lcp_out=lcp_b)
+        tuned.append(P.ss_autotune(q, sample_n=1_000_000, stream=stream)[0])
+    tunings = [tuned[r % 3] for r in range(nreq)]
     P.ss_sort_batch(breqs, stream=stream)   # warm-up (pool growth, attributes)
     torch.cuda.synchronize(dev)
     bt = []
@@ -179,6 +187,22 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         bt.append(e0.elapsed_time(e1))
+    P.ss_sort_batch_tuned(breqs, tunings, stream=stream)
+    torch.cuda.synchronize(dev)
+    tt = []
+    for _ in range(2):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.ss_sort_batch_tuned(breqs, tunings, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        tt.append(e0.elapsed_time(e1))
+    tuned_perm, tuned_lcp = perm_b.clone(), lcp_b.clone()
+    P.ss_sort_batch(breqs, stream=stream)   # the default-tuned result stays in perm_b / lcp_b
+    torch.cuda.synchronize(dev)
+    tuned_same = bool(torch.equal(tuned_perm, perm_b) and torch.equal(tuned_lcp, lcp_b))
+    del tuned_perm, tuned_lcp
     for r in range(0, nreq, 97):   # warm-up of the one-request path
         q = preqs[r]
         if q["fixed_len"]:
@@ -211,6 +235,11 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
                   "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
                   "launches": "one ss_sort per request, in arrival order"},
         "speedup": tp / tb,
+        "autotuned": {"tunings_by_generator": {n_: {"child_target": t[0], "min_step": t[1]}
+                                                for n_, t in zip(["random", "url_like", "dna_like"], tuned)},
+                      "ms": float(np.median(tt)), "strings_per_s": total / (float(np.median(tt)) / 1e3),
+                      "how": "ss_autotune on a 1 M sample of each generator's pool, then one ss_sort_batch_tuned call",
+                      "outputs_equal_default": tuned_same},
         "outputs_equal": equal,
     }
     del perm_b, lcp_b, perm_p, lcp_p, dpools
