@@ -1079,7 +1079,6 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     uint4 *pchunks = c.take<uint4>(N / kPrefChunk + caps.big + 1);
 
     int rc = SS_OK;
-    uint32_t *hc = (uint32_t *)host_staging(sizeof(uint32_t) * C_NUM + 64);
     // initial segments: one per request
     std::vector<BigSeg> big0;
     std::vector<SmallTask> s_task[kClasses];
@@ -1111,22 +1110,40 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         cudaError_t _e = (x);                            \
         if (_e != cudaSuccess) { rc = cuda_fail(_e, what); goto done; } \
     } while (0)
-    TRY(cudaMemcpyAsync(dreqs, reqs.data(), sizeof(ReqDesc) * nreq, cudaMemcpyHostToDevice, st), "copy requests");
-    TRY(cudaMemcpyAsync(counters, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, st), "copy counters");
-    if (!big0.empty()) TRY(cudaMemcpyAsync(big[0], big0.data(), sizeof(BigSeg) * big0.size(), cudaMemcpyHostToDevice, st), "copy big");
-    for (int k = 0; k < kClasses; k++)
-        if (!s_task[k].empty())
-            TRY(cudaMemcpyAsync(tl.l[k], s_task[k].data(), sizeof(SmallTask) * s_task[k].size(), cudaMemcpyHostToDevice, st),
-                "copy base-case tasks");
+    for (const BigSeg &b : big0)
+        for (uint32_t x = 0; x < b.size; x += kPrefChunk)
+            pchunk_host.push_back(make_uint4(b.begin + x, b.begin + std::min(b.size, x + kPrefChunk), b.req, 0));
+    // Everything the first launches read goes up from one pinned staging
+    // buffer, asynchronously; the counter readbacks land in its own tail.
+    uint32_t *hc;
+    {
+        size_t sz[4 + kClasses] = {sizeof(ReqDesc) * nreq, sizeof(hcnt), sizeof(BigSeg) * big0.size(),
+                                   sizeof(uint4) * pchunk_host.size()};
+        for (int k = 0; k < kClasses; k++) sz[4 + k] = sizeof(SmallTask) * s_task[k].size();
+        size_t at[4 + kClasses + 1];
+        at[0] = 0;
+        for (int k = 0; k < 4 + kClasses; k++) at[k + 1] = at[k] + ((sz[k] + 15) & ~(size_t)15);
+        char *up = (char *)host_staging(at[4 + kClasses] + sizeof(uint32_t) * C_NUM + 64);
+        hc = (uint32_t *)(up + at[4 + kClasses]);
+        memcpy(up + at[0], reqs.data(), sz[0]);
+        memcpy(up + at[1], hcnt, sz[1]);
+        if (sz[2]) memcpy(up + at[2], big0.data(), sz[2]);
+        if (sz[3]) memcpy(up + at[3], pchunk_host.data(), sz[3]);
+        for (int k = 0; k < kClasses; k++)
+            if (sz[4 + k]) memcpy(up + at[4 + k], s_task[k].data(), sz[4 + k]);
+        TRY(cudaMemcpyAsync(dreqs, up + at[0], sz[0], cudaMemcpyHostToDevice, st), "copy requests");
+        TRY(cudaMemcpyAsync(counters, up + at[1], sz[1], cudaMemcpyHostToDevice, st), "copy counters");
+        if (sz[2]) TRY(cudaMemcpyAsync(big[0], up + at[2], sz[2], cudaMemcpyHostToDevice, st), "copy big");
+        if (sz[3]) TRY(cudaMemcpyAsync(pchunks, up + at[3], sz[3], cudaMemcpyHostToDevice, st), "copy chunks");
+        for (int k = 0; k < kClasses; k++)
+            if (sz[4 + k])
+                TRY(cudaMemcpyAsync(tl.l[k], up + at[4 + k], sz[4 + k], cudaMemcpyHostToDevice, st), "copy base-case tasks");
+    }
     {
         uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
         SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0], key[0], key[1]));
         if (!big0.empty()) {
-            for (const BigSeg &b : big0)
-                for (uint32_t x = 0; x < b.size; x += kPrefChunk)
-                    pchunk_host.push_back(make_uint4(b.begin + x, b.begin + std::min(b.size, x + kPrefChunk), b.req, 0));
             const uint32_t nch = (uint32_t)pchunk_host.size();
-            TRY(cudaMemcpyAsync(pchunks, pchunk_host.data(), sizeof(uint4) * nch, cudaMemcpyHostToDevice, st), "copy chunks");
             TRY(cudaMemsetAsync(shared, 0xFF, sizeof(uint32_t) * nreq, st), "reset shared prefix");
             SS_LAUNCH_U("shared_prefix", st, elems0, k_shared_prefix<<<nch, 256, 0, st>>>(pchunks, dreqs, key[0], shared));
             SS_LAUNCH_U("skip_prefix", st, elems0, k_skip_prefix<<<nch, 256, 0, st>>>(pchunks, key[1], key[0], shared));
@@ -1137,9 +1154,9 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     {
         uint32_t nbig = (uint32_t)big0.size(), ntiles = tiles0, ncounts = counts0, npairs = pairs0, nelems = elems0;
         uint32_t cur = 0;
-        // the host-built first list must be synchronized before its vectors go away
-        TRY(cudaStreamSynchronize(st), "sync after setup");
+        bool ran = false;
         while (nbig > 0) {
+            ran = true;
             if (ncounts > caps.counts) {
                 set_error_detail("internal: counters %u exceed capacity %u", ncounts, caps.counts);
                 rc = SS_ERR_INTERNAL;
@@ -1172,10 +1189,8 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             nelems = hc[C_ELEMS];
             cur = nxt;
         }
-        if (!hc[C_ERROR] || nbig == 0) {
-            TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
-            TRY(cudaStreamSynchronize(st), "sync");
-        }
+        // after a level the counters are fresh in hc; without one they are the host's own
+        if (!ran) memcpy(hc, hcnt, sizeof(hcnt));
         if (hc[C_ERROR]) {
             set_error_detail("device-side check failed: code %u info %u", hc[C_ERROR], hc[C_ERRINFO]);
             rc = SS_ERR_INTERNAL;
