@@ -584,7 +584,10 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
     const size_t tot64 = ((size_t)total + a64) & ~a64;
     // thread starts: one per kMergeItems outputs, at most one partial window per pair
     const size_t max_starts = ((size_t)total / kMergeTile + K + 2) * kMergeTileThreads;
-    size_t bytes = 4ull * 8 * tot64 + 4ull * 4 * tot64 + 4ull * (4 * (K + 2) + 64) + sizeof(Coarse) * max_entries +
+    // one table region per round (rb, bases, cbase, wbase), so no round waits for the host
+    const size_t tstride = (4 * (K + 2) + 63) & ~(size_t)63;
+    const size_t nrt = rounds ? rounds : 1;
+    size_t bytes = 4ull * 8 * tot64 + 4ull * 4 * tot64 + 4ull * tstride * nrt + sizeof(Coarse) * max_entries +
                    sizeof(MergeStart) * max_starts + 4096;
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
@@ -600,11 +603,11 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
     uint32_t *ckd_buf[2] = {(uint32_t *)(ck_buf[1] + tot64), (uint32_t *)(ck_buf[1] + tot64) + tot64};
     uint32_t *tmp_perm = ckd_buf[1] + tot64;
     uint32_t *tmp_lcp = tmp_perm + tot64;
-    uint32_t *d_rb = tmp_lcp + tot64;   // rb[R+1], bases[R], cbase[pairs]
-    Coarse *d_coarse = (Coarse *)(d_rb + ((4 * (K + 2) + 63) & ~63u));
+    uint32_t *d_tables = tmp_lcp + tot64;   // per round: rb[R+1], bases[R], cbase[pairs], wbase[pairs]
+    Coarse *d_coarse = (Coarse *)(d_tables + tstride * nrt);
     MergeStart *d_starts = (MergeStart *)(d_coarse + ((max_entries + 63) & ~(size_t)63));
     int rc = SS_OK;
-    uint32_t *stage = (uint32_t *)host_staging(sizeof(uint32_t) * 4 * (K + 2));
+    uint32_t *stage_all = (uint32_t *)host_staging(sizeof(uint32_t) * tstride * nrt);
     do {
         if (R <= 1) {
             uint32_t base = rbase.empty() ? 0u : rbase[0];
@@ -623,7 +626,9 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             bool last = round == rounds;
             uint32_t *dst_p = last ? perm_out : ((rounds - round) % 2 ? tmp_perm : perm_out);
             uint32_t *dst_l = last ? lcp_out : ((rounds - round) % 2 ? tmp_lcp : lcp_out);
-            // staging: rb[R+1], bases[R] (first round), cbase[pairs]
+            // staging: rb[R+1], bases[R] (first round), cbase[pairs], wbase[pairs]
+            uint32_t *stage = stage_all + tstride * (round - 1);
+            uint32_t *d_rb = d_tables + tstride * (round - 1);
             const uint32_t npairs = (R + 1) / 2;
             memcpy(stage, rb.data(), sizeof(uint32_t) * (R + 1));
             if (round == 1) memcpy(stage + (R + 1), rbase.data(), sizeof(uint32_t) * R);
@@ -663,8 +668,6 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
                 set, src_p, src_l, d_rb, R, bases, d_wb, npairs, dst_p, dst_l, d_coarse, d_cb, d_starts, src_o, dst_o,
                 src_ck, src_ckd, dst_ck, dst_ckd));
             if ((e = cudaGetLastError())) break;
-            // the staging buffer is reused next round: wait for the copy
-            if ((e = cudaStreamSynchronize(st))) break;
             std::vector<uint32_t> nrb{0};
             for (uint32_t k = 2; k <= R; k += 2) nrb.push_back(rb[k]);
             if (R % 2) nrb.push_back(rb[R]);
@@ -673,6 +676,7 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             src_p = dst_p;
             src_l = dst_l;
         }
+        if (!e) e = cudaStreamSynchronize(st);
     } while (0);
     if (e) rc = cuda_fail(e, "ss_merge");
     scratch_free(block, st);
