@@ -345,3 +345,16 @@ def test_autotune_picks_a_candidate_and_leaves_outputs():
     assert ct in (256, 512, 1024, 2048) and ms_step in (1, 3, 5, 9) and ms > 0
     torch.cuda.synchronize()
     assert int((perm != -1).sum().item()) == 0 and int((lcp != -1).sum().item()) == 0
+
+
+def test_readme_example():
+    """The usage example of the README."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    strs = [b"banana", b"apple", b"cherry", b"apple"]
+    chars = torch.tensor(list(b"".join(s + b"\0" for s in strs)), dtype=torch.uint8, device="cuda")
+    offsets = torch.tensor(np.cumsum([0] + [len(s) + 1 for s in strs[:-1]]), dtype=torch.int64, device="cuda")
+    perm = torch.empty(4, dtype=torch.int32, device="cuda")
+    lcp = torch.empty(4, dtype=torch.int32, device="cuda")
+    P.ss_sort(chars, offsets, 4, perm, lcp)
+    assert perm.tolist() == [1, 3, 0, 2] and lcp.tolist() == [0, 5, 0, 0]
