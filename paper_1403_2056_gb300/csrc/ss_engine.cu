@@ -1079,6 +1079,8 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     uint4 *pchunks = c.take<uint4>(N / kPrefChunk + caps.big + 1);
 
     int rc = SS_OK;
+    bool any_status = false;   // some request wants its status written on the device
+    for (const ReqDesc &q : reqs) any_status = any_status || q.status_out;
     // initial segments: one per request
     std::vector<BigSeg> big0;
     std::vector<SmallTask> s_task[kClasses];
@@ -1206,7 +1208,8 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         // per-launch timing on they run one after another, so each kernel's time
         // is its own.
         AuxStreams &ax = aux_streams();
-        const bool fork = SS_BASE_CONCURRENT && ax.ok && !prof_on();
+        const int nclasses = (hc[C_NTASK + 1] > 0) + (hc[C_NTASK + 2] > 0) + (hc[C_NTASK + 3] > 0);
+        const bool fork = SS_BASE_CONCURRENT && nclasses > 1 && ax.ok && !prof_on();
         cudaStream_t s1 = fork ? ax.s[0] : st, s2 = fork ? ax.s[1] : st;
         if (fork) {
             TRY(cudaEventRecord(ax.ev[0], st), "fork");
@@ -1247,8 +1250,10 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             SS_LAUNCH_U("boundary", st, nb, k_boundary<<<grid, 256, 0, st>>>(bounds, nb, dreqs));
             TRY(cudaGetLastError(), "boundary launch");
         }
-        SS_LAUNCH("status", st, k_status<<<(nreq + 255) / 256, 256, 0, st>>>(dreqs, nreq, 0));
-        TRY(cudaGetLastError(), "status launch");
+        if (any_status) {
+            SS_LAUNCH("status", st, k_status<<<(nreq + 255) / 256, 256, 0, st>>>(dreqs, nreq, 0));
+            TRY(cudaGetLastError(), "status launch");
+        }
         TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
         TRY(cudaStreamSynchronize(st), "final sync");
         if (hc[C_ERROR]) {
@@ -1259,6 +1264,10 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     }
 done:
 #undef TRY
+    if (rc == SS_ERR_INTERNAL && any_status) {   // a device-side check failed: the requests learn it too
+        k_status<<<(nreq + 255) / 256, 256, 0, st>>>(dreqs, nreq, rc);
+        cudaStreamSynchronize(st);
+    }
     scratch_free(block, st);
     return rc;
 }
