@@ -6,9 +6,9 @@
  * Bingmann, Eberle, Sanders, "Engineering Parallel String Sorting": strings
  * over the alphabet {1..255} (unsigned bytes, no 0 byte inside a string),
  * ordered character by character with the end of a string below every
- * character.  The method is super scalar string sample sort (Section 3.3,
- * Algorithm 1) with LCP saving (Section 4.4) and LCP-aware merging of sorted
- * runs (Section 4.1-4.3, Algorithms 2-4), run on one GPU.
+ * character.  The method is super scalar string sample sort (Section 4.3,
+ * Algorithm 1) with LCP saving (Section 5.4) and LCP-aware merging of sorted
+ * runs (Section 5.1-5.3, Algorithms 2-4), run on one GPU.
  *
  * Conventions for every entry point:
  *   - Pointers named *_dev are DEVICE pointers owned by the caller; the
@@ -59,7 +59,7 @@ typedef enum {
 
 /*
  * ss_sort -- sort n NUL-terminated strings (Section 2; Algorithm 1 applied
- * recursively, Section 3.5; LCP saving, Section 4.4).
+ * recursively, Section 4.5; LCP saving, Section 5.4).
  *   chars_dev   : string bytes; string i starts at chars_dev[offsets_dev[i]]
  *                 and ends at the first 0 byte (the terminator).
  *   offsets_dev : uint64[n], byte offset of each string.
@@ -93,7 +93,7 @@ int ss_sort_ex(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint
  *   runs : 0 or 1 sorts the set in one piece.  runs = K > 1 sorts K
  *          index-contiguous runs together (as one ss_sort_batch) and merges
  *          them with ss_merge, the paper's "independent sorters, then LCP
- *          merge" structure (Section 4); the result is the same.
+ *          merge" structure (Section 5); the result is the same.
  */
 int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len_host, const uint64_t *offsets_host,
                  const uint32_t *lengths_host, uint32_t fixed_len, uint32_t n, uint32_t runs,
@@ -119,7 +119,7 @@ typedef struct {
  * ss_sort_batch -- sort `count` independent requests together (host array
  * reqs_host).  All requests advance through the same recursion levels in
  * the same kernel launches (the paper's job queue of independent
- * subproblems, Section 3.5, moved onto the device).  The sum of all n must
+ * subproblems, Section 4.5, moved onto the device).  The sum of all n must
  * not exceed 2^32 - 2.  Results equal those of one ss_sort_ex per request.
  */
 int ss_sort_batch(const ss_request *reqs_host, uint32_t count, ss_stream_t stream);
@@ -158,7 +158,7 @@ int ss_autotune(const ss_request *req_host, uint32_t sample_n, ss_tuning *best_o
 
 /*
  * ss_merge -- LCP-aware merge of K sorted runs of one string set
- * (Sections 4.1-4.3: LCP-Compare, Algorithm 2; binary LCP-merge,
+ * (Sections 5.1-5.3: LCP-Compare, Algorithm 2; binary LCP-merge,
  * Algorithm 3; the K-way merge is done as ceil(log2 K) rounds of pairwise
  * merges partitioned by merge path).
  *   chars_dev/offsets_dev/lengths_dev/fixed_len : the string set, as ss_sort_ex.
@@ -208,7 +208,7 @@ int ss_merge_noalloc(const uint8_t *chars_dev, const uint64_t *offsets_dev, cons
                      uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
 
 /*
- * ss_gather_keys -- chars_h (Section 3.4): for each string i, the 8 bytes at
+ * ss_gather_keys -- chars_h (Section 4.4): for each string i, the 8 bytes at
  * depth depth_dev[i] as a big-endian uint64 (first character in the most
  * significant byte), bytes past the end of the string zero.
  *   depth_dev : uint32[n] depths (each at most the string's length).
@@ -219,7 +219,7 @@ int ss_gather_keys(const uint8_t *chars_dev, const uint64_t *offsets_dev, const 
                    ss_stream_t stream);
 
 /*
- * ss_splitters -- splitter selection of Section 3.4 on the device: sort the
+ * ss_splitters -- splitter selection of Section 4.4 on the device: sort the
  * sample (a keys) and pick v = 2^d - 1 in-order splitters with the recursive
  * scheme that skips samples equal to the chosen middle splitter.
  *   sample_dev : uint64[a], 1 <= a <= 2047; d in [1, 10].
@@ -245,7 +245,7 @@ int ss_classify(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, uin
 
 /*
  * Sort server -- continuous batching of independent requests (the paper's
- * job queue of independent subproblems, Section 3.5, one level up: requests
+ * job queue of independent subproblems, Section 4.5, one level up: requests
  * arriving over time).  The server admits submitted requests in arrival order
  * while the scratch memory of the admitted, unfinished ones fits
  * budget_bytes; each of `workers` host threads drives its own CUDA stream and,

@@ -14,7 +14,7 @@
  *   orc_stats           L = sum of the LCP array and the distinguishing
  *                       prefix size D (Section 2), D by its closed form.
  *   orc_chars_h         chars_h(s): the 8 characters at depth h, big-endian,
- *                       zero past the end of the string (Section 3.4).
+ *                       zero past the end of the string (Section 4.4).
  *   orc_s5_tree         level-order splitter tree t from in-order splitters
  *                       x (Algorithm 1, tree construction; Figure 1).
  *   orc_s5_classify     classification of keys by descending t and one
@@ -23,7 +23,7 @@
  *                       redistribution (Algorithm 1, count / prefix sum /
  *                       redistribute).
  *   orc_s5_pick         splitter selection from a sorted sample with the
- *                       recursive "skip equal samples" scheme (Section 3.4).
+ *                       recursive "skip equal samples" scheme (Section 4.4).
  *   orc_lcp_insertion   LCP-aware insertion sort (Algorithm 5).
  *   orc_lcp_compare     LCP-Compare (Algorithm 2).
  *   orc_lcp_merge2      binary LCP-merge (Algorithm 3).
@@ -165,7 +165,7 @@ void orc_stats(const uint8_t *chars, const uint64_t *offsets, const uint32_t *le
     *N_out = N;
 }
 
-/* -------------------------------------------- chars_h (Section 3.4, w = 8) */
+/* -------------------------------------------- chars_h (Section 4.4, w = 8) */
 
 uint64_t orc_chars_h(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths,
                      uint32_t fixed_len, uint64_t i, uint64_t h)
@@ -252,7 +252,7 @@ void orc_s5_distribute(const uint16_t *bucket, uint64_t n, uint32_t v,
 }
 
 /*
- * Splitter selection of Section 3.4 from a sorted sample p[0..a-1]: take the
+ * Splitter selection of Section 4.4 from a sorted sample p[0..a-1]: take the
  * middle sample of range [lo, hi) as the middle splitter of the current
  * subtree, skip the samples equal to it on both sides, recurse on the left
  * and right remainders.  An empty range repeats the nearest splitter on its

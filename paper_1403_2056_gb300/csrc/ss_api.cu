@@ -243,7 +243,7 @@ int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *off
             ReqDesc r = make_req(d_chars, d_off, d_len, fixed_len, n, d_perm, d_lcp, nullptr);
             rc = engine_sort(&r, 1, st);
         } else {
-            // index-contiguous runs sorted together, then merged (Section 4)
+            // index-contiguous runs sorted together, then merged (Section 5)
             std::vector<ReqDesc> rq(runs);
             std::vector<uint32_t> rb(runs + 1);
             for (uint32_t k = 0; k <= runs; k++) rb[k] = (uint32_t)((uint64_t)n * k / runs);

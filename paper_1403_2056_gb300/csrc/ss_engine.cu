@@ -3,12 +3,12 @@
 // k_init gives every string its index, byte offset and first characters;
 // a large request whose strings all share a prefix starts that deep
 // (k_shared_prefix, k_skip_prefix).  Then every recursion level of the
-// paper's S5 (Algorithm 1, applied recursively as in Section 3.5) runs as a
+// paper's S5 (Algorithm 1, applied recursively as in Section 4.5) runs as a
 // handful of kernels over ALL segments that are still larger than the
 // base-case threshold, whatever request they belong to:
 //
 //   k_build_trees  sample (alpha = 2), sort, pick splitters with the
-//                  skip-equal-samples recursion (Section 3.4)      one CTA / segment
+//                  skip-equal-samples recursion (Section 4.4)      one CTA / segment
 //   k_classify     tree descent + equality test per 8-byte key,
 //                  bucket buffer, per-tile histogram (Alg. 1 loops)  one CTA / tile
 //   k_scan_*       exclusive prefix sum over the bucket-major
@@ -23,7 +23,7 @@
 // case (k_small_warp / k_base_cta in ss_base.cuh), which also emits their LCPs
 // (the role of LCP insertion sort, Algorithm 5).  The LCP between the last
 // string of one bucket and the first of the next is depth + lcp of their keys
-// at that depth (Section 4.4, "LCPs for free"), computed in k_boundary once all
+// at that depth (Section 5.4, "LCPs for free"), computed in k_boundary once all
 // strings are placed.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -259,7 +259,7 @@ __device__ void bitonic_u64(uint64_t *s, uint32_t n) {
     }
 }
 
-// Splitter pick of Section 3.4 on a sorted sample s[0..a): breadth-first over
+// Splitter pick of Section 4.4 on a sorted sample s[0..a): breadth-first over
 // the implicit tree; node state (lo, hi, has_right, right, left).
 struct PickNode {
     uint32_t lo, hi, has_right, pad;
@@ -317,7 +317,7 @@ struct TreeSmem {
 
 // The sample has alpha * v + alpha - 1 keys (alpha = 2) for the tree size the
 // segment's length allows (choose_d); the tree actually built has just enough
-// levels for the distinct keys of the sample (adaptivity, Section 7): a
+// levels for the distinct keys of the sample (adaptivity, Section 8.1): a
 // segment whose sample holds 27 distinct keys gets 31 splitters, not 1023.
 // The chosen depth is stored in the segment record; k_setup_big lays out the
 // counters from it.
@@ -421,7 +421,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict_
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) S.cnt[b] = 0;
     __syncthreads();
 
-    // four interleaved descents per thread (Section 3.3: unrolled, interleaved loops)
+    // four interleaved descents per thread (Section 4.3: unrolled, interleaved loops)
 #pragma unroll
     for (int it = 0; it < kItems; it += 4) {
         uint32_t p[4], node[4];
@@ -589,7 +589,7 @@ __device__ __forceinline__ uint32_t bucket_start(const BigSeg &sg, const uint32_
 #endif
 constexpr int kScatterBatch = SS_SCATTER_BATCH;   // elements whose reads are in flight together, per thread
 
-// Stable out-of-place redistribution of one tile (Section 3.3, the second hot
+// Stable out-of-place redistribution of one tile (Section 4.3, the second hot
 // loop).  Each element's rank inside the tile is fixed first (lanes in order
 // inside a warp, warps in order inside the tile); then each payload array in
 // turn is reordered through shared memory into tile-local bucket order, so that

@@ -4,7 +4,7 @@
 //   idx[2][N]  u32  string index (request-local) per global position, double buffered
 //   key[2][N]  u64  the 8 characters at the current depth of the element's segment
 //   obuf[N]    u16  bucket of each element in the current level (the "oracle" array
-//                   of Section 3.4; named bucket buffer here)
+//                   of Section 4.4; named bucket buffer here)
 //   counts[]   u32  per (segment, bucket, tile) counters, bucket-major per segment
 //   splitters  u64  in-order splitters of every big segment of the current level
 //   lists      big segments (per level), small tasks and boundary records

@@ -1,8 +1,8 @@
-// LCP-aware merging of sorted runs (Section 4: LCP-Compare, Algorithm 2;
+// LCP-aware merging of sorted runs (Section 5: LCP-Compare, Algorithm 2;
 // binary LCP-merge, Algorithm 3) on one GPU.
 //
 // The paper merges K runs with one LCP-aware tournament tree per job and
-// splits jobs by LCP minima (Section 4.3).  On the GPU the K-way merge is
+// splits jobs by LCP minima (Section 5.3).  On the GPU the K-way merge is
 // ceil(log2 K) rounds of pairwise merges.  Inside a round the output of every
 // pair is cut by merge path (binary search on the cross diagonal, full string
 // comparisons) at every kCoarse outputs, with the characters each window's
@@ -102,7 +102,7 @@ __device__ __forceinline__ uint32_t path_search(const ReqDesc &S, const PairView
 // Per round, for every run entry: its string offset (first round: looked up
 // and written to off; later rounds: carried in off) and its cached characters
 // ck = the 8 characters at its run LCP (0 for a run's first entry), the
-// distinguishing characters that the caching variant of Section 4.4 keeps so
+// distinguishing characters that the caching variant of Section 5.4 keeps so
 // that LCP-Compare's first character comparison needs no string access.
 __global__ void k_run_prep(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R,
                            const uint32_t *rbase, uint32_t total, int lookup_offsets, uint64_t *off, uint64_t *ck,

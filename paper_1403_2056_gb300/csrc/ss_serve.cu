@@ -1,7 +1,7 @@
 // Sort server: continuous batching of independent sort requests on one GPU.
 //
 // The paper's parallel sorter keeps a job queue of independent subproblems and
-// lets idle threads take the next one (Section 3.5).  Serving many callers is
+// lets idle threads take the next one (Section 4.5).  Serving many callers is
 // the same problem one level up: requests arrive over time, each is an
 // independent sort, and the device should be kept busy without letting a
 // request wait behind a long queue.  The server admits requests in arrival

@@ -1,4 +1,4 @@
-"""Seeded synthetic string sets shaped like the paper's inputs (Section 6.2, Table 3).
+"""Seeded synthetic string sets shaped like the paper's inputs (Section 7.2, Table 3).
 
 This module only draws random bytes and lays them out; it holds none of the
 sorting arithmetic.  Both the CPU oracle tests and the CUDA path read the
@@ -160,7 +160,7 @@ def random_lower(n: int = 200_000, seed: int = 1, min_len: int = 8, max_len: int
 
 
 def paper_random(n: int, seed: int = 11) -> StringSet:
-    """The paper's Random set (Section 6.2): length U[0,20), bytes U[33,127), NUL-terminated."""
+    """The paper's Random set (Section 7.2): length U[0,20), bytes U[33,127), NUL-terminated."""
     rng = np.random.default_rng(seed)
     lengths = rng.integers(0, 20, n).astype(np.uint64)
     offsets, total = _layout_terminated(lengths)
