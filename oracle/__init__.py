@@ -57,6 +57,7 @@ def _load():
             lib.orc_chars_h_all.argtypes = set_args + [C.c_uint64, _u64p, _u64p]
             lib.orc_s5_tree.argtypes = [_u64p, C.c_uint32, _u64p]
             lib.orc_s5_classify.argtypes = [_u64p, C.c_uint64, _u64p, C.c_uint32, _u16p]
+            lib.orc_s5_classify_equal.argtypes = [_u64p, C.c_uint64, _u64p, C.c_uint32, _u16p]
             lib.orc_s5_distribute.argtypes = [_u16p, C.c_uint64, C.c_uint32, _u64p, _u64p]
             lib.orc_s5_pick.argtypes = [_u64p, C.c_uint64, C.c_uint32, _u64p]
             lib.orc_lcp_compare.argtypes = set_args + [C.c_uint64] * 4 + [_u64p]
@@ -157,6 +158,16 @@ def s5_classify(keys, x):
     x = _c(x, np.uint64)
     b = np.empty(keys.shape[0], np.uint16)
     lib.orc_s5_classify(_p(keys, _u64p), keys.shape[0], _p(x, _u64p), x.shape[0], _p(b, _u16p))
+    return b
+
+
+def s5_classify_equal(keys, x):
+    """S5-Equal: equality test at every node of one descent (Section 4.4)."""
+    lib = _load()
+    keys = _c(keys, np.uint64)
+    x = _c(x, np.uint64)
+    b = np.empty(keys.shape[0], np.uint16)
+    lib.orc_s5_classify_equal(_p(keys, _u64p), keys.shape[0], _p(x, _u64p), x.shape[0], _p(b, _u16p))
     return b
 
 

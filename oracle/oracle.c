@@ -19,6 +19,8 @@
  *                       x (Algorithm 1, tree construction; Figure 1).
  *   orc_s5_classify     classification of keys by descending t and one
  *                       equality test (Algorithm 1, classification loop).
+ *   orc_s5_classify_equal  the S5-Equal alternative of Section 4.4: an
+ *                       equality test at every node of one descent.
  *   orc_s5_distribute   bucket counts, prefix sum and stable out-of-place
  *                       redistribution (Algorithm 1, count / prefix sum /
  *                       redistribute).
@@ -223,6 +225,44 @@ void orc_s5_classify(const uint64_t *keys, uint64_t n, const uint64_t *x, uint32
         uint32_t r = i - (v + 1);
         uint32_t m = 2 * r;
         if (r < v && x[r] == c) m++;
+        bucket[j] = (uint16_t)m;
+    }
+    free(t);
+}
+
+/*
+ * S5-Equal (the fourth way of placing the equality test in Section 4.4): one
+ * descent of t per key that tests c = t_i at every node and stops at the
+ * first node that holds c.  Node i of level l (2^l <= i < 2^(l+1)) holds the
+ * in-order splitter x_k with k = (2 (i - 2^l) + 1) 2^(d-l-1) - 1 (the inverse
+ * of the level-order layout of Figure 1), so a stop there is bucket 2k + 1.
+ * A descent that meets no equal splitter ends at leaf i of level d in the
+ * even bucket 2 (i - 2^d).  With distinct splitters this is orc_s5_classify's
+ * bucket; where a splitter value repeats, c stops at the copy nearest the
+ * root on its path, an equality bucket of the same value.
+ */
+void orc_s5_classify_equal(const uint64_t *keys, uint64_t n, const uint64_t *x, uint32_t v,
+                           uint16_t *bucket)
+{
+    uint64_t *t = (uint64_t *)malloc(sizeof(uint64_t) * (v ? v : 1));
+    orc_s5_tree(x, v, t);
+    uint32_t d = 0;
+    while ((1u << d) < v + 1) d++;
+    for (uint64_t j = 0; j < n; j++) {
+        uint64_t c = keys[j];
+        uint32_t i = 1;
+        int stopped = 0;
+        uint32_t m = 0;
+        for (uint32_t lvl = 0; lvl < d; lvl++) {
+            if (c == t[i - 1]) {
+                uint32_t k = ((2 * (i - (1u << lvl)) + 1) << (d - lvl - 1)) - 1;
+                m = 2 * k + 1;
+                stopped = 1;
+                break;
+            }
+            i = 2 * i + (c > t[i - 1] ? 1 : 0);
+        }
+        if (!stopped) m = 2 * (i - (1u << d));
         bucket[j] = (uint16_t)m;
     }
     free(t);

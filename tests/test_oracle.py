@@ -212,6 +212,58 @@ def test_s5_classify_full_64bit_keys():
     assert b.tolist() == [_closed_form_bucket(int(c), xs) for c in keys]
 
 
+def test_fig1_s5_equal():
+    """S5-Equal on Figure 1's tree: each splitter lands in its equality bucket
+    (stopping at its own node, whichever level), keys between splitters in the
+    even buckets."""
+    lines = [l.split() for l in open(os.path.join(GOLDEN, "fig1_tree_v7.txt")) if l.strip() and not l.startswith("#")]
+    eq = [int(v) for v in lines[1]]
+    x = np.array([10 * (i + 1) for i in range(7)], np.uint64)
+    assert oracle.s5_classify_equal(x, x).tolist() == eq
+    between = np.array([5 + 10 * i for i in range(8)], np.uint64)   # below x0, between, above x6
+    assert oracle.s5_classify_equal(between, x).tolist() == [2 * i for i in range(8)]
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 4, 6, 8, 10])
+def test_s5_equal_distinct_splitters_closed_form(d):
+    """With distinct splitters S5-Equal gives the closed-form bucket."""
+    rng = np.random.default_rng(100 + d)
+    v = (1 << d) - 1
+    x = np.sort(rng.choice(10 * v + 20, v, replace=False).astype(np.uint64) + 1)
+    keys = np.concatenate([rng.integers(0, 10 * v + 30, 4000).astype(np.uint64), x, x - 1, x + 1])
+    xs = [int(y) for y in x]
+    assert oracle.s5_classify_equal(keys, x).tolist() == [_closed_form_bucket(int(c), xs) for c in keys]
+
+
+def _highest_copy(xs, c):
+    """Among the in-order positions k with x_k = c (a contiguous range), the one
+    highest in the complete tree: the most trailing zero bits of k + 1."""
+    ks = [k for k, y in enumerate(xs) if y == c]
+    return max(ks, key=lambda k: ((k + 1) & -(k + 1)))
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 7, 9])
+def test_s5_equal_repeated_splitters(d):
+    """Repeated splitter values (what the pick emits for a sample with few
+    distinct keys): keys equal to no splitter keep the closed-form bucket; a
+    key equal to a splitter value lands in the equality bucket of the copy
+    highest in the tree; distributing by either bucketing gives the same
+    order."""
+    rng = np.random.default_rng(200 + d)
+    v = (1 << d) - 1
+    x = np.sort(rng.integers(0, max(3, v // 3), v).astype(np.uint64) * 4)   # many repeats
+    keys = rng.integers(0, 4 * max(3, v // 3) + 4, 3000).astype(np.uint64)
+    xs = [int(y) for y in x]
+    b_eq = oracle.s5_classify_equal(keys, x)
+    b_cf = oracle.s5_classify(keys, x)
+    for c, be, bc in zip(keys.tolist(), b_eq.tolist(), b_cf.tolist()):
+        if c in xs:
+            assert be == 2 * _highest_copy(xs, c) + 1
+        else:
+            assert be == bc
+    assert np.argsort(b_eq, kind="stable").tolist() == np.argsort(b_cf, kind="stable").tolist()
+
+
 def test_s5_distribute_stable():
     rng = np.random.default_rng(2)
     v = 31
