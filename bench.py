@@ -127,14 +127,57 @@ def other_workloads(P, torch, dev, stream, peak):
         nl, tms, units = prof[dom]
         bpu = BYTES_PER_UNIT.get(dom)
         ach = units * bpu / (tms / 1e3) / 1e9 if bpu else None
+        cls_cmp = compare_classifiers(P, torch, dev, stream, [dict(chars=chars, offsets=offsets, lengths=None,
+                                                                   fixed_len=ss.fixed_len, n=n, perm_out=perm,
+                                                                   lcp_out=lcp)])
         out[name] = {"workload": desc, "n": n, "ms": ms, "strings_per_s": n / (ms / 1e3),
                      "d_gb_per_s": D / (ms / 1e3) / 1e9,
                      "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
                                              "frac": balg / (ms / 1e3) / 1e9 / peak},
                      "dominant_kernel": {"kernel": dom, "ms": tms, "share": tms / sum(v[1] for v in prof.values()),
-                                         "achieved_gbs": ach, "frac": (ach / peak) if ach else None}}
+                                         "achieved_gbs": ach, "frac": (ach / peak) if ach else None},
+                     "classifiers": cls_cmp}
         del chars, offsets, perm, lcp
         torch.cuda.empty_cache()
+    return out
+
+
+CLASSIFIERS = ("unroll", "equal", "jump")
+
+
+def compare_classifiers(P, torch, dev, stream, reqs, reps=5):
+    """The same requests sorted with each classifier (one ss_sort_batch_tuned
+    call): median time of the call, the classification kernels' time per call
+    from the library's launch events, and whether the outputs equal the
+    default classifier's."""
+    out, ref = {}, None
+    for cls, name in enumerate(CLASSIFIERS):
+        tun = [(0, 0, cls)] * len(reqs)
+        P.ss_sort_batch_tuned(reqs, tun, stream=stream)
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            P.ss_sort_batch_tuned(reqs, tun, stream=stream)
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        P.profile_reset()
+        P.profile_enable(True)
+        P.ss_sort_batch_tuned(reqs, tun, stream=stream)
+        torch.cuda.synchronize(dev)
+        P.profile_enable(False)
+        prof = P.profile_read()
+        res = torch.cat([torch.cat([q["perm_out"], q["lcp_out"]]) for q in reqs]).clone()
+        if ref is None:
+            ref = res
+        out[name] = {"sort_ms": float(np.median(ts)),
+                     "classify_ms": prof.get("classify", (0, 0.0, 0))[1],
+                     "jump_tables_ms": prof.get("jump_tables", (0, 0.0, 0))[1],
+                     "classify_launches": prof.get("classify", (0, 0.0, 0))[0],
+                     "outputs_equal_unroll": bool(torch.equal(res, ref))}
     return out
 
 
@@ -235,7 +278,8 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
                   "service_p50_ms": float(np.percentile(service, 50)), "service_p99_ms": float(np.percentile(service, 99)),
                   "launches": "one ss_sort per request, in arrival order"},
         "speedup": tp / tb,
-        "autotuned": {"tunings_by_generator": {n_: {"child_target": t[0], "min_step": t[1]}
+        "autotuned": {"tunings_by_generator": {n_: {"child_target": t[0], "min_step": t[1],
+                                                    "classifier": ["unroll", "equal", "jump"][t[2]]}
                                                 for n_, t in zip(["random", "url_like", "dna_like"], tuned)},
                       "ms": float(np.median(tt)), "strings_per_s": total / (float(np.median(tt)) / 1e3),
                       "how": "ss_autotune on a 1 M sample of each generator's pool, then one ss_sort_batch_tuned call",
@@ -705,6 +749,8 @@ def main():
                        "equals_device_result": bool(same)}
 
     if rank == 0 and not args.no_extra:
+        line["classifiers"] = dict(what="the step's 4 runs sorted by one ss_sort_batch_tuned call per classifier",
+                                   **compare_classifiers(P, torch, dev, stream, reqs))
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_vs_plain(P, torch, dev, stream, nreq=args.batched_requests)

@@ -125,15 +125,38 @@ typedef struct {
 int ss_sort_batch(const ss_request *reqs_host, uint32_t count, ss_stream_t stream);
 
 /*
+ * Classifiers: how each key finds its bucket in the splitter tree (Section
+ * 4.4 weighs where the equality test goes; Section 8.1 proposes jump tables).
+ *   SS_CLASSIFIER_UNROLL  descents with > only, four interleaved per thread,
+ *                         then one equality test against the in-order
+ *                         splitters (S5-Unroll, the paper's choice; default)
+ *   SS_CLASSIFIER_EQUAL   one descent per key testing equality at every node
+ *                         and leaving the tree at the first equal splitter
+ *                         (S5-Equal)
+ *   SS_CLASSIFIER_JUMP    a table over the 10 key bits after the splitters'
+ *                         common prefix gives the node where the descent
+ *                         starts to depend on later bits; the descent goes on
+ *                         from there as SS_CLASSIFIER_UNROLL
+ * All three give the bucket 2r + [x_r = c], r = #{j : x_j < c}, except that
+ * S5-Equal puts a key equal to a repeated splitter value into the equality
+ * bucket of the copy highest in the tree; no sort result depends on it.
+ */
+#define SS_CLASSIFIER_UNROLL 0u
+#define SS_CLASSIFIER_EQUAL 1u
+#define SS_CLASSIFIER_JUMP 2u
+
+/*
  * Tuning of one request (0 fields: the library's defaults).  child_target:
  * the segment size the splitter tree aims its children at (a power of two in
  * [32, 65536]; the tree has about size / child_target leaves, at most 1024);
  * min_step: the smallest depth step an even bucket takes (in [1, 9]; 9: it
- * never steps and keeps its key).  Neither changes any result.
+ * never steps and keeps its key); classifier: one of SS_CLASSIFIER_*.  None
+ * changes any result.
  */
 typedef struct {
     uint32_t child_target;
     uint32_t min_step;
+    uint32_t classifier;
 } ss_tuning;
 
 /*
@@ -146,12 +169,13 @@ int ss_sort_batch_tuned(const ss_request *reqs_host, const ss_tuning *tunings_ho
 
 /*
  * ss_autotune -- picks a tuning for inputs like `req`'s: sorts its first
- * min(n, sample_n) strings (sample_n = 0: 2,000,000) with each of 16
- * candidate tunings (child_target 256..2048 x min_step 1, 3, 5, 9), once to
- * warm and once timed with CUDA events on `stream`, into scratch it
- * allocates (req's outputs are not touched), and writes the fastest to
- * *best_out and its time in ms to *best_ms_out (may be NULL).  Returns when
- * done.
+ * min(n, sample_n) strings (sample_n = 0: 2,000,000) with each of 18
+ * candidate tunings (child_target 256..2048 x min_step 1, 3, 5, 9 with the
+ * default classifier, then the best of those with SS_CLASSIFIER_EQUAL and
+ * SS_CLASSIFIER_JUMP), once to warm and once timed with CUDA events on
+ * `stream`, into scratch it allocates (req's outputs are not touched), and
+ * writes the fastest to *best_out and its time in ms to *best_ms_out (may be
+ * NULL).  Returns when done.
  */
 int ss_autotune(const ss_request *req_host, uint32_t sample_n, ss_tuning *best_out, double *best_ms_out,
                 ss_stream_t stream);
@@ -242,6 +266,17 @@ int ss_splitters(const uint64_t *sample_dev, uint32_t a, uint32_t d, uint64_t *x
 int ss_classify(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, uint32_t d,
                 uint16_t *bucket_out_dev, uint32_t *bucket_begin_out_dev, uint32_t *order_out_dev,
                 ss_stream_t stream);
+
+/*
+ * ss_classify_ex -- ss_classify with the classifier chosen (one of
+ * SS_CLASSIFIER_*; SS_ERR_INVALID otherwise).  With SS_CLASSIFIER_EQUAL and a
+ * repeated splitter value, keys equal to it go to the equality bucket of the
+ * copy highest in the tree (in-order index k with the most trailing one bits
+ * of k, i.e. trailing zero bits of k + 1), and order_out follows those buckets.
+ */
+int ss_classify_ex(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, uint32_t d,
+                   uint32_t classifier, uint16_t *bucket_out_dev, uint32_t *bucket_begin_out_dev,
+                   uint32_t *order_out_dev, ss_stream_t stream);
 
 /*
  * Sort server -- continuous batching of independent requests (the paper's

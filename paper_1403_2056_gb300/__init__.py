@@ -21,10 +21,14 @@ from . import build as _build
 __all__ = [
     "SortError", "lib", "library_path",
     "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge",
-    "ss_merge_noalloc", "ss_gather_keys", "ss_splitters", "ss_classify",
+    "ss_merge_noalloc", "ss_gather_keys", "ss_splitters", "ss_classify", "ss_classify_ex",
+    "CLASSIFIER_UNROLL", "CLASSIFIER_EQUAL", "CLASSIFIER_JUMP",
     "profile_enable", "profile_reset", "profile_read", "launch_count",
     "STATUS",
 ]
+
+# classifiers (SS_CLASSIFIER_* of the C header)
+CLASSIFIER_UNROLL, CLASSIFIER_EQUAL, CLASSIFIER_JUMP = 0, 1, 2
 
 STATUS = {0: "SS_OK", -1: "SS_ERR_INVALID", -2: "SS_ERR_OOM", -3: "SS_ERR_CUDA", -4: "SS_ERR_TIMEOUT",
           -5: "SS_ERR_TOO_LARGE", -6: "SS_ERR_UNIMPLEMENTED", -7: "SS_ERR_INTERNAL"}
@@ -64,6 +68,7 @@ def lib():
     L.ss_gather_keys.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp]
     L.ss_splitters.argtypes = [vp, u32, u32, vp, vp]
     L.ss_classify.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp]
+    L.ss_classify_ex.argtypes = [vp, u32, vp, u32, u32, vp, vp, vp, vp]
     L.ss_profile_enable.argtypes = [i32]
     L.ss_profile_read.argtypes = [vp, vp, vp, vp, i32]
     L.ss_launch_count.restype = u64
@@ -79,7 +84,7 @@ def lib():
     L.ss_scratch_bytes.argtypes = [u32]
     L.ss_scratch_bytes.restype = u64
     for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
-                 "ss_splitters", "ss_classify", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
+                 "ss_splitters", "ss_classify", "ss_classify_ex", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
                  "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
                  "ss_server_submit_host", "ss_sort_batch_tuned", "ss_autotune"):
         getattr(L, name).restype = i32
@@ -94,7 +99,7 @@ class HostRequest(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("child_target", C.c_uint32), ("min_step", C.c_uint32)]
+    _fields_ = [("child_target", C.c_uint32), ("min_step", C.c_uint32), ("classifier", C.c_uint32)]
 
 
 class Request(C.Structure):
@@ -199,7 +204,7 @@ def _request(q):
 
 
 def ss_sort_batch_tuned(requests, tunings=None, stream=None):
-    """As ss_sort_batch, with one (child_target, min_step) pair per request (0: default)."""
+    """As ss_sort_batch, with one (child_target, min_step[, classifier]) tuple per request (0: default)."""
     arr = (Request * max(1, len(requests)))()
     for k, q in enumerate(requests):
         arr[k] = _request(q)
@@ -207,17 +212,17 @@ def ss_sort_batch_tuned(requests, tunings=None, stream=None):
     if tunings is not None:
         tarr = (Tuning * max(1, len(requests)))()
         for k, t in enumerate(tunings):
-            tarr[k] = Tuning(int(t[0]), int(t[1]))
+            tarr[k] = Tuning(int(t[0]), int(t[1]), int(t[2]) if len(t) > 2 else 0)
     _check(lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
                                       len(requests), _stream(stream)))
 
 
 def ss_autotune(q, sample_n: int = 0, stream=None):
-    """((child_target, min_step), ms) fastest on the first sample_n strings of request q."""
+    """((child_target, min_step, classifier), ms) fastest on the first sample_n strings of request q."""
     t = Tuning()
     ms = C.c_double()
     _check(lib().ss_autotune(C.byref(_request(q)), int(sample_n), C.byref(t), C.byref(ms), _stream(stream)))
-    return (t.child_target, t.min_step), ms.value
+    return (t.child_target, t.min_step, t.classifier), ms.value
 
 
 def ss_scratch_bytes(n: int) -> int:
@@ -336,6 +341,13 @@ def ss_classify(keys, n, x, d, bucket_out, bucket_begin_out, order_out, stream=N
     _check(lib().ss_classify(_off(keys), int(n), _off(x), int(d), _dev(bucket_out, "int16", "bucket_out"),
                              _dev(bucket_begin_out, "int32", "bucket_begin_out"),
                              _dev(order_out, "int32", "order_out"), _stream(stream)))
+
+
+def ss_classify_ex(keys, n, x, d, classifier, bucket_out, bucket_begin_out, order_out, stream=None):
+    _check(lib().ss_classify_ex(_off(keys), int(n), _off(x), int(d), int(classifier),
+                                _dev(bucket_out, "int16", "bucket_out"),
+                                _dev(bucket_begin_out, "int32", "bucket_begin_out"),
+                                _dev(order_out, "int32", "order_out"), _stream(stream)))
 
 
 def profile_enable(on: bool = True):

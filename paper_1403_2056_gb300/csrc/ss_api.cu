@@ -327,7 +327,11 @@ static int pack_tuning(const ss_tuning &t, uint32_t &out, const char *who) {
         set_error_detail("%s: min_step must be in [0, 9], got %u", who, t.min_step);
         return SS_ERR_INVALID;
     }
-    out = s | (t.min_step << 8);
+    if (t.classifier > CLS_JUMP) {
+        set_error_detail("%s: classifier must be in [0, 2], got %u", who, t.classifier);
+        return SS_ERR_INVALID;
+    }
+    out = s | (t.min_step << 8) | (t.classifier << 16);
     return SS_OK;
 }
 
@@ -360,8 +364,7 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
     int rc = check_req(r, "ss_autotune");
     if (rc != SS_OK) return rc;
     const uint32_t n = std::min<uint32_t>(req->n, sample_n ? sample_n : 2000000u);
-    best_out->child_target = 0;
-    best_out->min_step = 0;
+    *best_out = ss_tuning{0, 0, 0};
     if (best_ms_out) *best_ms_out = 0;
     if (n < 2) return SS_OK;
     cudaStream_t st = as_stream(stream);
@@ -378,27 +381,33 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
     r.lcp_out = (uint32_t *)((char *)block + nb);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double best = -1;
+    // one candidate: a warm sort (pool, caches), then a timed one
+    auto try_one = [&](const ss_tuning &t) -> bool {
+        if ((rc = pack_tuning(t, r.tune, "ss_autotune")) != SS_OK) return false;
+        if ((rc = engine_sort(&r, 1, st)) != SS_OK) return false;
+        if ((e = cudaEventRecord(e0, st))) return false;
+        if ((rc = engine_sort(&r, 1, st)) != SS_OK) return false;
+        if ((e = cudaEventRecord(e1, st)) || (e = cudaEventSynchronize(e1))) return false;
+        float msec = 0;
+        if ((e = cudaEventElapsedTime(&msec, e0, e1))) return false;
+        if (best < 0 || msec < best) {
+            best = msec;
+            *best_out = t;
+        }
+        return true;
+    };
     const uint32_t targets[] = {256, 512, 1024, 2048};
     const uint32_t steps[] = {1, 3, 5, 9};
     do {
         if ((e = cudaEventCreate(&e0)) || (e = cudaEventCreate(&e1))) break;
-        for (uint32_t ct : targets) {
-            for (uint32_t ms : steps) {
-                ss_tuning t{ct, ms};
-                if ((rc = pack_tuning(t, r.tune, "ss_autotune")) != SS_OK) break;
-                if ((rc = engine_sort(&r, 1, st)) != SS_OK) break;   // warm: pool, caches
-                if ((e = cudaEventRecord(e0, st))) break;
-                if ((rc = engine_sort(&r, 1, st)) != SS_OK) break;
-                if ((e = cudaEventRecord(e1, st)) || (e = cudaEventSynchronize(e1))) break;
-                float msec = 0;
-                if ((e = cudaEventElapsedTime(&msec, e0, e1))) break;
-                if (best < 0 || msec < best) {
-                    best = msec;
-                    *best_out = t;
-                }
-            }
-            if (rc != SS_OK || e) break;
-        }
+        bool ok = true;
+        for (uint32_t ct : targets)
+            for (uint32_t ms : steps)
+                if (ok) ok = try_one(ss_tuning{ct, ms, CLS_UNROLL});
+        // the other classifiers with the best tree shape
+        const ss_tuning shape = *best_out;
+        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_EQUAL});
+        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_JUMP});
     } while (0);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
@@ -473,7 +482,22 @@ int ss_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d,
         return SS_ERR_INVALID;
     }
     if (n == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
-    return engine_classify(keys, n, x, d, bucket_out, bucket_begin_out, order_out, as_stream(stream));
+    return engine_classify(keys, n, x, d, CLS_UNROLL, bucket_out, bucket_begin_out, order_out, as_stream(stream));
+}
+
+int ss_classify_ex(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint32_t classifier,
+                   uint16_t *bucket_out, uint32_t *bucket_begin_out, uint32_t *order_out, ss_stream_t stream) {
+    t_detail.clear();
+    if (classifier > CLS_JUMP) {
+        set_error_detail("ss_classify_ex: classifier must be in [0, 2], got %u", classifier);
+        return SS_ERR_INVALID;
+    }
+    if (d < 1 || d > (uint32_t)kMaxD || !x || !bucket_begin_out || (n && (!keys || !bucket_out || !order_out))) {
+        set_error_detail("ss_classify_ex: need 1 <= d <= %d and non-NULL pointers", kMaxD);
+        return SS_ERR_INVALID;
+    }
+    if (n == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
+    return engine_classify(keys, n, x, d, classifier, bucket_out, bucket_begin_out, order_out, as_stream(stream));
 }
 
 int ss_profile_enable(int on) {

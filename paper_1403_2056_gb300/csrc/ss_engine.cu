@@ -373,6 +373,7 @@ struct ClassifySmem {
     uint64_t t[kMaxV + 1];   // level order, one-based (t[0] unused)
     uint64_t x[kMaxV + 1];   // in order, x[v] unused
     uint32_t cnt[kMaxB + 1];
+    uint16_t j[1 << kJumpBits];   // jump table (CLS_JUMP segments only)
 };
 
 // load the in-order splitters and build the level-order tree (Figure 1):
@@ -388,17 +389,69 @@ __device__ __forceinline__ void load_tree(const uint64_t *xs, uint32_t d, uint64
     }
 }
 
-// bucket of key c: descend with i := 2i + [c > t_i], then one equality test
-__device__ __forceinline__ uint32_t classify_one(uint64_t c, const uint64_t *t, const uint64_t *x, uint32_t d, uint32_t v) {
-    uint32_t i = 1;
-    for (uint32_t l = 0; l < d; l++) i = 2 * i + (c > t[i] ? 1u : 0u);
-    uint32_t r = i - (v + 1);
-    return 2 * r + ((r < v && x[r] == c) ? 1u : 0u);
+// Jump tables.  All keys between the smallest and the largest splitter share
+// the splitters' common prefix of s bits (s = clz(x_0 xor x_{v-1}), at most
+// 64 - kJumpBits); a key whose top s bits are below that prefix lies below
+// x_0 (leaf 2^d, bucket 0), above it lies above x_{v-1} (leaf 2^(d+1) - 1,
+// bucket 2v).  Entry p covers the keys with the prefix followed by the
+// kJumpBits bits p, an interval [lo, hi]; its descent is fixed while the node's
+// splitter t is below lo (every key goes right) or at least hi (every key goes
+// left), and the entry holds the first node where it is not, or the leaf.
+__device__ __forceinline__ uint32_t jump_shift(uint64_t x0, uint64_t xl) {
+    uint32_t s = x0 == xl ? 64u : (uint32_t)__clzll((long long)(x0 ^ xl));
+    return min(s, 64u - (uint32_t)kJumpBits);
+}
+__device__ __forceinline__ uint64_t prefix_mask(uint32_t s) { return s ? ~0ull << (64 - s) : 0ull; }
+
+// one table per segment whose request classifies with CLS_JUMP (all segments
+// when reqs is NULL); one CTA per segment
+__global__ void __launch_bounds__(kThreads) k_jump_tables(const BigSeg *__restrict__ segs, const ReqDesc *__restrict__ reqs,
+                                                          const uint64_t *__restrict__ splitters, uint16_t *__restrict__ jt) {
+    __shared__ uint64_t t[kMaxV + 1];
+    const BigSeg sg = segs[blockIdx.x];
+    if (reqs && req_classifier(reqs[sg.req]) != CLS_JUMP) return;
+    const uint32_t d = sg.d, v = (1u << d) - 1;
+    const uint64_t *x = splitters + (size_t)blockIdx.x * kMaxV;
+    for (uint32_t i = threadIdx.x + 1; i <= v; i += blockDim.x) {
+        uint32_t l = 31 - __clz(i);
+        t[i] = x[((2 * (i - (1u << l)) + 1) << (d - l - 1)) - 1];
+    }
+    __syncthreads();
+    const uint32_t s = jump_shift(x[0], x[v - 1]);
+    const uint64_t pre = x[0] & prefix_mask(s);
+    const uint32_t low = 64 - s - kJumpBits;   // key bits below an entry's range
+    uint16_t *J = jt + (size_t)blockIdx.x * kJumpStride;
+    for (uint32_t p = threadIdx.x; p < (1u << kJumpBits); p += blockDim.x) {
+        const uint64_t lo = pre | ((uint64_t)p << low);
+        const uint64_t hi = lo | ((1ull << low) - 1);
+        uint32_t i = 1;
+        while (i <= v) {
+            const uint64_t ti = t[i];
+            if (ti < lo) i = 2 * i + 1;
+            else if (ti >= hi) i = 2 * i;
+            else break;
+        }
+        J[p] = (uint16_t)i;
+    }
+    if (threadIdx.x == 0) J[1 << kJumpBits] = (uint16_t)s;
 }
 
+// bucket b of element p into the bucket buffer and the tile histogram (lanes
+// with equal buckets add once)
+__device__ __forceinline__ void emit_bucket(uint32_t *cnt, uint16_t *obuf, uint32_t p, bool ok, uint32_t b, uint32_t lane) {
+    if (ok) obuf[p] = (uint16_t)b;
+    uint32_t key_b = ok ? b : 0xFFFFu;
+    uint32_t peers = __match_any_sync(0xffffffffu, key_b);
+    if (ok && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt[b], (uint32_t)__popc(peers));
+}
+
+// The classifier is the segment's request's (or `cls` for all segments when
+// reqs is NULL); jt holds the jump tables of CLS_JUMP segments.
 __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict__ segs, uint32_t nseg,
+                                                       const ReqDesc *__restrict__ reqs, uint32_t cls_all,
                                                        const uint64_t *__restrict__ key,
                                                        const uint64_t *__restrict__ splitters,
+                                                       const uint16_t *__restrict__ jt,
                                                        uint16_t *__restrict__ obuf, uint32_t *__restrict__ counts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     ClassifySmem &S = *reinterpret_cast<ClassifySmem *>(smem_raw);
@@ -407,6 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict_
     const BigSeg sg = segs[si];
     const uint32_t tl = tile - sg.tile_base;
     const uint32_t d = sg.d, v = (1u << d) - 1, B = 2 * v + 1;
+    const uint32_t cls = reqs ? req_classifier(reqs[sg.req]) : cls_all;
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t seg_end = sg.begin + sg.size;
     const uint32_t wbeg = sg.begin + tl * kTile + warp * kWarpSpan;
@@ -419,31 +473,76 @@ __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict_
     }
     load_tree(splitters + (size_t)si * kMaxV, d, S.t, S.x);
     for (uint32_t b = threadIdx.x; b < B; b += blockDim.x) S.cnt[b] = 0;
+    uint32_t jshift = 0;
+    if (cls == CLS_JUMP) {
+        const uint16_t *J = jt + (size_t)si * kJumpStride;   // 16-byte aligned rows
+        const uint4 *src = reinterpret_cast<const uint4 *>(J);
+        uint4 *dst = reinterpret_cast<uint4 *>(S.j);
+        for (uint32_t k = threadIdx.x; k < (1u << kJumpBits) / 8; k += blockDim.x) dst[k] = src[k];
+        jshift = J[1 << kJumpBits];
+    }
     __syncthreads();
 
-    // four interleaved descents per thread (Section 4.3: unrolled, interleaved loops)
+    if (cls == CLS_EQUAL) {
+        // one descent per key; the first splitter equal to the key ends it
 #pragma unroll
-    for (int it = 0; it < kItems; it += 4) {
-        uint32_t p[4], node[4];
-        bool ok[4];
-#pragma unroll
-        for (int u = 0; u < 4; u++) {
-            p[u] = wbeg + (it + u) * 32 + lane;
-            ok[u] = p[u] < seg_end;
-            node[u] = 1;
+        for (int u = 0; u < kItems; u++) {
+            const uint32_t p = wbeg + u * 32 + lane;
+            uint32_t i = 1, b = 0xFFFFFFFFu;
+            for (uint32_t l = 0; l < d; l++) {
+                const uint64_t tv = S.t[i];
+                if (c[u] == tv) {   // node i of level l is in-order splitter k
+                    b = 2 * ((((2 * (i - (1u << l)) + 1) << (d - l - 1)) - 1)) + 1;
+                    break;
+                }
+                i = 2 * i + (c[u] > tv ? 1u : 0u);
+            }
+            if (b == 0xFFFFFFFFu) b = 2 * (i - (v + 1));
+            emit_bucket(S.cnt, obuf, p, p < seg_end, b, lane);
         }
-        for (uint32_t l = 0; l < d; l++) {
+    } else {
+        const uint64_t pm = prefix_mask(jshift);
+        const uint64_t pre = S.x[0] & pm;
+        // four interleaved descents per thread (Section 4.3: unrolled, interleaved loops)
 #pragma unroll
-            for (int u = 0; u < 4; u++) node[u] = 2 * node[u] + (c[it + u] > S.t[node[u]] ? 1u : 0u);
-        }
+        for (int it = 0; it < kItems; it += 4) {
+            uint32_t p[4], node[4];
+            bool ok[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) {
-            uint32_t r = node[u] - (v + 1);
-            uint32_t b = 2 * r + ((r < v && S.x[r] == c[it + u]) ? 1u : 0u);
-            if (ok[u]) obuf[p[u]] = (uint16_t)b;
-            uint32_t key_b = ok[u] ? b : 0xFFFFu;
-            uint32_t peers = __match_any_sync(0xffffffffu, key_b);
-            if (ok[u] && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&S.cnt[b], (uint32_t)__popc(peers));
+            for (int u = 0; u < 4; u++) {
+                p[u] = wbeg + (it + u) * 32 + lane;
+                ok[u] = p[u] < seg_end;
+                node[u] = 1;
+            }
+            if (cls == CLS_JUMP) {
+                uint32_t lmin = kMaxD;
+#pragma unroll
+                for (int u = 0; u < 4; u++) {
+                    const uint64_t cu = c[it + u], cp = cu & pm;
+                    node[u] = cp < pre ? v + 1 : cp > pre ? 2 * v + 1 : (uint32_t)S.j[(cu << jshift) >> (64 - kJumpBits)];
+                    lmin = min(lmin, 31u - __clz(node[u]));
+                }
+                // finish the descents: nodes already at a leaf stay there
+                for (uint32_t l = lmin; l < d; l++) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) {
+                        const bool in = node[u] <= v;
+                        const uint64_t tv = S.t[in ? node[u] : 1u];
+                        node[u] = in ? 2 * node[u] + (c[it + u] > tv ? 1u : 0u) : node[u];
+                    }
+                }
+            } else {
+                for (uint32_t l = 0; l < d; l++) {
+#pragma unroll
+                    for (int u = 0; u < 4; u++) node[u] = 2 * node[u] + (c[it + u] > S.t[node[u]] ? 1u : 0u);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                uint32_t r = node[u] - (v + 1);
+                uint32_t b = 2 * r + ((r < v && S.x[r] == c[it + u]) ? 1u : 0u);
+                emit_bucket(S.cnt, obuf, p[u], ok[u], b, lane);
+            }
         }
     }
     __syncthreads();
@@ -1002,6 +1101,7 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     c.take<uint32_t>(caps.counts);
     c.take<uint32_t>(np);
     c.take<uint64_t>((size_t)caps.big * kMaxV);
+    c.take<uint16_t>((size_t)caps.big * kJumpStride);
     c.take<BigSeg>(caps.big); c.take<BigSeg>(caps.big);
     for (int k = 0; k < kClasses; k++) c.take<SmallTask>(caps.small[k]);
     c.take<Boundary>(caps.bound);
@@ -1066,6 +1166,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     uint32_t *counts = c.take<uint32_t>(caps.counts);
     uint32_t *partial = c.take<uint32_t>(np);
     uint64_t *splitters = c.take<uint64_t>((size_t)caps.big * kMaxV);
+    uint16_t *jt = c.take<uint16_t>((size_t)caps.big * kJumpStride);
     BigSeg *big[2] = {c.take<BigSeg>(caps.big), c.take<BigSeg>(caps.big)};
     TaskLists tl;
     for (int k = 0; k < kClasses; k++) {
@@ -1080,7 +1181,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
 
     int rc = SS_OK;
     bool any_status = false;   // some request wants its status written on the device
-    for (const ReqDesc &q : reqs) any_status = any_status || q.status_out;
+    bool any_jump = false;     // some request classifies with jump tables
+    for (const ReqDesc &q : reqs) {
+        any_status = any_status || q.status_out;
+        any_jump = any_jump || req_classifier(q) == CLS_JUMP;
+    }
     // initial segments: one per request
     std::vector<BigSeg> big0;
     std::vector<SmallTask> s_task[kClasses];
@@ -1168,7 +1273,10 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             // trees first: each chooses its depth; then the counter layout follows
             SS_LAUNCH_U("build_trees", st, nbig, k_build_trees<<<nbig, kThreads, sizeof(TreeSmem), st>>>(big[cur], dreqs, key[cur], splitters));
             SS_LAUNCH_U("setup_big", st, nbig, k_setup_big<<<1, 1024, 0, st>>>(big[cur], nbig, counters + C_LVL_COUNTS));
-            SS_LAUNCH_U("classify", st, nelems, k_classify<<<ntiles, kThreads, sizeof(ClassifySmem), st>>>(big[cur], nbig, key[cur], splitters, obuf, counts));
+            if (any_jump)
+                SS_LAUNCH_U("jump_tables", st, nbig, k_jump_tables<<<nbig, kThreads, 0, st>>>(big[cur], dreqs, splitters, jt));
+            SS_LAUNCH_U("classify", st, nelems, k_classify<<<ntiles, kThreads, sizeof(ClassifySmem), st>>>(
+                big[cur], nbig, dreqs, 0u, key[cur], splitters, jt, obuf, counts));
             TRY(cudaGetLastError(), "classify launch");
             if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) goto done;
             SS_LAUNCH_U("scatter", st, nelems, k_scatter<MODE_SORT><<<ntiles, kThreads, sizeof(ScatterSmem), st>>>(
@@ -1274,8 +1382,8 @@ done:
 
 // ------------------------------------------------ single-step entry points
 
-int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
-                    uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t st) {
+int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint32_t classifier,
+                    uint16_t *bucket_out, uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t st) {
     if (ensure_attrs() != cudaSuccess) return cuda_fail(cudaGetLastError(), "kernel attributes");
     uint32_t v = (1u << d) - 1, B = 2 * v + 1;
     uint32_t tiles = tiles_of(n);
@@ -1283,7 +1391,8 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
     uint32_t np = ncounts / kScanChunk + 2;
     size_t bytes = 0;
     Carve c0{nullptr, 0};
-    c0.take<uint32_t>(ncounts); c0.take<uint32_t>(np); c0.take<uint64_t>(kMaxV); c0.take<BigSeg>(1); c0.take<uint32_t>(C_NUM);
+    c0.take<uint32_t>(ncounts); c0.take<uint32_t>(np); c0.take<uint64_t>(kMaxV); c0.take<uint16_t>(kJumpStride);
+    c0.take<BigSeg>(1); c0.take<uint32_t>(C_NUM);
     bytes = c0.off + 256;
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
@@ -1292,6 +1401,7 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
     uint32_t *counts = c.take<uint32_t>(ncounts);
     uint32_t *partial = c.take<uint32_t>(np);
     uint64_t *spl = c.take<uint64_t>(kMaxV);
+    uint16_t *jt = c.take<uint16_t>(kJumpStride);
     BigSeg *seg = c.take<BigSeg>(1);
     uint32_t *counters = c.take<uint32_t>(C_NUM);
     BigSeg s{};
@@ -1306,7 +1416,10 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
         if ((e = cudaMemcpyAsync(spl, x, sizeof(uint64_t) * v, cudaMemcpyDeviceToDevice, st))) break;
         if ((e = cudaMemcpyAsync(counters, hcnt, sizeof(hcnt), cudaMemcpyHostToDevice, st))) break;
         if (n) {
-            SS_LAUNCH("classify", st, k_classify<<<tiles, kThreads, sizeof(ClassifySmem), st>>>(seg, 1, keys, spl, bucket_out, counts));
+            if (classifier == CLS_JUMP)
+                SS_LAUNCH("jump_tables", st, k_jump_tables<<<1, kThreads, 0, st>>>(seg, nullptr, spl, jt));
+            SS_LAUNCH("classify", st, k_classify<<<tiles, kThreads, sizeof(ClassifySmem), st>>>(
+                seg, 1, nullptr, classifier, keys, spl, jt, bucket_out, counts));
             if ((e = cudaGetLastError())) break;
             if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) break;
             SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY><<<tiles, kThreads, sizeof(ScatterSmem), st>>>(

@@ -62,7 +62,8 @@ struct ReqDesc {
     uint32_t fixed_len;
     uint32_t n;
     uint32_t base;             // global position of the request's first element
-    uint32_t tune;             // log2 child target (bits 0..7) | minimum depth step (bits 8..15); 0: defaults
+    uint32_t tune;             // log2 child target (bits 0..7) | minimum depth step (bits 8..15) |
+                               // classifier (bits 16..17); 0: defaults
     uint32_t *perm_out;
     uint32_t *lcp_out;
     int32_t *status_out;
@@ -78,6 +79,26 @@ __host__ __device__ __forceinline__ uint32_t req_min_step(const ReqDesc &r) {
     const uint32_t m = (r.tune >> 8) & 0xFFu;
     return m ? m : (uint32_t)SS_MIN_STEP;
 }
+
+// How k_classify finds a key's bucket (every classifier gives the bucket of
+// the closed form 2r + [x_r = c], r = #{j : x_j < c}, except that S5-Equal
+// puts a key equal to a repeated splitter value into the equality bucket of
+// the copy highest in the tree; the sorted result is the same):
+//   CLS_UNROLL  descents with > only, four interleaved per thread, then one
+//               equality test (S5-Unroll, Section 4.4's first alternative)
+//   CLS_EQUAL   one descent per key with an equality test at every node,
+//               leaving the tree at the first equal splitter (S5-Equal,
+//               Section 4.4's fourth alternative)
+//   CLS_JUMP    a table over the key bits that follow the splitters' shared
+//               prefix gives the node where the descent starts to depend on
+//               later bits (jump tables, Section 8.1), then as CLS_UNROLL
+enum Classifier : uint32_t { CLS_UNROLL = 0, CLS_EQUAL = 1, CLS_JUMP = 2 };
+__host__ __device__ __forceinline__ uint32_t req_classifier(const ReqDesc &r) { return (r.tune >> 16) & 0x3u; }
+#ifndef SS_JUMP_BITS
+#define SS_JUMP_BITS 10
+#endif
+constexpr int kJumpBits = SS_JUMP_BITS;            // 2^kJumpBits entries per jump table
+constexpr int kJumpStride = (1 << kJumpBits) + 8;  // u16 per segment: the table, then the prefix length
 
 struct BigSeg {                 // a segment sorted by one multi-CTA S5 step
     uint32_t begin, size, depth, req;
@@ -308,8 +329,8 @@ int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream);
 size_t engine_scratch_bytes(size_t N, uint32_t nreq);
 int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host, const uint32_t *lengths_host,
               uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host, uint32_t *lcp_host, cudaStream_t st);
-int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint16_t *bucket_out,
-                    uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t stream);
+int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint32_t classifier,
+                    uint16_t *bucket_out, uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t st);
 int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t stream);
 int engine_gather(const ReqDesc &r, const uint32_t *depth, uint64_t *keys_out, cudaStream_t stream);
 

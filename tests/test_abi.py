@@ -68,8 +68,16 @@ def test_tuning_ranges_checked_on_the_host():
     import paper_1403_2056_gb300 as P
     q = P.Request(1, 1, None, 0, 5, 1, 1, None)   # pointers are never dereferenced: the check fails first
     arr = (P.Request * 1)(q)
-    for bad in [(48, 0), (16, 0), (1 << 17, 0), (0, 10)]:
+    for bad in [(48, 0, 0), (16, 0, 0), (1 << 17, 0, 0), (0, 10, 0), (0, 0, 3)]:
         t = (P.Tuning * 1)(P.Tuning(*bad))
         rc = P.lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), C.cast(t, C.c_void_p), 1, None)
         assert rc == -1, bad
         assert b"ss_sort_batch_tuned" in P._detail().encode()
+
+
+def test_classifier_range_checked_on_the_host():
+    """ss_classify_ex refuses an unknown classifier before any device work."""
+    import paper_1403_2056_gb300 as P
+    rc = P.lib().ss_classify_ex(None, 0, None, 3, 3, None, None, None, None)
+    assert rc == -1
+    assert "classifier" in P._detail()

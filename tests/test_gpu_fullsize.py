@@ -40,6 +40,15 @@ def test_url_like_10m_sort_and_runs_merge():
     torch.cuda.synchronize()
     assert np.array_equal(mp.cpu().numpy().view(np.uint32), perm)
     assert np.array_equal(ml.cpu().numpy().view(np.uint32), lcp)
+    # the other classifiers give the same arrays at full size
+    for cls in (1, 2):
+        cp = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+        cl = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+        P.ss_sort_batch_tuned([dict(chars=chars, offsets=offsets, lengths=None, fixed_len=0, n=n, perm_out=cp,
+                                    lcp_out=cl)], [(0, 0, cls)])
+        torch.cuda.synchronize()
+        assert np.array_equal(cp.cpu().numpy().view(np.uint32), perm), cls
+        assert np.array_equal(cl.cpu().numpy().view(np.uint32), lcp), cls
 
 
 def test_dna_windows_20m():

@@ -199,6 +199,87 @@ def test_classify_step_matches_oracle(d, n):
     assert np.array_equal(order[:n].cpu().numpy().view(np.uint32).astype(np.uint64), want_order)
 
 
+def _classifier_cases():
+    """(name, d, splitters, keys): small integers with repeated splitters,
+    distinct full-range 64-bit values, text-like keys whose splitters share a
+    long prefix (keys below, inside and above it), all splitters equal, and
+    splitters at 0 and 2^64 - 1; every case holds keys equal to splitters and
+    their neighbours.  n spans three tiles of 4096 and a ragged tail."""
+    rng = np.random.default_rng(91)
+    n = 3 * 4096 + 123
+    cases = []
+    for d in (1, 2, 3, 5, 7, 10):
+        v = (1 << d) - 1
+        x = np.sort(rng.integers(0, 4 * v + 8, v)).astype(np.uint64)
+        k = rng.integers(0, 4 * v + 10, n).astype(np.uint64)
+        cases.append((f"small_d{d}", d, x, k))
+        x = np.unique(rng.integers(1, 2**64 - 1, v + 64, dtype=np.uint64))[:v]
+        k = rng.integers(0, 2**64, n, dtype=np.uint64)
+        cases.append((f"full_d{d}", d, x, k))
+        pre = np.uint64(int.from_bytes(b"http://w", "big") & ~0xFFFFFF)   # 40 shared bits
+        x = np.sort(pre | rng.integers(0, 1 << 24, v).astype(np.uint64))
+        k = pre | rng.integers(0, 1 << 24, n).astype(np.uint64)
+        k[: n // 8] = rng.integers(0, 2**64, n // 8, dtype=np.uint64)   # mostly outside the prefix
+        cases.append((f"prefix_d{d}", d, x, k))
+    x = np.full(7, 12345, np.uint64)
+    cases.append(("all_equal_d3", 3, x, rng.integers(12340, 12350, n).astype(np.uint64)))
+    x = np.array([0] + sorted(rng.integers(1, 2**64 - 1, 5, dtype=np.uint64).tolist()) + [2**64 - 1], np.uint64)
+    cases.append(("extremes_d3", 3, x, np.concatenate([rng.integers(0, 2**64, n - 4, dtype=np.uint64),
+                                                         np.array([0, 1, 2**64 - 2, 2**64 - 1], np.uint64)])))
+    out = []
+    for name, d, x, k in cases:
+        k = k.copy()
+        m = min(len(x), n // 4)
+        k[-3 * m:] = np.concatenate([x[:m], x[:m] - np.uint64(1), x[:m] + np.uint64(1)])   # wraps at the extremes
+        out.append((name, d, x, k))
+    return out
+
+
+@pytest.mark.parametrize("cls", [0, 1, 2])
+def test_classifiers_match_oracle(cls):
+    """ss_classify_ex with each classifier against the oracle: S5-Unroll and
+    the jump table give the closed-form bucket (orc_s5_classify), S5-Equal the
+    oracle's S5-Equal buckets; bucket starts and the stable order follow."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    for name, d, x, keys in _classifier_cases():
+        n, v = keys.shape[0], (1 << d) - 1
+        tk = torch.from_numpy(keys.view(np.int64)).cuda()
+        tx = torch.from_numpy(x.view(np.int64)).cuda()
+        b = torch.zeros(n, dtype=torch.int16, device="cuda:0")
+        bb = torch.zeros(2 * v + 2, dtype=torch.int32, device="cuda:0")
+        order = torch.zeros(n, dtype=torch.int32, device="cuda:0")
+        P.ss_classify_ex(tk, n, tx, d, cls, b, bb, order)
+        want_b = oracle.s5_classify_equal(keys, x) if cls == 1 else oracle.s5_classify(keys, x)
+        want_bb, want_order = oracle.s5_distribute(want_b, v)
+        assert np.array_equal(b.cpu().numpy().view(np.uint16), want_b), (name, cls)
+        assert np.array_equal(bb.cpu().numpy().view(np.uint32).astype(np.uint64), want_bb), (name, cls)
+        assert np.array_equal(order.cpu().numpy().view(np.uint32).astype(np.uint64), want_order), (name, cls)
+
+
+def test_mixed_classifiers_in_one_batch():
+    """Requests with different classifiers in one batch (jump tables built for
+    the jump requests' segments only): each result is the oracle's."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    sets = [W.url_like(80_000, seed=51), W.sinha_dna_like(70_000, seed=52), W.random_lower(90_000, seed=53),
+            W.dna_windows(60_000, 1_200_100, 100, seed=54), W.paper_random(50_000, seed=55), W.url_like(9_000, seed=56)]
+    reqs, outs = [], []
+    for ss in sets:
+        chars, offsets, lengths = to_device(ss)
+        perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+        reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=ss.n,
+                         perm_out=perm, lcp_out=lcp))
+        outs.append((perm, lcp))
+    P.ss_sort_batch_tuned(reqs, [(0, 0, k % 3) for k in range(len(reqs))])
+    torch.cuda.synchronize()
+    for k, (ss, (perm, lcp)) in enumerate(zip(sets, outs)):
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm), (ss.name, k % 3)
+        assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp), (ss.name, k % 3)
+
+
 @pytest.mark.parametrize("K", [1, 2, 3, 4, 7, 16])
 def test_merge_runs(K):
     import torch
@@ -311,12 +392,14 @@ def test_batch_with_different_shared_prefixes():
 
 
 # ------------------------------------------------------------- tuning
-@pytest.mark.parametrize("tuning", [(256, 1), (2048, 9), (32, 3), (65536, 5), (0, 0)])
+@pytest.mark.parametrize("tuning", [(256, 1), (2048, 9), (32, 3), (65536, 5), (0, 0), (0, 0, 1), (0, 0, 2),
+                                    (32, 1, 2), (2048, 9, 1)])
 def test_tunings_do_not_change_results(tuning):
     """Any tuning gives the same order and LCPs (the oracle's)."""
     import torch
     import paper_1403_2056_gb300 as P
-    sets = [W.url_like(60_000, seed=41), W.dna_windows(60_000, 1_200_100, 100, seed=42), W.random_lower(60_000, seed=43)]
+    sets = [W.url_like(60_000, seed=41), W.dna_windows(60_000, 1_200_100, 100, seed=42), W.random_lower(60_000, seed=43),
+            W.sinha_dna_like(60_000, seed=44)]
     reqs, outs = [], []
     for ss in sets:
         chars, offsets, lengths = to_device(ss)
@@ -340,9 +423,9 @@ def test_autotune_picks_a_candidate_and_leaves_outputs():
     chars, offsets, _ = to_device(ss)
     perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
     lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
-    (ct, ms_step), ms = P.ss_autotune(dict(chars=chars, offsets=offsets, lengths=None, fixed_len=0, n=ss.n,
+    (ct, ms_step, cls), ms = P.ss_autotune(dict(chars=chars, offsets=offsets, lengths=None, fixed_len=0, n=ss.n,
                                            perm_out=perm, lcp_out=lcp), sample_n=200_000)
-    assert ct in (256, 512, 1024, 2048) and ms_step in (1, 3, 5, 9) and ms > 0
+    assert ct in (256, 512, 1024, 2048) and ms_step in (1, 3, 5, 9) and cls in (0, 1, 2) and ms > 0
     torch.cuda.synchronize()
     assert int((perm != -1).sum().item()) == 0 and int((lcp != -1).sum().item()) == 0
 
