@@ -436,13 +436,33 @@ __global__ void __launch_bounds__(kThreads) k_jump_tables(const BigSeg *__restri
     if (threadIdx.x == 0) J[1 << kJumpBits] = (uint16_t)s;
 }
 
-// bucket b of element p into the bucket buffer and the tile histogram (lanes
-// with equal buckets add once)
+// Tile histogram update: 0 = lanes with equal buckets add once (warp match);
+// 1 = one shared atomic per element; 2 = runs of equal buckets in consecutive
+// lanes add once.
+#ifndef SS_CLASSIFY_COUNT
+#define SS_CLASSIFY_COUNT 0
+#endif
+
+// bucket b of element p into the bucket buffer and the tile histogram
 __device__ __forceinline__ void emit_bucket(uint32_t *cnt, uint16_t *obuf, uint32_t p, bool ok, uint32_t b, uint32_t lane) {
     if (ok) obuf[p] = (uint16_t)b;
+#if SS_CLASSIFY_COUNT == 1
+    if (ok) atomicAdd(&cnt[b], 1u);
+#elif SS_CLASSIFY_COUNT == 2
+    const uint32_t key_b = ok ? b : 0xFFFFu;
+    const uint32_t prev = __shfl_up_sync(0xffffffffu, key_b, 1);
+    const bool head = lane == 0 || prev != key_b;
+    const uint32_t heads = __ballot_sync(0xffffffffu, head);
+    if (ok && head) {
+        const uint32_t later = heads & ~(0xFFFFFFFFu >> (31 - lane));   // heads above this lane
+        const uint32_t end = later ? (uint32_t)(__ffs(later) - 1) : 32u;
+        atomicAdd(&cnt[b], end - lane);
+    }
+#else
     uint32_t key_b = ok ? b : 0xFFFFu;
     uint32_t peers = __match_any_sync(0xffffffffu, key_b);
     if (ok && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&cnt[b], (uint32_t)__popc(peers));
+#endif
 }
 
 // The classifier is the segment's request's (or `cls` for all segments when
@@ -693,6 +713,12 @@ constexpr int kScatterBatch = SS_SCATTER_BATCH;   // elements whose reads are in
 // inside a warp, warps in order inside the tile); then each payload array in
 // turn is reordered through shared memory into tile-local bucket order, so that
 // consecutive threads write the consecutive positions of a bucket's run.
+// phase A's per-warp counts: 0 = warp match, lanes with equal buckets add once;
+// 1 = one shared atomic per element
+#ifndef SS_SCATTER_COUNT
+#define SS_SCATTER_COUNT 0
+#endif
+
 template <int MODE>
 __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const BigSeg *__restrict__ segs, uint32_t nseg,
                                                       const ReqDesc *__restrict__ reqs,
@@ -729,12 +755,21 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         reinterpret_cast<uint32_t *>(&S.u.wpos[0][0])[k] = 0;
     __syncthreads();
     // phase A: per-warp bucket counts of its contiguous span
+#if SS_SCATTER_COUNT == 1
+    // one shared atomic per element on the 32-bit word holding the 16-bit count
+    // (a warp's span has 512 elements, so a count never carries into its neighbour)
+#pragma unroll
+    for (int u = 0; u < kItems; u++)
+        if (bk[u] != 0xFFFFu)
+            atomicAdd(reinterpret_cast<uint32_t *>(&S.u.wpos[warp][bk[u] & ~1u]), 1u << (16 * (bk[u] & 1u)));
+#else
 #pragma unroll
     for (int u = 0; u < kItems; u++) {
         uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
         if (bk[u] != 0xFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) S.u.wpos[warp][bk[u]] += (uint16_t)__popc(peers);
         __syncwarp();
     }
+#endif
     __syncthreads();
     // phase B: each warp's offset inside the tile's part of every bucket, the
     // tile's count of every bucket (in lbase for now) and the bucket facts.  The
