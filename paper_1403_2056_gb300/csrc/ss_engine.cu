@@ -436,11 +436,25 @@ __global__ void __launch_bounds__(kThreads) k_jump_tables(const BigSeg *__restri
     if (threadIdx.x == 0) J[1 << kJumpBits] = (uint16_t)s;
 }
 
-// Tile histogram update: 0 = lanes with equal buckets add once (warp match);
-// 1 = one shared atomic per element; 2 = runs of equal buckets in consecutive
-// lanes add once.
+// Lanes of the warp whose value b agrees with this lane's in the low nbits
+// bits: one vote per bit (nbits must be the same in the whole warp).  A bucket
+// id of a tree of depth d has d + 1 bits and is at most 2^(d+1) - 2, so the
+// marker 0xFFFF of an empty slot never agrees with a bucket.
+__device__ __forceinline__ uint32_t peers_of(uint32_t b, uint32_t nbits) {
+    uint32_t m = 0xFFFFFFFFu;
+    for (uint32_t k = 0; k < nbits; k++) {
+        const uint32_t bit = (b >> k) & 1u;
+        const uint32_t vote = __ballot_sync(0xFFFFFFFFu, bit);
+        m &= bit ? vote : ~vote;
+    }
+    return m;
+}
+
+// Tile histogram update: 1 = one shared atomic per element; 0 = lanes with
+// equal buckets add once (warp match), slower on GB300 for every workload
+// measured (the match costs more than the atomics it saves).
 #ifndef SS_CLASSIFY_COUNT
-#define SS_CLASSIFY_COUNT 0
+#define SS_CLASSIFY_COUNT 1
 #endif
 
 // bucket b of element p into the bucket buffer and the tile histogram
@@ -448,16 +462,6 @@ __device__ __forceinline__ void emit_bucket(uint32_t *cnt, uint16_t *obuf, uint3
     if (ok) obuf[p] = (uint16_t)b;
 #if SS_CLASSIFY_COUNT == 1
     if (ok) atomicAdd(&cnt[b], 1u);
-#elif SS_CLASSIFY_COUNT == 2
-    const uint32_t key_b = ok ? b : 0xFFFFu;
-    const uint32_t prev = __shfl_up_sync(0xffffffffu, key_b, 1);
-    const bool head = lane == 0 || prev != key_b;
-    const uint32_t heads = __ballot_sync(0xffffffffu, head);
-    if (ok && head) {
-        const uint32_t later = heads & ~(0xFFFFFFFFu >> (31 - lane));   // heads above this lane
-        const uint32_t end = later ? (uint32_t)(__ffs(later) - 1) : 32u;
-        atomicAdd(&cnt[b], end - lane);
-    }
 #else
     uint32_t key_b = ok ? b : 0xFFFFu;
     uint32_t peers = __match_any_sync(0xffffffffu, key_b);
@@ -713,10 +717,15 @@ constexpr int kScatterBatch = SS_SCATTER_BATCH;   // elements whose reads are in
 // inside a warp, warps in order inside the tile); then each payload array in
 // turn is reordered through shared memory into tile-local bucket order, so that
 // consecutive threads write the consecutive positions of a bucket's run.
-// phase A's per-warp counts: 0 = warp match, lanes with equal buckets add once;
-// 1 = one shared atomic per element
+// Phase A's per-warp counts: 1 = one shared atomic per element; 0 = lanes
+// with equal buckets add once (warp match).  Ranks inside a warp step: 1 = the
+// lanes with the same bucket found by one vote per bucket bit (peers_of); 0 =
+// warp match.  The defaults measured fastest on GB300 on every workload.
 #ifndef SS_SCATTER_COUNT
-#define SS_SCATTER_COUNT 0
+#define SS_SCATTER_COUNT 1
+#endif
+#ifndef SS_SCATTER_RANK
+#define SS_SCATTER_RANK 1
 #endif
 
 template <int MODE>
@@ -849,7 +858,11 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     for (int u = 0; u < kItems; u++) {
         const uint32_t b = bk[u];
         const bool ok = b != 0xFFFFu;
+#if SS_SCATTER_RANK == 1
+        uint32_t peers = peers_of(b, d + 1);
+#else
         uint32_t peers = __match_any_sync(0xffffffffu, b);
+#endif
         uint32_t rank = __popc(peers & lanemask_lt());
         uint32_t off = ok ? S.u.wpos[warp][b] : 0u;
         lp[u] = ok ? S.lbase[b] + off + rank : 0u;
