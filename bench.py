@@ -59,6 +59,9 @@ BYTES_PER_UNIT = {
 }
 
 
+L2_BYTES = 129 * 1024 * 1024   # GB300 L2
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -663,7 +666,8 @@ def main():
         try:
             with open(tp) as f:
                 tj = json.load(f)
-            if tj.get("source_hash") == _source_hash():
+            # only for the sources and the workload the counters were taken on
+            if (tj.get("source_hash") == _source_hash() and tj.get("n") == n and tj.get("runs") == K):
                 traffic = tj.get("bytes_per_launch", {}).get(dom)
         except Exception:
             traffic = None
@@ -681,7 +685,10 @@ def main():
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
         "config": {"workload": workload_name(n, K), "n": n, "N_bytes": int(ss.chars.nbytes),
                    "mean_len": ss.meta.get("mean_len"), "runs": K, "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (chars 0.5 GB + offsets 80 MB per step)"},
+                   "l2": (f"inputs larger than L2 (chars {ss.chars.nbytes / 1e9:.2f} GB + offsets "
+                          f"{ss.offsets.nbytes / 1e6:.0f} MB per step)"
+                          if ss.chars.nbytes + ss.offsets.nbytes > L2_BYTES else
+                          "inputs smaller than L2: not a valid bench configuration")},
         "d_gb_per_s": D * (job_strings // n) / (ms / 1e3) / 1e9, "D": D,
         "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
                                 "frac": balg / (ms / 1e3) / 1e9 / peak},
