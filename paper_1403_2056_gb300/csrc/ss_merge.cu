@@ -32,7 +32,10 @@ namespace ss {
 #define SS_MERGE_ITEMS 16
 #endif
 constexpr uint32_t kMergeItems = SS_MERGE_ITEMS;   // outputs per thread
-constexpr uint32_t kCoarse = 256;      // outputs per merge-path window
+#ifndef SS_MERGE_COARSE
+#define SS_MERGE_COARSE 256
+#endif
+constexpr uint32_t kCoarse = SS_MERGE_COARSE;   // outputs per merge-path window
 
 // full comparison of strings a and b from depth h on (both share h characters),
 // 16 characters per round; returns -1/0/+1 and the lcp in *l
@@ -141,18 +144,50 @@ __device__ __forceinline__ uint32_t pair_of_entry(const uint32_t *cbase, uint32_
     return lo;
 }
 
-// window cuts: pair p has entries cbase[p] + k for diagonals min(k kCoarse, na + nb)
+// The same search by a group of kCutLanes lanes: each round the lanes test
+// kCutLanes evenly spaced candidates at once (the comparison is monotone in
+// the candidate), and the range shrinks to the gap between the last one that
+// does not pass A and the first that does, kCutLanes + 1 times smaller.  A cut
+// searches a whole pair from depth 0, so its chain of dependent string reads
+// is what bounds the kernel; the group shortens it from log2 to
+// log_(kCutLanes+1) of the pair length.
+constexpr uint32_t kCutLanes = 8;
+
+__device__ __forceinline__ uint32_t path_search_group(const ReqDesc &S, const PairView &v, uint32_t diag, uint32_t lo,
+                                                      uint32_t hi, uint32_t glane, uint32_t gmask, uint32_t gshift) {
+    while (lo < hi) {
+        const uint32_t n = hi - lo;
+        auto probe = [&](uint32_t k) { return lo + (uint32_t)(((uint64_t)(k + 1) * n) / (kCutLanes + 1)); };
+        const uint32_t x = probe(glane);   // in [lo, hi)
+        uint32_t l;
+        const bool past = str_cmp_from(S, v.A(x), v.OA(x), v.B(diag - 1 - x), v.OB(diag - 1 - x), 0, &l) > 0;
+        const uint32_t votes = (__ballot_sync(gmask, past) >> gshift) & ((1u << kCutLanes) - 1);
+        const uint32_t first = votes ? (uint32_t)(__ffs(votes) - 1) : kCutLanes;   // first probe past A
+        const uint32_t nlo = first > 0 ? probe(first - 1) + 1 : lo;
+        const uint32_t nhi = first < kCutLanes ? probe(first) : hi;
+        lo = nlo;
+        hi = nhi;
+    }
+    return lo;
+}
+
+// window cuts: pair p has entries cbase[p] + k for diagonals min(k kCoarse, na + nb);
+// kCutLanes consecutive lanes per entry
 __global__ void k_merge_cuts(ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint64_t *in_off,
                              const uint32_t *rb, uint32_t R, const uint32_t *rbase, const uint32_t *cbase,
                              uint32_t npairs, uint32_t nentries, Coarse *C) {
-    uint32_t e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= nentries) return;
+    const uint32_t g = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t e = g / kCutLanes, glane = g % kCutLanes;
+    if (e >= nentries) return;   // whole groups leave together
+    const uint32_t gshift = (threadIdx.x & 31) & ~(kCutLanes - 1);
+    const uint32_t gmask = ((1u << kCutLanes) - 1) << gshift;
     uint32_t p = pair_of_entry(cbase, npairs, e);
     PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
     uint32_t len = v.na + v.nb;
     uint32_t diag = min((e - cbase[p]) * kCoarse, len);
     uint32_t lo = diag > v.nb ? diag - v.nb : 0, hi = min(diag, v.na);
-    C[e].i = path_search(S, v, diag, lo, hi, 0);
+    const uint32_t i = path_search_group(S, v, diag, lo, hi, glane, gmask, gshift);
+    if (glane == 0) C[e].i = i;
 }
 
 // characters shared by a whole window: the strings of a window are a
@@ -658,7 +693,7 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
                 SS_LAUNCH_U("run_prep", st, total, k_run_prep<<<grid, 256, 0, st>>>(
                     set, src_p, src_l, d_rb, R, bases, total, 1, off_buf[0], ck_buf[0], ckd_buf[0]));
             }
-            SS_LAUNCH_U("merge_cuts", st, nentries, k_merge_cuts<<<(nentries + 127) / 128, 128, 0, st>>>(
+            SS_LAUNCH_U("merge_cuts", st, nentries, k_merge_cuts<<<(nentries * kCutLanes + 127) / 128, 128, 0, st>>>(
                 set, src_p, src_l, src_o, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
             SS_LAUNCH_U("merge_windows", st, nentries, k_merge_windows<<<(nentries + 127) / 128, 128, 0, st>>>(
                 set, src_p, src_l, src_o, d_rb, R, bases, d_cb, npairs, nentries, d_coarse));
