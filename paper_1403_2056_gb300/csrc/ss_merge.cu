@@ -33,7 +33,7 @@ namespace ss {
 #endif
 constexpr uint32_t kMergeItems = SS_MERGE_ITEMS;   // outputs per thread
 #ifndef SS_MERGE_COARSE
-#define SS_MERGE_COARSE 256
+#define SS_MERGE_COARSE 1024
 #endif
 constexpr uint32_t kCoarse = SS_MERGE_COARSE;   // outputs per merge-path window
 
@@ -148,10 +148,17 @@ __device__ __forceinline__ uint32_t pair_of_entry(const uint32_t *cbase, uint32_
 // kCutLanes evenly spaced candidates at once (the comparison is monotone in
 // the candidate), and the range shrinks to the gap between the last one that
 // does not pass A and the first that does, kCutLanes + 1 times smaller.  A cut
-// searches a whole pair from depth 0, so its chain of dependent string reads
-// is what bounds the kernel; the group shortens it from log2 to
-// log_(kCutLanes+1) of the pair length.
-constexpr uint32_t kCutLanes = 8;
+// searches a whole pair from depth 0; with few cuts (one per kCoarse outputs)
+// the chain of dependent string reads bounds the kernel, which the group
+// shortens from log2 to log_(kCutLanes+1) of the pair length.  Measured on
+// GB300 (4 runs of 10 M URL-like / 20 M DNA strings): 4 lanes with 1024-output
+// windows beat one lane with 256-output windows by 6 % / 2 % of the merge.
+#ifndef SS_CUT_LANES
+#define SS_CUT_LANES 4
+#endif
+constexpr uint32_t kCutLanes = SS_CUT_LANES;   // a power of two, at most 32
+constexpr uint32_t kCutMask = kCutLanes == 32 ? 0xFFFFFFFFu : ((1u << kCutLanes) - 1);
+static_assert((kCutLanes & (kCutLanes - 1)) == 0 && kCutLanes >= 1 && kCutLanes <= 32, "lanes per cut");
 
 __device__ __forceinline__ uint32_t path_search_group(const ReqDesc &S, const PairView &v, uint32_t diag, uint32_t lo,
                                                       uint32_t hi, uint32_t glane, uint32_t gmask, uint32_t gshift) {
@@ -161,7 +168,7 @@ __device__ __forceinline__ uint32_t path_search_group(const ReqDesc &S, const Pa
         const uint32_t x = probe(glane);   // in [lo, hi)
         uint32_t l;
         const bool past = str_cmp_from(S, v.A(x), v.OA(x), v.B(diag - 1 - x), v.OB(diag - 1 - x), 0, &l) > 0;
-        const uint32_t votes = (__ballot_sync(gmask, past) >> gshift) & ((1u << kCutLanes) - 1);
+        const uint32_t votes = (__ballot_sync(gmask, past) >> gshift) & kCutMask;
         const uint32_t first = votes ? (uint32_t)(__ffs(votes) - 1) : kCutLanes;   // first probe past A
         const uint32_t nlo = first > 0 ? probe(first - 1) + 1 : lo;
         const uint32_t nhi = first < kCutLanes ? probe(first) : hi;
@@ -180,7 +187,7 @@ __global__ void k_merge_cuts(ReqDesc S, const uint32_t *in_perm, const uint32_t 
     const uint32_t e = g / kCutLanes, glane = g % kCutLanes;
     if (e >= nentries) return;   // whole groups leave together
     const uint32_t gshift = (threadIdx.x & 31) & ~(kCutLanes - 1);
-    const uint32_t gmask = ((1u << kCutLanes) - 1) << gshift;
+    const uint32_t gmask = kCutMask << gshift;
     uint32_t p = pair_of_entry(cbase, npairs, e);
     PairView v = pair_view(S, p, in_perm, in_lcp, in_off, rb, R, rbase);
     uint32_t len = v.na + v.nb;
