@@ -776,13 +776,41 @@ def main():
     return 0
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++ source without // and /* */ comments (string and character
+    literals kept), whitespace runs collapsed: what the compiler sees."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _source_hash():
+    """Hash of the CUDA sources without their comments: DRAM counters taken on
+    one revision stay valid across comment-only edits."""
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1403_2056_gb300", "csrc")
     for f in sorted(os.listdir(d)):
         if f.endswith((".cu", ".cuh")):
-            h.update(open(os.path.join(d, f), "rb").read())
+            h.update(f.encode() + b"\0")
+            h.update(_strip_comments(open(os.path.join(d, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

@@ -4,15 +4,16 @@
 // The paper merges K runs with one LCP-aware tournament tree per job and
 // splits jobs by LCP minima (Section 5.3).  On the GPU the K-way merge is
 // ceil(log2 K) rounds of pairwise merges.  Inside a round the output of every
-// pair is cut by merge path (binary search on the cross diagonal, full string
-// comparisons) at every kCoarse outputs, with the characters each window's
-// strings share; then every chunk of kMergeItems outputs gets its start (the
-// search inside its window, from the shared prefix, and the LCPs of both
-// fronts with the string before the chunk: one side's is the run's own LCP
-// entry, the other is one string comparison).  The merge proper runs per CTA
-// window of kMergeTile outputs: the window's LCPs and cached characters are
-// staged in shared memory, each thread runs the binary LCP-merge over its
-// chunk there, and the CTA writes the outputs with coalesced stores.
+// pair is cut by merge path (a search on the cross diagonal by a group of
+// lanes, full string comparisons) at every kCoarse outputs, with the
+// characters each window's strings share; then every chunk of kMergeItems
+// outputs gets its start (the search inside its window, from the shared
+// prefix, and the LCPs of both fronts with the string before the chunk: one
+// side's is the run's own LCP entry, the other is one string comparison).
+// The merge proper runs per CTA window of kMergeTile outputs: the window's
+// LCPs and cached characters are staged in shared memory, each thread runs
+// the binary LCP-merge over its chunk there, and the CTA writes the outputs
+// with coalesced stores.
 // Comparisons whose LCPs differ cost no string access at all (cases 2 and 3
 // of LCP-Compare); equal LCPs first try the cached characters, and only then
 // read characters, 8 at a time from the known common prefix on.
