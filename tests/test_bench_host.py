@@ -1,0 +1,42 @@
+"""Host-side pieces of bench.py (no GPU): the reference arm's JSON line and
+the comment-insensitive source hash that guards the stored DRAM counters."""
+import json
+import os
+import subprocess
+import sys
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+
+
+def test_strip_comments_keeps_code_and_literals():
+    src = ('a = "http://x" /* c1 */ + b; // tail\n'
+           "char q = '/'; int z = 1; /* multi\nline */ w = \"\\\"//\"; // x\n"
+           "s = \"/* not a comment */\";")
+    out = bench._strip_comments(src)
+    assert out == ('a = "http://x" + b; char q = \'/\'; int z = 1; w = "\\"//"; '
+                   's = "/* not a comment */";')
+
+
+def test_strip_comments_ignores_comment_and_spacing_edits_only():
+    a = "int f(int x) {  // one\n  return x + 1; /* two */\n}\n"
+    b = "int f(int x) {\n  // other words\n  return x + 1;\n}\n"
+    c = "int f(int x) {\n  return x + 2;\n}\n"
+    assert bench._strip_comments(a) == bench._strip_comments(b)
+    assert bench._strip_comments(a) != bench._strip_comments(c)
+
+
+def test_reference_arm_prints_one_json_line():
+    """`bench.py --impl reference` times the oracle on the host and prints the
+    contract's line with impl, cpu_baseline and e2e."""
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "20000",
+                        "--steps", "1", "--warmup", "1"], capture_output=True, text=True, cwd=ROOT, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [l for l in r.stdout.splitlines() if l.strip()]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "strings/s" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
