@@ -429,7 +429,9 @@ class Clocks:
 
     def __init__(self, index):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_rank{index}.csv")
+        # raw samples go to $SS_BENCH_OUT (default: bench_out/ in the repository)
+        out = os.environ.get("SS_BENCH_OUT", os.path.join(ROOT, "bench_out"))
+        self.path = os.path.join(out, f"clocks_rank{index}.csv")
         self.index = index
         self.t0 = self.t1 = None
 
