@@ -809,10 +809,11 @@ def _source_hash():
     import hashlib
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1403_2056_gb300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            h.update(f.encode() + b"\0")
-            h.update(_strip_comments(open(os.path.join(d, f), encoding="utf-8").read()).encode())
+    files = [os.path.join(d, f) for f in sorted(os.listdir(d)) if f.endswith((".cu", ".cuh"))]
+    files.append(os.path.join(ROOT, "include", "ss.h"))
+    for path in files:
+        h.update(os.path.basename(path).encode() + b"\0")
+        h.update(_strip_comments(open(path, encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

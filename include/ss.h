@@ -101,8 +101,11 @@ int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len_host, const uint6
 
 /*
  * One independent sort request of a batch.  Fields as in ss_sort_ex; all
- * pointers are device pointers.  status_out_dev may be NULL; otherwise the
- * library writes the request's ss_status (int32) there when it is done.
+ * pointers are device pointers.  status_out may be NULL; otherwise the
+ * library writes an int32 ss_status there on the device, in stream order:
+ * SS_OK when the request's outputs are complete, SS_ERR_INTERNAL when a
+ * device-side check of the batch failed.  Argument errors are reported by
+ * the return value alone, before anything is written.
  */
 typedef struct {
     const uint8_t *chars;
