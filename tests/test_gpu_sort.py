@@ -87,6 +87,37 @@ def test_long_common_prefix_last_char_differs():
     _check(W.from_bytes_list(strs))
 
 
+def test_deep_recursion_two_long_prefixes():
+    """Two halves with different 1,000-character prefixes: no request-wide
+    shared prefix, so both big segments recurse 8 characters per level for
+    about 125 levels before their strings differ."""
+    rng = np.random.default_rng(5)
+    strs = []
+    for k in range(6000):
+        pre = (b"a" if k % 2 else b"b") * 1000
+        strs.append(pre + bytes(rng.integers(97, 100, int(rng.integers(0, 6))).astype(np.uint8)))
+    _check(W.from_bytes_list(strs))
+
+
+def test_prefix_chain_and_duplicates():
+    """Every string a prefix of the next ("x", "xx", ... 3,000 x's), each twice,
+    shuffled: the order is by length, ties by index, and every LCP is the
+    shorter length."""
+    rng = np.random.default_rng(6)
+    strs = [b"x" * L for L in range(1, 3001)] * 2
+    order = rng.permutation(len(strs))
+    _check(W.from_bytes_list([strs[i] for i in order]))
+
+
+def test_explicit_lengths_long_strings():
+    """Length-delimited strings of up to 4,000 bytes over two letters, packed
+    back to back without terminators."""
+    rng = np.random.default_rng(7)
+    strs = [bytes(rng.integers(1, 3, int(rng.integers(0, 4000))).astype(np.uint8)) for _ in range(3000)]
+    strs += strs[:500]   # duplicates
+    _check(W.from_bytes_list(strs, terminated=False))
+
+
 def test_high_bytes_and_unaligned_offsets():
     rng = np.random.default_rng(3)
     strs = [bytes(rng.integers(1, 256, int(rng.integers(0, 40))).astype(np.uint8)) for _ in range(70000)]
