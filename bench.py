@@ -77,6 +77,9 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-plain measurement")
     ap.add_argument("--batched-requests", type=int, default=4096)
     ap.add_argument("--no-serving", action="store_true", help="skip the served-vs-plain measurement")
+    ap.add_argument("--e2e-workers", type=int, default=4, help="server workers for the end-to-end stream")
+    ap.add_argument("--e2e-inflight", type=int, default=6, help="host-request steps in flight end to end")
+    ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end stream (0: max(30, --steps))")
     ap.add_argument("--serving-requests", type=int, default=2000)
     return ap.parse_args()
 
@@ -723,19 +726,20 @@ def main():
         torch.cuda.synchronize(dev)
         one_ms, _ = aggregate(dist, (time.perf_counter() - t0) / reps * 1e3, n, dev)
         same = np.array_equal(hp.numpy(), perm.cpu().numpy()) and np.array_equal(hl.numpy(), lcp.cpu().numpy())
-        # the same steps as a stream of host requests through a 2-worker server:
-        # each step still copies its inputs in and its result out, and one step's
-        # copies overlap the previous step's sort
+        # the same steps as a stream of host requests through the server: each
+        # step still copies its inputs in and its result out, and one step's
+        # copies overlap another step's sort
         outs = [(torch.empty(n, dtype=torch.int32).pin_memory(), torch.empty(n, dtype=torch.int32).pin_memory())
-                for _ in range(3)]
-        with P.Server(64 << 30, workers=2) as srv:
+                for _ in range(max(1, args.e2e_inflight))]
+        with P.Server(64 << 30, workers=args.e2e_workers) as srv:
             for k in range(2):
-                srv.wait(srv.submit_host(hc, ho, None, 0, outs[k][0], outs[k][1], runs=K))
+                o = outs[k % len(outs)]
+                srv.wait(srv.submit_host(hc, ho, None, 0, o[0], o[1], runs=K))
             barrier()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
             inflight = []
-            reps_p = max(6, args.steps)
+            reps_p = args.e2e_steps if args.e2e_steps > 0 else max(30, args.steps)
             for i in range(reps_p):
                 if len(inflight) == len(outs):
                     st_, _ = srv.wait(inflight.pop(0))
@@ -751,8 +755,8 @@ def main():
         line["e2e"] = {"value": e2e_strings / (pipe_ms / 1e3), "unit": "strings/s",
                        "h2d_bytes_per_step": int(ss.chars.nbytes + 8 * n), "d2h_bytes_per_step": int(8 * n),
                        "ms_per_step": pipe_ms, "steps": reps_p,
-                       "api": "ss_server_submit_host (2 workers, up to 3 steps in flight): copies in, sort of 4 runs + "
-                              "merge, copies out per step",
+                       "api": (f"ss_server_submit_host ({args.e2e_workers} workers, up to {len(outs)} steps in "
+                               f"flight): copies in, sort of {K} runs + merge, copies out per step"),
                        "single_call": {"api": "ss_sort_host, one call per step", "ms_per_step": one_ms,
                                        "value": e2e_strings / (one_ms / 1e3)},
                        "equals_device_result": bool(same)}
