@@ -514,6 +514,22 @@ def cpu_baseline(ss, seconds):
             "sample": f"first {m:,} strings of the workload, one qsort + naive LCP pass ({dt:.1f} s)"}
 
 
+def cpu_parallel(ss):
+    """Context beside the oracle: the same order from a parallel library
+    stable sort (libstdc++ parallel mode, OpenMP) on all host cores, on the
+    whole workload."""
+    import oracle
+    try:
+        t0 = time.perf_counter()
+        _, _, used = oracle.sort_parallel(ss, threads=os.cpu_count() or 1)
+        dt = time.perf_counter() - t0
+    except Exception as e:   # no g++/OpenMP on this host
+        return {"unavailable": f"parallel CPU baseline not built: {e}"}
+    return {"value": ss.n / dt, "unit": "strings/s", "cores": used,
+            "kind": "library parallel stable sort with the oracle's comparator + naive LCP",
+            "sample": f"the whole workload, {ss.n:,} strings ({dt:.1f} s)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -775,6 +791,7 @@ def main():
         import oracle
         oracle.build()
         line["cpu_baseline"] = cpu_baseline(ss, args.cpu_seconds)
+        line["cpu_parallel"] = cpu_parallel(ss)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

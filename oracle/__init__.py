@@ -40,6 +40,40 @@ def build(force: bool = False) -> str:
     return _SO
 
 
+_PAR_SRC = os.path.join(_HERE, "parallel.cpp")
+_PAR_SO = os.path.join(_OUT_DIR, "libparallel.so")
+_par = None
+
+
+def build_parallel(force: bool = False) -> str:
+    """Compile parallel.cpp (the parallel library-sort baseline) with g++ and OpenMP."""
+    os.makedirs(_OUT_DIR, exist_ok=True)
+    if force or not os.path.exists(_PAR_SO) or os.path.getmtime(_PAR_SO) < os.path.getmtime(_PAR_SRC):
+        tmp = _PAR_SO + f".tmp{os.getpid()}"
+        subprocess.check_call(["g++", "-O2", "-std=c++17", "-fopenmp", "-Wall", "-shared", "-fPIC", "-o", tmp,
+                               _PAR_SRC])
+        os.replace(tmp, _PAR_SO)
+    return _PAR_SO
+
+
+def sort_parallel(ss, threads: int = 0):
+    """(perm, lcp, threads used): the oracle's order by a parallel library
+    stable sort on `threads` host threads (0: all), naive LCPs; a CPU
+    baseline for comparison, checked against sort() by the tests."""
+    global _par
+    with _lock:
+        if _par is None:
+            lib = C.CDLL(build_parallel())
+            lib.orc_sort_parallel.argtypes = [_u8p, _u64p, _u32p, C.c_uint32, C.c_uint64, _u32p, _u32p, C.c_int]
+            lib.orc_sort_parallel.restype = C.c_int
+            _par = lib
+    keep, a = _set(ss)
+    perm = np.empty(ss.n, np.uint32)
+    lcp = np.empty(ss.n, np.uint32)
+    used = _par.orc_sort_parallel(*a, ss.n, _p(perm, _u32p), _p(lcp, _u32p), int(threads))
+    return perm, lcp, int(used)
+
+
 def _load():
     global _lib
     with _lock:

@@ -428,3 +428,20 @@ def test_check_sorted_tie_order():
     ss = W.from_bytes_list([b"x", b"x", b"a"])
     assert oracle.check_sorted(ss, np.array([2, 0, 1]), np.array([0, 0, 1])) == (0, 3)
     assert oracle.check_sorted(ss, np.array([2, 1, 0]), np.array([0, 0, 1]))[0] == 1   # equal strings out of index order
+
+
+# ------------------------------------------- parallel library-sort baseline
+
+def test_parallel_baseline_equals_oracle():
+    """The CPU baseline that sorts with a parallel library stable sort gives
+    the oracle's perm and lcp (same order, ties by index) on every layout."""
+    sets = [W.random_lower(30_000, seed=31, min_len=0, max_len=12), W.url_like(20_000, seed=32),
+            W.sinha_dna_like(20_000, seed=33), W.dna_windows(15_000, 300_100, 100, seed=34),
+            W.paper_random(20_000, seed=35),
+            W.from_bytes_list([b"ab", b"", b"a", b"ab", b"b\xff", b"b", b""] * 300, terminated=False)]
+    for ss in sets:
+        want_perm, want_lcp = oracle.sort(ss)
+        perm, lcp, used = oracle.sort_parallel(ss, threads=4)
+        assert used >= 1
+        assert np.array_equal(perm, want_perm), ss.name
+        assert np.array_equal(lcp, want_lcp), ss.name
