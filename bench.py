@@ -133,6 +133,7 @@ def other_workloads(P, torch, dev, stream, peak):
         nl, tms, units = prof[dom]
         bpu = BYTES_PER_UNIT.get(dom)
         ach = units * bpu / (tms / 1e3) / 1e9 if bpu else None
+        radix = library_radix_context(P, torch, dev, stream, chars, offsets, n) if name == "no_lcp_64Mi" else None
         cls_cmp = compare_classifiers(P, torch, dev, stream, [dict(chars=chars, offsets=offsets, lengths=None,
                                                                    fixed_len=ss.fixed_len, n=n, perm_out=perm,
                                                                    lcp_out=lcp)])
@@ -143,9 +144,39 @@ def other_workloads(P, torch, dev, stream, peak):
                      "dominant_kernel": {"kernel": dom, "ms": tms, "share": tms / sum(v[1] for v in prof.values()),
                                          "achieved_gbs": ach, "frac": (ach / peak) if ach else None},
                      "classifiers": cls_cmp}
+        if radix:
+            out[name]["library_radix_sort_context"] = radix
         del chars, offsets, perm, lcp
         torch.cuda.empty_cache()
     return out
+
+
+def library_radix_context(P, torch, dev, stream, chars, offsets, n, reps=5):
+    """Context only: a library radix sort (torch.sort, stable, on CUDA) of
+    each string's first 8 bytes as a 64-bit key with the string indices, the
+    keys gathered by ss_gather_keys.  It orders by 8 characters only and
+    returns no LCPs, so it is not a string sort; it shows what one pass of a
+    tuned 64-bit key sort costs on the same device."""
+    depth = torch.zeros(n, dtype=torch.int32, device=dev)
+    keys = torch.empty(n, dtype=torch.int64, device=dev)
+    P.ss_gather_keys(chars, offsets, None, 0, n, depth, keys, stream=stream)
+    skeys = keys ^ torch.tensor(-(1 << 63), dtype=torch.int64, device=dev)   # unsigned order as signed
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            torch.sort(skeys, stable=True)
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            torch.sort(skeys, stable=True)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1) / reps
+    del depth, keys, skeys
+    return {"ms": ms, "keys_per_s": n / (ms / 1e3),
+            "what": "torch.sort(stable) of the 64-bit first-8-byte keys with indices: a library radix sort, "
+                    "8 characters only, no LCPs; context, not a target"}
 
 
 CLASSIFIERS = ("unroll", "equal", "jump")
