@@ -54,7 +54,8 @@ typedef enum {
     SS_ERR_TIMEOUT = -4,       /* a bounded device-side wait gave up */
     SS_ERR_TOO_LARGE = -5,     /* n or a total beyond 2^32 - 2 */
     SS_ERR_UNIMPLEMENTED = -6, /* feature not available in this build */
-    SS_ERR_INTERNAL = -7       /* a device-side consistency check failed */
+    SS_ERR_INTERNAL = -7,      /* a device-side consistency check failed */
+    SS_ERR_CANCELLED = -8      /* a queued server request was cancelled before it started */
 } ss_status;
 
 /*
@@ -307,6 +308,10 @@ int ss_classify_ex(const uint64_t *keys_dev, uint32_t n, const uint64_t *x_dev, 
  *   status (an ss_status) and, if times_ms_out is not NULL, three times in ms
  *   on the server's clock: submitted, batch started, batch finished.  Each
  *   ticket is waited for once; an unknown ticket gives SS_ERR_INVALID.
+ * ss_server_cancel: withdraws a request that is still queued: *cancelled_out
+ *   = 1, and its ss_server_wait reports SS_ERR_CANCELLED with its outputs
+ *   untouched.  A request a worker has already taken runs to the end:
+ *   *cancelled_out = 0.  SS_ERR_INVALID for an unknown ticket.
  * ss_server_destroy: finishes every submitted request, stops the workers and
  *   frees the server.
  * ss_scratch_bytes: scratch bytes one request of n strings is charged.
@@ -336,8 +341,18 @@ typedef struct {
 } ss_host_request;
 int ss_server_submit_host(ss_server *server, const ss_host_request *req, uint64_t *ticket_out);
 int ss_server_wait(ss_server *server, uint64_t ticket, int32_t *status_out, double *times_ms_out);
+int ss_server_cancel(ss_server *server, uint64_t ticket, int32_t *cancelled_out);
 int ss_server_destroy(ss_server *server);
 uint64_t ss_scratch_bytes(uint32_t n);
+
+/*
+ * ss_debug_fail_allocs -- fault injection on the host for tests: of the
+ * library's next scratch allocations (any thread), the first `skip` succeed
+ * and the `count` after them fail as an exhausted pool would, so the calls
+ * that make them return SS_ERR_OOM (a server request gets it as its status).
+ * count = 0 switches injection off.  Nothing is injected on the device.
+ */
+int ss_debug_fail_allocs(uint32_t skip, uint32_t count);
 
 /* Kernel timing: when enabled, the library records CUDA events around each of
  * its kernel launches (on the launch stream) and accumulates per-kernel time.

@@ -31,7 +31,7 @@ __all__ = [
 CLASSIFIER_UNROLL, CLASSIFIER_EQUAL, CLASSIFIER_JUMP = 0, 1, 2
 
 STATUS = {0: "SS_OK", -1: "SS_ERR_INVALID", -2: "SS_ERR_OOM", -3: "SS_ERR_CUDA", -4: "SS_ERR_TIMEOUT",
-          -5: "SS_ERR_TOO_LARGE", -6: "SS_ERR_UNIMPLEMENTED", -7: "SS_ERR_INTERNAL"}
+          -5: "SS_ERR_TOO_LARGE", -6: "SS_ERR_UNIMPLEMENTED", -7: "SS_ERR_INTERNAL", -8: "SS_ERR_CANCELLED"}
 
 
 class SortError(RuntimeError):
@@ -81,12 +81,15 @@ def lib():
     L.ss_sort_batch_tuned.argtypes = [vp, vp, u32, vp]
     L.ss_autotune.argtypes = [vp, u32, C.POINTER(Tuning), C.POINTER(C.c_double), vp]
     L.ss_server_destroy.argtypes = [vp]
+    L.ss_server_cancel.argtypes = [vp, u64, C.POINTER(i32)]
+    L.ss_debug_fail_allocs.argtypes = [u32, u32]
     L.ss_scratch_bytes.argtypes = [u32]
     L.ss_scratch_bytes.restype = u64
     for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_classify_ex", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
                  "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
-                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_autotune"):
+                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_autotune", "ss_server_cancel",
+                 "ss_debug_fail_allocs"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -259,8 +262,22 @@ def ss_server_wait(server, ticket: int):
     return int(st.value), (tm[0], tm[1], tm[2])
 
 
+def ss_server_cancel(server, ticket: int) -> bool:
+    """True if the request was still queued and is withdrawn (its wait reports
+    SS_ERR_CANCELLED); False if a worker already took it."""
+    c = C.c_int32()
+    _check(lib().ss_server_cancel(server, int(ticket), C.byref(c)))
+    return bool(c.value)
+
+
 def ss_server_destroy(server):
     _check(lib().ss_server_destroy(server))
+
+
+def ss_debug_fail_allocs(skip: int, count: int):
+    """Host-side fault injection for tests: after `skip` successful scratch
+    allocations, the next `count` fail as an exhausted pool would (0: off)."""
+    _check(lib().ss_debug_fail_allocs(int(skip), int(count)))
 
 
 class Server:
@@ -288,6 +305,9 @@ class Server:
         r = ss_server_wait(self._h, ticket)
         self._keep.pop(ticket, None)
         return r
+
+    def cancel(self, ticket: int) -> bool:
+        return ss_server_cancel(self._h, ticket)
 
     def close(self):
         if self._h:

@@ -63,7 +63,27 @@ static cudaMemPool_t pool_for_current() {
     return pool;
 }
 
+// host-side allocation-failure injection (ss_debug_fail_allocs)
+static std::atomic<uint32_t> g_inject_skip{0}, g_inject_fail{0};
+static std::mutex g_inject_mu;
+
+static bool inject_failure() {
+    if (g_inject_fail.load(std::memory_order_relaxed) == 0) return false;
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    if (g_inject_fail.load() == 0) return false;
+    if (g_inject_skip.load() > 0) {
+        g_inject_skip.fetch_sub(1);
+        return false;
+    }
+    g_inject_fail.fetch_sub(1);
+    return true;
+}
+
 cudaError_t scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+    if (inject_failure()) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
     cudaMemPool_t pool = pool_for_current();
     if (!pool) return cudaErrorMemoryAllocation;
     return cudaMallocFromPoolAsync(p, bytes ? bytes : 256, pool, s);
@@ -532,5 +552,12 @@ int ss_profile_read(char *names48, uint64_t *launches, double *total_ms, uint64_
 }
 
 uint64_t ss_launch_count(void) { return g_launches.load(); }
+
+int ss_debug_fail_allocs(uint32_t skip, uint32_t count) {
+    std::lock_guard<std::mutex> lk(g_inject_mu);
+    g_inject_skip.store(count ? skip : 0u);
+    g_inject_fail.store(count);
+    return SS_OK;
+}
 
 }  // extern "C"

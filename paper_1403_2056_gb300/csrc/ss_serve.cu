@@ -271,6 +271,39 @@ int ss_server_wait(ss_server *server, uint64_t ticket, int32_t *status_out, doub
     return SS_OK;
 }
 
+int ss_server_cancel(ss_server *server, uint64_t ticket, int32_t *cancelled_out) {
+    Server *s = reinterpret_cast<Server *>(server);
+    if (!s) {
+        set_error_detail("ss_server_cancel: NULL server");
+        return SS_ERR_INVALID;
+    }
+    std::lock_guard<std::mutex> lk(s->mu);
+    auto it = s->jobs.find(ticket);
+    if (it == s->jobs.end()) {
+        set_error_detail("ss_server_cancel: unknown ticket %llu", (unsigned long long)ticket);
+        return SS_ERR_INVALID;
+    }
+    // only a job still in the queue can be withdrawn; it holds no budget yet
+    bool cancelled = false;
+    for (auto w = s->waiting.begin(); w != s->waiting.end(); ++w) {
+        if (*w == ticket) {
+            s->waiting.erase(w);
+            ServerJob &j = it->second;
+            j.status = SS_ERR_CANCELLED;
+            j.t_start = j.t_done = s->now_ms();
+            j.done = true;
+            cancelled = true;
+            break;
+        }
+    }
+    if (cancelled) {
+        s->cv_done.notify_all();
+        s->cv_work.notify_all();   // the queue's head may have changed
+    }
+    if (cancelled_out) *cancelled_out = cancelled ? 1 : 0;
+    return SS_OK;
+}
+
 int ss_server_destroy(ss_server *server) {
     Server *s = reinterpret_cast<Server *>(server);
     if (!s) return SS_OK;
