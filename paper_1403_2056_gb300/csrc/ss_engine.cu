@@ -9,8 +9,11 @@
 //
 //   k_build_trees  sample (alpha = 2), sort, pick splitters with the
 //                  skip-equal-samples recursion (Section 4.4)      one CTA / segment
-//   k_classify     tree descent + equality test per 8-byte key,
-//                  bucket buffer, per-tile histogram (Alg. 1 loops)  one CTA / tile
+//   k_jump_tables  (jump-table classifier only) a table over the key bits
+//                  after the splitters' shared prefix (Section 8.1)  one CTA / segment
+//   k_classify     tree descent + equality test per 8-byte key (or the
+//                  S5-Equal descent, or table + descent), bucket buffer,
+//                  per-tile histogram (Alg. 1 loops)                 one CTA / tile
 //   k_scan_*       exclusive prefix sum over the bucket-major
 //                  (segment, bucket, tile) counters (Theorem 1)
 //   k_scatter      stable out-of-place redistribution of (index, offset,
