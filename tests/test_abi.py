@@ -81,3 +81,19 @@ def test_classifier_range_checked_on_the_host():
     rc = P.lib().ss_classify_ex(None, 0, None, 3, 3, None, None, None, None)
     assert rc == -1
     assert "classifier" in P._detail()
+
+
+def test_header_is_plain_c_and_cxx(tmp_path):
+    """include/ss.h compiles as strict C99 and as C++ (a C ABI with no torch or
+    CUDA types beyond an opaque stream pointer)."""
+    import shutil
+    import subprocess
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "use_header.c"
+    src.write_text('#include "ss.h"\n'
+                   "int main(void) { ss_tuning t = {0, 0, SS_CLASSIFIER_JUMP}; (void)t;\n"
+                   "  ss_request q = {0}; (void)q; return SS_ERR_CANCELLED == -8 ? 0 : 1; }\n")
+    for cc, args in (("gcc", ["-std=c99", "-pedantic", "-Werror", "-Wall"]), ("g++", ["-std=c++11", "-x", "c++"])):
+        if shutil.which(cc) is None:
+            continue
+        subprocess.run([cc, *args, "-I", inc, "-c", str(src), "-o", str(tmp_path / f"o_{cc}.o")], check=True)
