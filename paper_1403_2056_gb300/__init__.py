@@ -180,9 +180,40 @@ def _off(offsets):
     return _ptr(offsets)
 
 
+def _host(a, itemsize, what, min_len=None):
+    """Checks a host array (numpy or CPU tensor): integer elements of the given
+    size, one dimension, at least min_len of them."""
+    if a is None:
+        return
+    if isinstance(a, np.ndarray):
+        ok_kind, size, length, on_host = a.dtype.kind in "iu", a.dtype.itemsize, a.size, True
+        ndim = a.ndim
+    else:
+        ok_kind = not (a.dtype.is_floating_point or a.dtype.is_complex)
+        size, length, on_host, ndim = a.element_size(), a.numel(), not a.is_cuda, a.dim()
+    if not on_host:
+        raise ValueError(f"{what} must be a host array")
+    if not ok_kind or size != itemsize:
+        raise TypeError(f"{what} must hold {8 * itemsize}-bit integers")
+    if ndim != 1:
+        raise ValueError(f"{what} must be one-dimensional")
+    if min_len is not None and length < min_len:
+        raise ValueError(f"{what} holds {length} elements, needs {min_len}")
+
+
+def _check_host_request(chars, offsets, lengths, perm_out, lcp_out):
+    n = int(offsets.shape[0])
+    _host(chars, 1, "chars")
+    _host(offsets, 8, "offsets")
+    _host(lengths, 4, "lengths", n)
+    _host(perm_out, 4, "perm_out", n)
+    _host(lcp_out, 4, "lcp_out", n)
+    return n
+
+
 def ss_sort_host(chars, offsets, lengths, fixed_len, perm_out, lcp_out, runs=1, stream=None):
     """Host arrays (numpy, or pinned CPU tensors) in and out; the copies happen inside the call."""
-    n = int(offsets.shape[0])
+    n = _check_host_request(chars, offsets, lengths, perm_out, lcp_out)
     nbytes = int(chars.nbytes) if isinstance(chars, np.ndarray) else int(chars.numel() * chars.element_size())
     _check(lib().ss_sort_host(_ptr(chars), nbytes, _ptr(offsets), _ptr(lengths), int(fixed_len), n, int(runs),
                               _ptr(perm_out), _ptr(lcp_out), _stream(stream)))
@@ -246,7 +277,7 @@ def ss_server_submit(server, q) -> int:
 
 def ss_server_submit_host(server, chars, offsets, lengths, fixed_len, perm_out, lcp_out, runs=1) -> int:
     """Host arrays (numpy, or pinned CPU tensors), as for ss_sort_host."""
-    n = int(offsets.shape[0])
+    n = _check_host_request(chars, offsets, lengths, perm_out, lcp_out)
     nbytes = int(chars.nbytes) if isinstance(chars, np.ndarray) else int(chars.numel() * chars.element_size())
     q = HostRequest(_ptr(chars), nbytes, _ptr(offsets), _ptr(lengths), int(fixed_len), n, int(runs), _ptr(perm_out),
                     _ptr(lcp_out))

@@ -97,3 +97,25 @@ def test_header_is_plain_c_and_cxx(tmp_path):
         if shutil.which(cc) is None:
             continue
         subprocess.run([cc, *args, "-I", inc, "-c", str(src), "-o", str(tmp_path / f"o_{cc}.o")], check=True)
+
+
+def test_host_buffer_arguments_checked_before_any_device_work():
+    """ss_sort_host refuses host arrays of the wrong element size, shape or
+    length in the binding, before the library is called."""
+    import numpy as np
+    import paper_1403_2056_gb300 as P
+    chars = np.frombuffer(b"b\0a\0", np.uint8).copy()
+    offs = np.array([0, 2], np.uint64)
+    good = lambda: np.zeros(2, np.uint32)
+    bad_cases = [
+        (dict(perm_out=np.zeros(2, np.float32)), TypeError),
+        (dict(lcp_out=np.zeros(1, np.uint32)), ValueError),
+        (dict(offsets=np.array([0, 2], np.uint32)), TypeError),
+        (dict(perm_out=np.zeros((2, 1), np.uint32)), ValueError),
+        (dict(lengths=np.array([1], np.uint32)), ValueError),
+    ]
+    for change, exc in bad_cases:
+        args = dict(chars=chars, offsets=offs, lengths=None, fixed_len=0, perm_out=good(), lcp_out=good())
+        args.update(change)
+        with pytest.raises(exc):
+            P.ss_sort_host(**args)
