@@ -34,29 +34,37 @@ sys.path.insert(0, ROOT)
 
 METRIC = "strings/s and D-GB/s vs HBM roofline (bit-exact); batched p50/p99 vs plain"
 
-# Algorithmic bytes per unit of each kernel (unit = string, counter or record);
-# the minimal traffic the step needs, independent of cache behaviour.
+# Algorithmic bytes per unit of each kernel (unit = string, counter or record):
+# the minimal traffic of the step the kernel performs, as the hot-path table
+# lays out its inputs and outputs, independent of cache behaviour and of what
+# this implementation carries beside it (CARRIED_BYTES_PER_UNIT).
 BYTES_PER_UNIT = {
-    "init": 8 + 8 + 4 + 8,           # offset read, key gather, index + key write
-    "classify": 8 + 2,               # key read, bucket write
-    # bucket id, index, string offset, carried key read; index, offset, key written
-    # (the gather of a key at a new depth is extra: it is counted in the whole-sort B_alg)
-    "scatter": 2 + 4 + 8 + 8 + 4 + 8 + 8,
-    "base_warp": 4 + 8 + 4 + 4,      # index + key read, perm + lcp write
+    # a1: offset read, 8-byte key gathered, key + string index written
+    "init": 8 + 8 + 8 + 4,
+    # a3: key read, bucket id (u16) written
+    "classify": 8 + 2,
+    # a6: bucket id read; string index (u32) and next key (u64) read and written
+    "scatter": 2 + 4 + 8 + 4 + 8,
+    # a8: index + key read, perm + lcp written
+    "base_warp": 4 + 8 + 4 + 4,
     "base_c1": 4 + 8 + 4 + 4,
     "base_c2": 4 + 8 + 4 + 4,
     "base_c3": 4 + 8 + 4 + 4,
-    "boundary": 4 + 4 + 8 + 8 + 4,   # two perm reads, two key gathers, lcp write
-    # per output: perm, lcp, offset, cached key + its depth read (28 B); written again in a
-    # round that feeds another (28 B), perm + lcp only in the last round (8 B): mean of the
-    # two rounds of a 4-way merge
-    "merge_round": (28 + 28 + 28 + 8) / 2,
-    "run_prep": 4 + 4 + 8 + 8 + 8 + 4,   # perm + lcp read, offset gather, offset + cached key + depth write
+    # a9: two perm reads, two key gathers, lcp write
+    "boundary": 4 + 4 + 8 + 8 + 4,
+    # a10: per output of a merge round, (index, lcp) read and written
+    "merge_round": 4 + 4 + 4 + 4,
+    "merge_kway": 4 + 4 + 4 + 4,
     "copy_run": 16,
     "scan_reduce": 4,
     "scan_down": 8,
     "buckets": 8,
 }
+# Bytes per unit that this implementation moves beyond the table's layout by
+# design (reported beside the roofline, never inside it): the scatter carries
+# each string's 8-byte offset with its index (read and written) so that a
+# later key gather is one random read instead of two.
+CARRIED_BYTES_PER_UNIT = {"scatter": 8 + 8}
 
 
 L2_BYTES = 129 * 1024 * 1024   # GB300 L2
@@ -80,7 +88,7 @@ def parse():
     ap.add_argument("--e2e-workers", type=int, default=4, help="server workers for the end-to-end stream")
     ap.add_argument("--e2e-inflight", type=int, default=6, help="host-request steps in flight end to end")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end stream (0: max(30, --steps))")
-    ap.add_argument("--serving-requests", type=int, default=2000)
+    ap.add_argument("--serving-requests", type=int, default=20000)
     return ap.parse_args()
 
 
@@ -133,6 +141,8 @@ def other_workloads(P, torch, dev, stream, peak):
         nl, tms, units = prof[dom]
         bpu = BYTES_PER_UNIT.get(dom)
         ach = units * bpu / (tms / 1e3) / 1e9 if bpu else None
+        kinds = {"no_lcp_64Mi": "no_lcp", "dna_windows_20M": "dna_windows"}
+        kern = {k: {"launches": v[0], "ms": v[1], "units": v[2]} for k, v in prof.items()}
         radix = library_radix_context(P, torch, dev, stream, chars, offsets, n) if name == "no_lcp_64Mi" else None
         cls_cmp = compare_classifiers(P, torch, dev, stream, [dict(chars=chars, offsets=offsets, lengths=None,
                                                                    fixed_len=ss.fixed_len, n=n, perm_out=perm,
@@ -142,7 +152,11 @@ def other_workloads(P, torch, dev, stream, peak):
                      "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
                                              "frac": balg / (ms / 1e3) / 1e9 / peak},
                      "dominant_kernel": {"kernel": dom, "ms": tms, "share": tms / sum(v[1] for v in prof.values()),
-                                         "achieved_gbs": ach, "frac": (ach / peak) if ach else None},
+                                         "launches": nl, "units_per_launch": units / max(nl, 1),
+                                         "bytes_per_unit": bpu, "achieved_gbs": ach,
+                                         "frac": (ach / peak) if ach else None,
+                                         "traffic": dram_traffic(dom, kinds[name], units / max(nl, 1))},
+                     "kernels": kern,
                      "classifiers": cls_cmp}
         if radix:
             out[name]["library_radix_sort_context"] = radix
@@ -328,15 +342,36 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
     return out
 
 
-def serving_vs_plain(P, torch, dev, url_chars, url_offsets, capacity_sps, nreq=2000, load=0.7, seed=5, workers=3):
+def _output_hash(torch, perm, lcp, chunk=1 << 28):
+    """Two 64-bit sums over positions i of the outputs (wrapping int64
+    arithmetic), taken in chunks: equal hashes of two runs stand for equal
+    outputs without holding both on the device."""
+    h1 = torch.zeros((), dtype=torch.int64, device=perm.device)
+    h2 = torch.zeros((), dtype=torch.int64, device=perm.device)
+    n = perm.shape[0]
+    for a in range(0, n, chunk):
+        b = min(n, a + chunk)
+        i = torch.arange(a, b, dtype=torch.int64, device=perm.device)
+        p_ = perm[a:b].to(torch.int64) & 0xFFFFFFFF
+        l_ = lcp[a:b].to(torch.int64) & 0xFFFFFFFF
+        h1 += ((p_ + 1) * (i * 2 + 1) * 0x9E3779B1 + (l_ + 7) * 0x85EBCA77).sum()
+        h2 += ((p_ * 0xC2B2AE3D + 3) * (l_ * 2 + 1) + i * 0x27D4EB2F).sum()
+        del i, p_, l_
+    return (int(h1.item()), int(h2.item()))
+
+
+def serving_vs_plain(P, torch, dev, url_chars, url_offsets, capacity_sps, nreq=20000, loads=(0.7, 0.5, 0.9, 1.1),
+                     seed=5, workers=3):
     """The serving configuration: requests of log-uniform sizes 1,000..4,000,000
     strings (generators random / URL-like / DNA-like by request mod 3) arrive as
-    a Poisson stream whose offered load is `load` times the batched capacity
+    a Poisson stream whose offered load is a multiple of the batched capacity
     measured before (strings/s), plus one no-LCP job of 64 Mi strings in the
     middle.  Served = the continuous-batching server (`workers` streams, 120 GB
-    budget); plain = the same stream through a server with one worker and
-    batches of one request (one request per launch sequence).  Latency =
-    completion - arrival, on the server's clock."""
+    budget), at the first load and at each of the others; plain = the first
+    load's stream through a server with one worker and batches of one request
+    (one request per launch sequence).  Latency = completion - arrival, on the
+    server's clock.  Every run writes the same output arrays; their hashes
+    are compared run against run (outputs_equal)."""
     import threading
     import workloads as W
     rng = np.random.default_rng(seed)
@@ -357,19 +392,22 @@ def serving_vs_plain(P, torch, dev, url_chars, url_offsets, capacity_sps, nreq=2
     starts.insert(mid, 0)
     nall = len(sizes)
     total = int(sizes.sum())
-    rate = load * capacity_sps / float(sizes.mean())   # requests per second
-    gaps = rng.exponential(1.0 / rate, nall)
+    unit_gaps = rng.exponential(1.0, nall)   # one arrival pattern, scaled per offered load
     base = np.concatenate([[0], np.cumsum(sizes)])
+    perm = torch.empty(total, dtype=torch.int32, device=dev)
+    lcp = torch.empty(total, dtype=torch.int32, device=dev)
+    reqs = []
+    for r in range(nall):
+        chars, offs, fixed, _ = src[r]
+        n = int(sizes[r])
+        reqs.append(dict(chars=chars, offsets=offs[starts[r]:starts[r] + n], lengths=None, fixed_len=fixed, n=n,
+                         perm_out=perm[int(base[r]):int(base[r + 1])], lcp_out=lcp[int(base[r]):int(base[r + 1])]))
 
-    def run(workers_, max_batch):
-        perm = torch.empty(total, dtype=torch.int32, device=dev)
-        lcp = torch.empty(total, dtype=torch.int32, device=dev)
-        reqs = []
-        for r in range(nall):
-            chars, offs, fixed, _ = src[r]
-            n = int(sizes[r])
-            reqs.append(dict(chars=chars, offsets=offs[starts[r]:starts[r] + n], lengths=None, fixed_len=fixed, n=n,
-                             perm_out=perm[int(base[r]):int(base[r + 1])], lcp_out=lcp[int(base[r]):int(base[r + 1])]))
+    def run(workers_, max_batch, load):
+        rate = load * capacity_sps / float(sizes.mean())   # requests per second
+        gaps = unit_gaps / rate
+        perm.fill_(-1)
+        lcp.fill_(-1)
         torch.cuda.synchronize(dev)
         tickets = [None] * nall
         with P.Server(120 << 30, workers=workers_, max_batch=max_batch) as srv:
@@ -389,25 +427,33 @@ def serving_vs_plain(P, torch, dev, url_chars, url_offsets, capacity_sps, nreq=2
         tm = np.array([t_ for _, t_ in res])
         lat = tm[:, 2] - tm[:, 0]
         span = float(tm[:, 2].max() - tm[:, 0].min())
-        out = {"makespan_ms": span, "strings_per_s": total / (span / 1e3),
+        torch.cuda.synchronize(dev)
+        out = {"offered_load": load, "arrival_rate_per_s": rate, "makespan_ms": span,
+               "strings_per_s": total / (span / 1e3),
                "latency_p50_ms": float(np.percentile(lat, 50)), "latency_p99_ms": float(np.percentile(lat, 99)),
                "latency_64Mi_job_ms": float(lat[mid]), "errors": int(sum(1 for x in st if x != 0)),
                "batches": int(len(set(tm[:, 1].tolist())))}
-        return out, perm, lcp
+        return out, _output_hash(torch, perm, lcp)
 
-    served, perm_s, lcp_s = run(workers, 0)
-    plain, perm_p, lcp_p = run(1, 1)
-    equal = bool(torch.equal(perm_s, perm_p) and torch.equal(lcp_s, lcp_p))
-    del perm_s, lcp_s, perm_p, lcp_p, pools, big
+    served, h_served = run(workers, 0, loads[0])
+    plain, h_plain = run(1, 1, loads[0])
+    sweep, sweep_equal = [], True
+    for ld in loads[1:]:
+        o, h = run(workers, 0, ld)
+        sweep.append(o)
+        sweep_equal = sweep_equal and h == h_served
+    del perm, lcp, reqs, pools, big
     torch.cuda.empty_cache()
     return {
         "workload": (f"{nreq} requests, sizes log-uniform 1,000..4,000,000 strings, generators random/URL-like/DNA-like "
-                     f"by request mod 3, Poisson arrivals at {load:.1f} x the batched capacity, plus one no-LCP job of "
-                     f"64 Mi strings in the middle; seed {seed}"),
-        "requests": nall, "strings": total, "arrival_rate_per_s": rate, "budget_bytes": 120 << 30,
+                     f"by request mod 3, Poisson arrivals at {loads[0]:.1f} x the batched capacity, plus one no-LCP "
+                     f"job of 64 Mi strings in the middle; seed {seed}"),
+        "requests": nall, "strings": total, "budget_bytes": 120 << 30,
         "served": dict(served, workers=workers, batching="continuous: every idle worker takes all admitted waiting requests"),
         "plain": dict(plain, workers=1, batching="one request per launch sequence, first come first served"),
-        "outputs_equal": equal,
+        "load_sweep": sweep,
+        "outputs_equal": bool(h_served == h_plain and sweep_equal),
+        "outputs_compared": "two 64-bit position-weighted sums of every run's perm and lcp arrays",
     }
 
 
@@ -422,6 +468,25 @@ def aggregate(dist, ms, units, device):
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     dist.all_reduce(u, op=dist.ReduceOp.SUM)
     return float(t.item()), int(round(u.item()))
+
+
+def dram_traffic(kernel, workload_kind, units_per_launch):
+    """DRAM bytes (read + write) per launch of `kernel`: the bytes per unit
+    that one small-case ncu capture of that kernel measured (profiles/traffic.json),
+    times the units of a full launch.  None when the sources changed since the
+    capture, or the capture was taken on another kind of workload."""
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(tp) as f:
+            tj = json.load(f)
+    except Exception:
+        return None
+    if tj.get("source_hash") != _source_hash():
+        return None
+    k = tj.get("kernels", {}).get(kernel)
+    if not k or k.get("workload_kind") != workload_kind:
+        return None
+    return float(k["dram_bytes_per_unit"]) * float(units_per_launch)
 
 
 def load_peaks():
@@ -712,24 +777,18 @@ def main():
     for v in kernels.values():
         v["share"] = v["ms_per_step"] / tot
     dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
-    traffic = None
-    tp = os.path.join(ROOT, "profiles", "traffic.json")
-    if dom and os.path.exists(tp):
-        try:
-            with open(tp) as f:
-                tj = json.load(f)
-            # only for the sources and the workload the counters were taken on
-            if (tj.get("source_hash") == _source_hash() and tj.get("n") == n and tj.get("runs") == K):
-                traffic = tj.get("bytes_per_launch", {}).get(dom)
-        except Exception:
-            traffic = None
     roofline = None
     if dom:
         kd = kernels[dom]
         ach = kd["achieved_gbs"] or 0.0
         roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
-                    "frac": ach / peak, "traffic": traffic, "peak_kind": peak_kind,
-                    "algorithmic_bytes_per_launch": kd["units_per_launch"] * (kd["bytes_per_unit"] or 0)}
+                    "frac": ach / peak, "peak_kind": peak_kind,
+                    "traffic": dram_traffic(dom, "url_like", kd["units_per_launch"]),
+                    "units_per_launch": kd["units_per_launch"], "bytes_per_unit": kd["bytes_per_unit"],
+                    "algorithmic_bytes_per_launch": kd["units_per_launch"] * (kd["bytes_per_unit"] or 0),
+                    "launch_ms": kd["ms_per_step"] * args.steps / max(kd["launches"], 1),
+                    "carried_bytes_per_unit": CARRIED_BYTES_PER_UNIT.get(dom, 0),
+                    "whole_step": {"algorithmic_bytes": balg, "frac": balg / (ms / 1e3) / 1e9 / peak}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": world, "steps": args.steps,
@@ -812,6 +871,18 @@ def main():
         line["classifiers"] = dict(what="the step's 4 runs sorted by one ss_sort_batch_tuned call per classifier",
                                    **compare_classifiers(P, torch, dev, stream, reqs))
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)
+        # the 64 Mi no-LCP job's fractions travel in the roofline object itself
+        nl_ = line["other_workloads"]["no_lcp_64Mi"]
+        if line.get("roofline") is not None:
+            line["roofline"]["no_lcp_64Mi"] = {
+                "ms": nl_["ms"], "strings_per_s": nl_["strings_per_s"],
+                "whole_sort": {"algorithmic_bytes": nl_["whole_sort_roofline"]["algorithmic_bytes"],
+                               "achieved": nl_["whole_sort_roofline"]["achieved_gbs"],
+                               "frac": nl_["whole_sort_roofline"]["frac"]},
+                "kernel": nl_["dominant_kernel"]["kernel"], "achieved": nl_["dominant_kernel"]["achieved_gbs"],
+                "frac": nl_["dominant_kernel"]["frac"], "traffic": nl_["dominant_kernel"]["traffic"],
+                "bytes_per_unit": nl_["dominant_kernel"]["bytes_per_unit"],
+                "units_per_launch": nl_["dominant_kernel"]["units_per_launch"]}
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_vs_plain(P, torch, dev, stream, nreq=args.batched_requests)
         if not args.no_serving:

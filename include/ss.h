@@ -224,9 +224,10 @@ int ss_merge(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32
  *   library until the process exits.  Every call on a device shares that
  *   array: calls that overlap on the GPU (unordered streams or threads)
  *   race and give wrong results, so order them on one stream.
- *   Set-up: the first call on each device looks up the array's device
- *   address (with that device current); make that first call before any
- *   stream capture.
+ *   Set-up: every call looks up the array's device address with the
+ *   current device (a lookup, no allocation); the first call on a device
+ *   may load the library's module there, so make that first call before
+ *   any stream capture.
  *   Completion: the call only queues work on `stream` and returns; results
  *   are complete when the stream reaches that point.
  */

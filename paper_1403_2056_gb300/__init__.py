@@ -138,7 +138,14 @@ def _ptr(t):
     return t.data_ptr()
 
 
-def _dev(t, dtype_name, what):
+def _need(t, min_len, what):
+    """A device tensor must hold at least min_len elements: the kernels index
+    it up to min_len - 1 and nothing on the device checks the bound."""
+    if min_len is not None and t.numel() < min_len:
+        raise ValueError(f"{what} holds {t.numel()} elements, needs {min_len}")
+
+
+def _dev(t, dtype_name, what, min_len=None):
     if t is None:
         return None
     if isinstance(t, int):
@@ -147,6 +154,7 @@ def _dev(t, dtype_name, what):
         raise ValueError(f"{what} must be a CUDA tensor")
     if str(t.dtype) != f"torch.{dtype_name}":
         raise TypeError(f"{what} must be torch.{dtype_name}, got {t.dtype}")
+    _need(t, min_len, what)
     return _ptr(t)
 
 
@@ -160,23 +168,29 @@ def _stream(stream):
 
 
 def ss_sort(chars, offsets, n, perm_out, lcp_out, stream=None):
-    _check(lib().ss_sort(_dev(chars, "uint8", "chars"), _off(offsets), int(n), _dev(perm_out, "int32", "perm_out"),
-                         _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+    n = int(n)
+    _check(lib().ss_sort(_dev(chars, "uint8", "chars"), _off(offsets, "offsets", n), n,
+                         _dev(perm_out, "int32", "perm_out", n), _dev(lcp_out, "int32", "lcp_out", n),
+                         _stream(stream)))
 
 
 def ss_sort_ex(chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, stream=None):
-    _check(lib().ss_sort_ex(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
-                            int(fixed_len), int(n), _dev(perm_out, "int32", "perm_out"),
-                            _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+    n = int(n)
+    _check(lib().ss_sort_ex(_dev(chars, "uint8", "chars"), _off(offsets, "offsets", n),
+                            _dev(lengths, "int32", "lengths", n), int(fixed_len), n,
+                            _dev(perm_out, "int32", "perm_out", n), _dev(lcp_out, "int32", "lcp_out", n),
+                            _stream(stream)))
 
 
-def _off(offsets):
+def _off(offsets, what="offsets", min_len=None):
+    """A 64-bit device tensor (offsets, keys, splitters)."""
     if offsets is None or isinstance(offsets, int):
         return offsets
     if str(offsets.dtype) not in ("torch.int64", "torch.uint64"):
-        raise TypeError("offsets must be a 64-bit integer tensor")
+        raise TypeError(f"{what} must be a 64-bit integer tensor")
     if not offsets.is_cuda:
-        raise ValueError("offsets must be a CUDA tensor")
+        raise ValueError(f"{what} must be a CUDA tensor")
+    _need(offsets, min_len, what)
     return _ptr(offsets)
 
 
@@ -223,18 +237,16 @@ def ss_sort_batch(requests, stream=None):
     """requests: list of dicts with keys chars, offsets, lengths, fixed_len, n, perm_out, lcp_out, status_out."""
     arr = (Request * max(1, len(requests)))()
     for k, q in enumerate(requests):
-        arr[k] = Request(_dev(q["chars"], "uint8", "chars"), _off(q["offsets"]),
-                         _dev(q.get("lengths"), "int32", "lengths"), int(q.get("fixed_len", 0)), int(q["n"]),
-                         _dev(q["perm_out"], "int32", "perm_out"), _dev(q["lcp_out"], "int32", "lcp_out"),
-                         _dev(q.get("status_out"), "int32", "status_out"))
+        arr[k] = _request(q)
     _check(lib().ss_sort_batch(C.cast(arr, C.c_void_p), len(requests), _stream(stream)))
 
 
 def _request(q):
-    return Request(_dev(q["chars"], "uint8", "chars"), _off(q["offsets"]),
-                   _dev(q.get("lengths"), "int32", "lengths"), int(q.get("fixed_len", 0)), int(q["n"]),
-                   _dev(q["perm_out"], "int32", "perm_out"), _dev(q["lcp_out"], "int32", "lcp_out"),
-                   _dev(q.get("status_out"), "int32", "status_out"))
+    n = int(q["n"])
+    return Request(_dev(q["chars"], "uint8", "chars"), _off(q["offsets"], "offsets", n),
+                   _dev(q.get("lengths"), "int32", "lengths", n), int(q.get("fixed_len", 0)), n,
+                   _dev(q["perm_out"], "int32", "perm_out", n), _dev(q["lcp_out"], "int32", "lcp_out", n),
+                   _dev(q.get("status_out"), "int32", "status_out", 1))
 
 
 def ss_sort_batch_tuned(requests, tunings=None, stream=None):
@@ -353,52 +365,83 @@ class Server:
         self.close()
 
 
+def _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out, run_base):
+    """Marshals the arguments of ss_merge / ss_merge_noalloc.  Every device
+    buffer must hold what the runs index: run_perm, run_lcp, perm_out and
+    lcp_out run_begin[K] entries, offsets (and lengths) one per string index
+    the runs name (run_base[k] + run k's length, or run_begin[K] without
+    bases); run_base has K entries."""
+    rb = np.ascontiguousarray(np.asarray(run_begin, dtype=np.uint32))
+    if rb.ndim != 1 or rb.shape[0] < 1:
+        raise ValueError("run_begin must list K + 1 run starts")
+    K = rb.shape[0] - 1
+    if np.any(rb[1:] < rb[:-1]):
+        raise ValueError("run_begin must be non-decreasing")
+    total = int(rb[-1]) if K else 0
+    base = None
+    strings = total
+    if run_base is not None:
+        base = np.ascontiguousarray(np.asarray(run_base, dtype=np.uint32))
+        if base.ndim != 1 or base.shape[0] < K:
+            raise ValueError(f"run_base holds {base.size} entries, needs {K}")
+        sizes = rb[1:].astype(np.int64) - rb[:-1].astype(np.int64)
+        strings = int((base[:K].astype(np.int64) + sizes).max()) if K else 0
+    args = (_dev(chars, "uint8", "chars"), _off(offsets, "offsets", strings),
+            _dev(lengths, "int32", "lengths", strings), int(fixed_len),
+            _dev(run_perm, "int32", "run_perm", total), _dev(run_lcp, "int32", "run_lcp", total),
+            rb.ctypes.data, None if base is None else base.ctypes.data, K,
+            _dev(perm_out, "int32", "perm_out", total), _dev(lcp_out, "int32", "lcp_out", total))
+    return args, (rb, base)
+
+
 def ss_merge(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
              run_base=None, stream=None):
-    rb = np.ascontiguousarray(np.asarray(run_begin, dtype=np.uint32))
-    K = rb.shape[0] - 1
-    base = None if run_base is None else np.ascontiguousarray(np.asarray(run_base, dtype=np.uint32))
-    _check(lib().ss_merge(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
-                          int(fixed_len), _dev(run_perm, "int32", "run_perm"), _dev(run_lcp, "int32", "run_lcp"),
-                          rb.ctypes.data, None if base is None else base.ctypes.data, K,
-                          _dev(perm_out, "int32", "perm_out"), _dev(lcp_out, "int32", "lcp_out"), _stream(stream)))
+    args, keep = _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+                             run_base)
+    _check(lib().ss_merge(*args, _stream(stream)))
+    del keep
 
 
 def ss_merge_noalloc(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
                      run_base=None, stream=None):
     """ss_merge without allocation (fixed 8 MiB device array; <= 1,048,576 strings, <= 64 runs).
     Only queues work on the stream: synchronize before reading the outputs."""
-    rb = np.ascontiguousarray(np.asarray(run_begin, dtype=np.uint32))
-    K = rb.shape[0] - 1
-    base = None if run_base is None else np.ascontiguousarray(np.asarray(run_base, dtype=np.uint32))
-    _check(lib().ss_merge_noalloc(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
-                                  int(fixed_len), _dev(run_perm, "int32", "run_perm"), _dev(run_lcp, "int32", "run_lcp"),
-                                  rb.ctypes.data, None if base is None else base.ctypes.data, K,
-                                  _dev(perm_out, "int32", "perm_out"), _dev(lcp_out, "int32", "lcp_out"),
-                                  _stream(stream)))
+    args, keep = _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+                             run_base)
+    _check(lib().ss_merge_noalloc(*args, _stream(stream)))
+    del keep
 
 
 def ss_gather_keys(chars, offsets, lengths, fixed_len, n, depth, keys_out, stream=None):
-    _check(lib().ss_gather_keys(_dev(chars, "uint8", "chars"), _off(offsets), _dev(lengths, "int32", "lengths"),
-                                int(fixed_len), int(n), _dev(depth, "int32", "depth"), _off(keys_out),
-                                _stream(stream)))
+    n = int(n)
+    _check(lib().ss_gather_keys(_dev(chars, "uint8", "chars"), _off(offsets, "offsets", n),
+                                _dev(lengths, "int32", "lengths", n), int(fixed_len), n,
+                                _dev(depth, "int32", "depth", n), _off(keys_out, "keys_out", n), _stream(stream)))
 
 
 def ss_splitters(sample, a, d, x_out, stream=None):
-    _check(lib().ss_splitters(_off(sample), int(a), int(d), _off(x_out), _stream(stream)))
+    a, d = int(a), int(d)
+    v = (1 << d) - 1 if 0 <= d < 32 else None
+    _check(lib().ss_splitters(_off(sample, "sample", a), a, d, _off(x_out, "x_out", v), _stream(stream)))
+
+
+def _classify_args(keys, n, x, d, bucket_out, bucket_begin_out, order_out):
+    n, d = int(n), int(d)
+    v = (1 << d) - 1 if 0 <= d < 32 else None
+    return (_off(keys, "keys", n), n, _off(x, "x", v), d), (
+        _dev(bucket_out, "int16", "bucket_out", n),
+        _dev(bucket_begin_out, "int32", "bucket_begin_out", None if v is None else 2 * v + 2),
+        _dev(order_out, "int32", "order_out", n))
 
 
 def ss_classify(keys, n, x, d, bucket_out, bucket_begin_out, order_out, stream=None):
-    _check(lib().ss_classify(_off(keys), int(n), _off(x), int(d), _dev(bucket_out, "int16", "bucket_out"),
-                             _dev(bucket_begin_out, "int32", "bucket_begin_out"),
-                             _dev(order_out, "int32", "order_out"), _stream(stream)))
+    head, outs = _classify_args(keys, n, x, d, bucket_out, bucket_begin_out, order_out)
+    _check(lib().ss_classify(*head, *outs, _stream(stream)))
 
 
 def ss_classify_ex(keys, n, x, d, classifier, bucket_out, bucket_begin_out, order_out, stream=None):
-    _check(lib().ss_classify_ex(_off(keys), int(n), _off(x), int(d), int(classifier),
-                                _dev(bucket_out, "int16", "bucket_out"),
-                                _dev(bucket_begin_out, "int32", "bucket_begin_out"),
-                                _dev(order_out, "int32", "order_out"), _stream(stream)))
+    head, outs = _classify_args(keys, n, x, d, bucket_out, bucket_begin_out, order_out)
+    _check(lib().ss_classify_ex(*head, int(classifier), *outs, _stream(stream)))
 
 
 def profile_enable(on: bool = True):

@@ -766,24 +766,18 @@ __global__ void k_store_run_table(RunTable t, uint32_t R, uint32_t *dst) {
     for (uint32_t k = threadIdx.x; k < R; k += blockDim.x) dst[kNoAllocMaxRuns + 1 + k] = t.base[k];
 }
 
-// device address of g_noalloc_scratch, looked up once per device with that
-// device current (in host code the symbol name is only a host-side stand-in)
-static std::mutex g_noalloc_mu;
-static void *g_noalloc_ptr[128];
-
+// Device address of g_noalloc_scratch on the current device.  In host code the
+// symbol name is only a host-side stand-in, so the address is asked for with
+// the device current, on every call: the lookup allocates nothing, and an
+// address cached across calls could go stale after cudaDeviceReset or a
+// re-created primary context (the module is loaded again, possibly elsewhere).
+// The first call on a device may load the library's module there, so that
+// first call should come before any stream capture.
 static cudaError_t noalloc_setup(uint32_t **out) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
     if (e != cudaSuccess) return e;
-    if (dev < 0 || dev >= 128) return cudaErrorInvalidDevice;
-    std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
-        void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_noalloc_ptr[dev] = p;
-    }
-    *out = (uint32_t *)g_noalloc_ptr[dev];
+    *out = (uint32_t *)p;
     return cudaSuccess;
 }
 

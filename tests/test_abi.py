@@ -119,3 +119,26 @@ def test_host_buffer_arguments_checked_before_any_device_work():
         args.update(change)
         with pytest.raises(exc):
             P.ss_sort_host(**args)
+
+
+def test_merge_run_tables_checked_in_the_binding():
+    """ss_merge's host run tables are checked before any device buffer is
+    looked at: K + 1 non-decreasing run starts and K index bases."""
+    import paper_1403_2056_gb300 as P
+    with pytest.raises(ValueError):
+        P.ss_merge(1, 1, None, 0, 1, 1, [0, 5, 3], 1, 1)
+    with pytest.raises(ValueError):
+        P.ss_merge(1, 1, None, 0, 1, 1, [0, 2, 4], 1, 1, run_base=[0])
+    with pytest.raises(ValueError):
+        P.ss_merge_noalloc(1, 1, None, 0, 1, 1, [], 1, 1)
+
+
+def test_device_buffer_length_rule():
+    """The binding's length rule for device tensors (checked on CPU tensors
+    here; the GPU test calls the entry points with CUDA tensors)."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    P._need(torch.zeros(4), 4, "x")
+    P._need(torch.zeros(4), None, "x")
+    with pytest.raises(ValueError):
+        P._need(torch.zeros(3), 4, "x")

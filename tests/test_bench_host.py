@@ -40,3 +40,32 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["unit"] == "strings/s" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+def test_scatter_bytes_follow_the_step_layout():
+    """The scatter's algorithmic bytes are the redistribution's own: a u16
+    bucket id read, a u32 index and a u64 key read and written (26 bytes per
+    string); the offsets this implementation carries beside them are
+    reported apart, never inside the roofline's bytes."""
+    assert bench.BYTES_PER_UNIT["scatter"] == 26
+    assert bench.CARRIED_BYTES_PER_UNIT["scatter"] == 16
+    assert bench.BYTES_PER_UNIT["classify"] == 10
+    assert bench.BYTES_PER_UNIT["merge_round"] == 16
+
+
+def test_dram_traffic_needs_matching_sources_and_workload(tmp_path, monkeypatch):
+    """roofline.traffic scales a small-case capture's bytes per unit to a full
+    launch only while the sources hash to the capture's and the workload kind
+    matches; otherwise it is null."""
+    prof = tmp_path / "profiles"
+    prof.mkdir()
+    tj = {"source_hash": bench._source_hash(),
+          "kernels": {"scatter": {"workload_kind": "url_like", "dram_bytes_per_unit": 50.0}}}
+    (prof / "traffic.json").write_text(json.dumps(tj))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    monkeypatch.setattr(bench, "_source_hash", lambda: tj["source_hash"])
+    assert bench.dram_traffic("scatter", "url_like", 1000) == 50000.0
+    assert bench.dram_traffic("scatter", "no_lcp", 1000) is None
+    assert bench.dram_traffic("classify", "url_like", 1000) is None
+    monkeypatch.setattr(bench, "_source_hash", lambda: "other")
+    assert bench.dram_traffic("scatter", "url_like", 1000) is None

@@ -126,3 +126,39 @@ def test_server_cancel_withdraws_queued_requests():
         else:
             assert results[k] == 0
             assert _same(ss, q["perm_out"], q["lcp_out"])
+
+
+def test_undersized_device_buffers_refused_by_the_binding():
+    """A device tensor shorter than what the call indexes is refused in the
+    binding (ValueError) before the library runs any kernel on it; the
+    library keeps working afterwards."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = W.random_lower(5_000, seed=67)
+    chars, offsets, _ = to_device(ss)
+    n = ss.n
+    perm, lcp = _outs(torch, n)
+    short = torch.zeros(n - 1, dtype=torch.int32, device="cuda:0")
+    with pytest.raises(ValueError):
+        P.ss_sort(chars, offsets, n, short, lcp)
+    with pytest.raises(ValueError):
+        P.ss_sort(chars, offsets, n, perm, short)
+    with pytest.raises(ValueError):
+        P.ss_sort(chars, offsets[: n - 1], n, perm, lcp)
+    with pytest.raises(ValueError):
+        P.ss_sort_batch([dict(chars=chars, offsets=offsets, n=n, perm_out=short, lcp_out=lcp)])
+    depth = torch.zeros(n, dtype=torch.int32, device="cuda:0")
+    keys = torch.zeros(n - 1, dtype=torch.int64, device="cuda:0")
+    with pytest.raises(ValueError):
+        P.ss_gather_keys(chars, offsets, None, 0, n, depth, keys)
+    # merge: runs index up to run_begin[K]; offsets must cover run_base[k] + run length
+    rb = [0, n // 2, n]
+    with pytest.raises(ValueError):
+        P.ss_merge(chars, offsets, None, 0, perm, lcp, rb, short, lcp, run_base=[0, n // 2])
+    with pytest.raises(ValueError):
+        P.ss_merge(chars, offsets, None, 0, perm, lcp, rb, perm, lcp, run_base=[0, n])
+    with pytest.raises(ValueError):
+        P.ss_merge(chars, offsets, None, 0, perm, lcp, rb, perm, lcp, run_base=[0])
+    P.ss_sort(chars, offsets, n, perm, lcp)
+    torch.cuda.synchronize()
+    assert _same(ss, perm, lcp)

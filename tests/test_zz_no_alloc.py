@@ -1,8 +1,14 @@
 """ss_merge_noalloc: the merge for callers that cannot allocate (a process
 whose device memory is owned by its own arena, a hard memory budget, or a
 latency-critical path that must not call cudaMalloc/cudaFree).  Its output
-must equal ss_merge's, bit for bit, on consecutive calls that share the
-library's fixed scratch array.  Kept in a file collected last."""
+must equal ss_merge's and the oracle's, bit for bit, on consecutive calls
+that share the library's fixed scratch array.
+
+The file name sorts last so that pytest collects it after every other test
+file: it is a deployment variant outside the paper's method, and a run that
+stops at its first failure (-x) has then already run all the other tests.
+Nothing in it depends on what earlier tests left behind; it also passes run
+alone in a fresh process."""
 import numpy as np
 import pytest
 
@@ -45,13 +51,16 @@ def _merge_both(ss, K, seed):
 
 
 def test_noalloc_merge_equals_merge_on_two_calls_in_a_row():
+    import oracle
     # first call: 5 runs (3 rounds through the fixed array); second: 3 runs of another set
     cases = [(W.url_like(300_000, seed=31), 5, 1), (W.dna_windows(200_000, 500_000, 100, seed=32), 3, 2)]
     for ss, K, seed in cases:
         ref_p, ref_l, out_p, out_l = _merge_both(ss, K, seed)
         assert np.array_equal(out_p, ref_p), ss.name
         assert np.array_equal(out_l, ref_l), ss.name
-        assert sorted(out_p.tolist()) == list(range(ss.n))
+        want_p, want_l = oracle.sort(ss)
+        assert np.array_equal(out_p.view(np.uint32), want_p), ss.name
+        assert np.array_equal(out_l.view(np.uint32), want_l), ss.name
 
 
 def test_noalloc_merge_rejects_beyond_limit():
@@ -59,10 +68,13 @@ def test_noalloc_merge_rejects_beyond_limit():
     import paper_1403_2056_gb300 as P
     ss = W.from_bytes_list([b"a", b"b"])
     chars, offsets, lengths = to_device(ss)
+    # raw addresses: the binding cannot check their sizes, so the library's own
+    # limit check is what refuses these (before any device work)
     buf = torch.zeros(2, dtype=torch.int32, device="cuda:0")
+    b = buf.data_ptr()
     with pytest.raises(P.SortError) as ei:
-        P.ss_merge_noalloc(chars, offsets, None, 0, buf, buf, [0, 1, (1 << 20) + 1], buf, buf)
+        P.ss_merge_noalloc(chars, offsets.data_ptr(), None, 0, b, b, [0, 1, (1 << 20) + 1], b, b)
     assert ei.value.status == -5 and "limit" in ei.value.detail
     with pytest.raises(P.SortError) as ei:
-        P.ss_merge_noalloc(chars, offsets, None, 0, buf, buf, list(range(66)), buf, buf)
+        P.ss_merge_noalloc(chars, offsets.data_ptr(), None, 0, b, b, list(range(66)), b, b)
     assert ei.value.status == -5
