@@ -269,23 +269,128 @@ struct BaseSmem {
     uint16_t GS[CAP];        // size of the group that starts at a position
     uint16_t ACT[CAP];       // positions still being sorted, in order
     uint32_t WL[CAP / 2];    // groups of 2..32 strings for the warps: start << 16 | size
+    uint64_t wlast[NT / 32]; // last key of each warp's slots (first round's neighbour test)
     uint32_t wsum[NT / 32];
     uint32_t nwl, nws, wbase;   // small groups, their strings, first reserved list slot
+    uint32_t task, next;     // task taken from the queue, and the one after it
 };
+
+// First round by one counting pass (the adaptivity of Section 8.1: when a few
+// key bits already spread a segment, distribute by them as radix sort does).
+// All keys of the segment share their leading cp bits (cp = clz of the OR of
+// every key xor the first); the next B bits (2^B >= m digit values) are a
+// digit that is monotone in the key.  One shared-memory histogram, scan and
+// placement put the segment in digit order; each digit's strings (at most
+// kRadixBucketMax, otherwise the merge sort below is used instead) are then
+// put in (key, original index) order by insertion sort.  kin holds the keys
+// of this thread's slots tid + r NT (SK holds all of them by position).  On
+// success SK / SP hold the segment sorted by (key, original index) by
+// position and true is returned; false leaves SK untouched and SP unset (all
+// keys equal, or a digit too full).  Every thread of the CTA calls this.
+constexpr uint32_t kRadixBucketMax = 8;
+
+template <int NT, int ITEMS>
+__device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32_t m, const uint64_t (&kin)[ITEMS]) {
+    constexpr int NW = NT / 32;
+    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t k0 = S.SK[0];
+    uint64_t k[ITEMS];
+    uint64_t x = 0;
+#pragma unroll
+    for (int r = 0; r < ITEMS; r++) {
+        const uint32_t i = tid + r * NT;
+        k[r] = i < m ? kin[r] : k0;
+        x |= k[r] ^ k0;
+    }
+    const uint32_t xl = __reduce_or_sync(0xffffffffu, (uint32_t)x);
+    const uint32_t xh = __reduce_or_sync(0xffffffffu, (uint32_t)(x >> 32));
+    if (lane == 0) S.wlast[warp] = ((uint64_t)xh << 32) | xl;
+    __syncthreads();
+    x = 0;
+#pragma unroll
+    for (int w = 0; w < NW; w++) x |= S.wlast[w];
+    if (x == 0) return false;   // every key equal: nothing to distribute
+    const uint32_t cp = (uint32_t)__clzll((long long)x);
+    uint32_t B = 1;
+    while ((1u << B) < m) B++;
+    const uint32_t nb = 1u << B;   // <= NT * ITEMS
+    // the digit spreads the keys only if (nearly) all of its bits vary among
+    // them (characters of a small alphabet leave some bits of every byte
+    // fixed): otherwise the merge sort is used without trying
+    if ((uint32_t)__popcll((x << cp) >> (64 - B)) + 1 < B) return false;
+    uint32_t *C = S.MG;
+    for (uint32_t b = tid; b < nb; b += NT) C[b] = 0;
+    __syncthreads();
+    uint32_t d[ITEMS], rk[ITEMS];
+#pragma unroll
+    for (int r = 0; r < ITEMS; r++) {
+        const uint32_t i = tid + r * NT;
+        d[r] = (uint32_t)((k[r] << cp) >> (64 - B));
+        rk[r] = i < m ? atomicAdd(&C[d[r]], 1u) : 0u;
+    }
+    __syncthreads();
+    bool full = false;
+    for (uint32_t b = tid; b < nb; b += NT) full = full || C[b] > kRadixBucketMax;
+    if (__syncthreads_or(full)) return false;
+    block_scan<NT, ITEMS, false>(C, nb, S.wsum);
+#pragma unroll
+    for (int r = 0; r < ITEMS; r++) {
+        const uint32_t i = tid + r * NT;
+        if (i < m) {
+            const uint32_t pos = C[d[r]] + rk[r];
+            S.SK[pos] = k[r];
+            S.SP[pos] = (uint16_t)i;
+        }
+    }
+    __syncthreads();
+    for (uint32_t b = tid; b < nb; b += NT) {
+        const uint32_t st = C[b], en = b + 1 < nb ? C[b + 1] : m;
+        for (uint32_t a = st + 1; a < en; a++) {
+            const uint64_t kk = S.SK[a];
+            const uint16_t pp = S.SP[a];
+            uint32_t z = a;
+            while (z > st && (S.SK[z - 1] > kk || (S.SK[z - 1] == kk && S.SP[z - 1] > pp))) {
+                S.SK[z] = S.SK[z - 1];
+                S.SP[z] = S.SP[z - 1];
+                z--;
+            }
+            S.SK[z] = kk;
+            S.SP[z] = pp;
+        }
+    }
+    __syncthreads();
+    return true;
+}
 
 // Small groups are handed to the warp kernel through the other parity's
 // buffers: base cases run after the last level, so those positions of the
 // task are free, and no other task reads them.
+//
+// Tasks come from a device work queue: each CTA takes the next task of its
+// class list with one atomic on the queue head (`next_task`), so the grid is
+// sized to the CTAs that fit on the device at once and segments of uneven
+// size balance themselves.  The task count is read on the device.
+//
+// First round: the segment is sorted by its keys at the task's depth.  When
+// every pair of neighbours is then decided (different keys, or equal keys
+// that hold the end of the string), the sorted keys still in registers give
+// every LCP and the task ends there; only segments with equal keys that
+// continue past these 8 characters go through the group rounds below.
 template <int NT, int ITEMS>
-__global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_t ntask, const ReqDesc *reqs,
-                                                 ElemBufs eb, SmallTask *tiny, uint32_t tiny_cap,
+__global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const uint32_t *ntask_dev, uint32_t *next_task,
+                                                 const ReqDesc *reqs, ElemBufs eb, SmallTask *tiny, uint32_t tiny_cap,
                                                  uint32_t *counters) {
     constexpr uint32_t CAP = NT * ITEMS;
     constexpr int NW = NT / 32;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BaseSmem<NT, ITEMS> &S = *reinterpret_cast<BaseSmem<NT, ITEMS> *>(smem_raw);
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (uint32_t tk = blockIdx.x; tk < ntask; tk += gridDim.x) {
+    const uint32_t ntask = *ntask_dev;
+    if (tid == 0) S.task = atomicAdd(next_task, 1u);
+    __syncthreads();
+    for (;;) {
+        const uint32_t tk = S.task;
+        if (tk >= ntask) break;
         const SmallTask t = tasks[tk];
         const uint32_t *idx = eb.idx[t.parity];
         const uint64_t *soff = eb.soff[t.parity];
@@ -295,18 +400,56 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
         const ReqDesc &R = reqs[t.req];
         const uint32_t m = t.size <= CAP ? t.size : CAP;
         const uint32_t lbase = t.begin - R.base;
-        for (uint32_t i = tid; i < m; i += NT) {
-            S.SI[i] = idx[t.begin + i];
-            S.SK[i] = key[t.begin + i];
-            S.SP[i] = (uint16_t)i;
-            S.SG[i] = 0;
-            S.ACT[i] = (uint16_t)i;
+        // every load of the segment in flight at once (striped: slot tid + r NT)
+        uint64_t kk[ITEMS];
+        uint32_t ii[ITEMS];
+#pragma unroll
+        for (int r = 0; r < ITEMS; r++) {
+            const uint32_t i = tid + r * NT;
+            kk[r] = i < m ? key[t.begin + i] : 0ull;
+            ii[r] = i < m ? idx[t.begin + i] : 0u;
         }
-        if (tid == 0) { S.GS[0] = (uint16_t)min(m, 0xFFFFu); S.nwl = 0; S.nws = 0; }
+        // the next task is fetched while this one runs
+        if (tid == 0) S.next = atomicAdd(next_task, 1u);
+#pragma unroll
+        for (int r = 0; r < ITEMS; r++) {
+            const uint32_t i = tid + r * NT;
+            if (i < m) { S.SI[i] = ii[r]; S.SK[i] = kk[r]; }
+        }
+        if (tid == 0) { S.nwl = 0; S.nws = 0; }
         uint32_t M = m, depth = t.depth;
+        bool finished = false;   // the first round decided every neighbour pair
         __syncthreads();
-        while (M > 0) {
+        bool presorted = radix_first_round<NT, ITEMS>(S, m, kk);
+        if (presorted) {
+            bool open = false;   // some neighbours share all 8 characters and continue
+            for (uint32_t s = tid + 1; s < m; s += NT) {
+                const uint64_t a = S.SK[s - 1], b = S.SK[s];
+                open = open || (a == b && !has_zero(b));
+            }
+            if (!__syncthreads_or(open)) {
+                for (uint32_t s = tid; s < m; s += NT) {
+                    R.perm_out[lbase + s] = S.SI[S.SP[s]];
+                    if (s > 0) {
+                        const uint64_t a = S.SK[s - 1], b = S.SK[s];
+                        R.lcp_out[lbase + s] = a != b ? depth + lcp8(a, b) : depth + nulpos(b);
+                    }
+                }
+                finished = true;
+            }
+        }
+        if (!finished) {   // state of the group rounds: one group, positions in order
+            for (uint32_t i = tid; i < m; i += NT) {
+                if (!presorted) S.SP[i] = (uint16_t)i;
+                S.SG[i] = 0;
+                S.ACT[i] = (uint16_t)i;
+            }
+            if (tid == 0) S.GS[0] = (uint16_t)min(m, 0xFFFFu);
+            __syncthreads();
+        }
+        while (!finished && M > 0) {
             const uint16_t *act = S.ACT;
+            if (!presorted) {
             // load the active slots, sort them by (group, key, original index)
             uint64_t k[ITEMS];
             uint32_t g[ITEMS];
@@ -350,6 +493,41 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
                 }
             }
             __syncthreads();
+            if (depth == t.depth) {
+                // one group in original-index order: slot s holds position s, and
+                // (sorted or all equal) the registers hold the keys in position order
+                if (lane == 31) S.wlast[warp] = k[ITEMS - 1];
+                __syncthreads();
+                uint64_t prev = __shfl_up_sync(0xffffffffu, k[ITEMS - 1], 1);
+                if (lane == 0) prev = warp ? S.wlast[warp - 1] : 0ull;
+                uint32_t lc[ITEMS];
+                bool open = false;   // some neighbours share all 8 characters and continue
+#pragma unroll
+                for (int j = 0; j < ITEMS; j++) {
+                    const uint32_t s = tid * ITEMS + j;
+                    const uint64_t a = j ? k[j - 1] : prev, b = k[j];
+                    lc[j] = 0;
+                    if (s > 0 && s < M) {
+                        if (a != b) lc[j] = depth + lcp8(a, b);
+                        else if (has_zero(b)) lc[j] = depth + nulpos(b);
+                        else open = true;
+                    }
+                }
+                if (!__syncthreads_or(open)) {
+#pragma unroll
+                    for (int j = 0; j < ITEMS; j++) {
+                        const uint32_t s = tid * ITEMS + j;
+                        if (s < M) {
+                            R.perm_out[lbase + s] = S.SI[g[j] & 0xFFFu];
+                            if (s > 0) R.lcp_out[lbase + s] = lc[j];
+                        }
+                    }
+                    finished = true;
+                    break;
+                }
+            }
+            }   // !presorted
+            presorted = false;
             // split groups: LCPs at new boundaries, new group starts (as positions, max-scanned)
             for (uint32_t s = tid; s < M; s += NT) {
                 uint32_t pos = act[s];
@@ -439,8 +617,11 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, uint32_
             __syncthreads();
         }
         // positions that ended as groups of one
-        for (uint32_t i = tid; i < m; i += NT)
-            if (S.GS[S.SG[i]] == 1) R.perm_out[lbase + i] = S.SI[S.SP[i]];
+        if (!finished)
+            for (uint32_t i = tid; i < m; i += NT)
+                if (S.GS[S.SG[i]] == 1) R.perm_out[lbase + i] = S.SI[S.SP[i]];
+        __syncthreads();
+        if (tid == 0) S.task = S.next;
         __syncthreads();
     }
 }

@@ -1066,7 +1066,7 @@ static int sm_count() {
 #define SS_C1_NT 64     // threads of the CTA base case for 33..256 strings
 #endif
 #ifndef SS_C2_NT
-#define SS_C2_NT 256    // .. for 257..1024 strings
+#define SS_C2_NT 128    // .. for 257..1024 strings
 #endif
 #ifndef SS_C3_NT
 #define SS_C3_NT 256    // .. for 1025..kSmallMax strings
@@ -1089,10 +1089,34 @@ AuxStreams &aux_streams() {
 
 static std::atomic<bool> g_attrs_done[64];
 static std::mutex g_attrs_mu;
+// CTAs of each base-case class that are resident on the device at once
+// (occupancy of its kernel times the SMs), set with the attributes
+static uint32_t g_base_grid[kClasses];
+
+template <typename K>
+static uint32_t resident_grid(K kernel, int threads, size_t smem) {
+    int per_sm = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return (uint32_t)per_sm * (uint32_t)(sms > 0 ? sms : 1);
+}
 
 template <typename K>
 static cudaError_t set_smem(K kernel, size_t bytes) {
     return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// kernels whose residency is limited by shared memory: the largest carveout
+template <typename K>
+static cudaError_t set_smem_max(K kernel, size_t bytes) {
+    cudaError_t e = set_smem(kernel, bytes);
+    if (e) return e;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
 }
 
 static cudaError_t ensure_attrs() {
@@ -1106,9 +1130,13 @@ static cudaError_t ensure_attrs() {
     if ((e = set_smem(k_classify, sizeof(ClassifySmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_SORT>, sizeof(ScatterSmem)))) return e;
     if ((e = set_smem(k_scatter<MODE_CLASSIFY>, sizeof(ScatterSmem)))) return e;
-    if ((e = set_smem(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>)))) return e;
-    if ((e = set_smem(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>)))) return e;
-    if ((e = set_smem(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>)))) return e;
+    if ((e = set_smem_max(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>)))) return e;
+    if ((e = set_smem_max(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>)))) return e;
+    if ((e = set_smem_max(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>)))) return e;
+    g_base_grid[1] = resident_grid(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, SS_C1_NT, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>));
+    g_base_grid[2] = resident_grid(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, SS_C2_NT, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>));
+    g_base_grid[3] = resident_grid(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, SS_C3_NT,
+                                   sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>));
     if (dev < 64) g_attrs_done[dev] = true;
     return cudaSuccess;
 }
@@ -1375,23 +1403,25 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             TRY(cudaStreamWaitEvent(s1, ax.ev[0], 0), "fork");
             TRY(cudaStreamWaitEvent(s2, ax.ev[0], 0), "fork");
         }
+        // grids of the CTAs that fit on the device at once; each CTA takes its
+        // tasks from the class's work queue (head in the counters)
         if (uint32_t n3 = hc[C_NTASK + 3]) {
             constexpr int NT = SS_C3_NT, IT = (int)(kSmallMax / SS_C3_NT);
-            uint32_t grid = std::min<uint32_t>(n3, sms * (uint32_t)(4096 / kSmallMax) * 2);   // CTAs that fit in shared memory
+            uint32_t grid = std::min<uint32_t>(n3, g_base_grid[3]);
             SS_LAUNCH_U("base_c3", st, hc[C_ETASK + 3], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), st>>>(
-                L[3], n3, dreqs, eb, L[0], tl.cap[0], counters)));
+                L[3], counters + C_NTASK + 3, counters + C_QHEAD + 3, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (uint32_t n2 = hc[C_NTASK + 2]) {
             constexpr int NT = SS_C2_NT, IT = (int)(1024 / SS_C2_NT);
-            uint32_t grid = std::min<uint32_t>(n2, sms * 8);
+            uint32_t grid = std::min<uint32_t>(n2, g_base_grid[2]);
             SS_LAUNCH_U("base_c2", s1, hc[C_ETASK + 2], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s1>>>(
-                L[2], n2, dreqs, eb, L[0], tl.cap[0], counters)));
+                L[2], counters + C_NTASK + 2, counters + C_QHEAD + 2, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (uint32_t n1 = hc[C_NTASK + 1]) {
             constexpr int NT = SS_C1_NT, IT = (int)(256 / SS_C1_NT);
-            uint32_t grid = std::min<uint32_t>(n1, sms * 32);
+            uint32_t grid = std::min<uint32_t>(n1, g_base_grid[1]);
             SS_LAUNCH_U("base_c1", s2, hc[C_ETASK + 1], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s2>>>(
-                L[1], n1, dreqs, eb, L[0], tl.cap[0], counters)));
+                L[1], counters + C_NTASK + 1, counters + C_QHEAD + 1, dreqs, eb, L[0], tl.cap[0], counters)));
         }
         if (fork) {
             TRY(cudaEventRecord(ax.ev[1], s1), "join");

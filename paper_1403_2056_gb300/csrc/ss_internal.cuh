@@ -131,6 +131,7 @@ enum Counter : int {
     C_LVL_PAIRS = 9,  // (segment, bucket) pairs of the current level
     C_NTASK = 10,     // base-case tasks of class c at C_NTASK + c
     C_ETASK = 14,     // their strings at C_ETASK + c
+    C_QHEAD = 18,     // next task of class c's work queue at C_QHEAD + c
     C_NUM = 24
 };
 
