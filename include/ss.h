@@ -29,9 +29,9 @@
  *   - Return value: SS_OK, or a negative ss_status.  On error
  *     ss_last_error_detail() gives a message for the calling thread.  Outputs
  *     are unspecified after an error.
- *   - Reads of string bytes are aligned 8-byte words that hold at least one
- *     byte of the string being read (or of its terminator), so no read
- *     touches a page the strings do not touch.
+ *   - Reads of string bytes are aligned 8-byte words in a 4 KiB page that
+ *     holds at least one byte of the string being read (or of its
+ *     terminator), so no read touches a page the strings do not touch.
  */
 #ifndef SS_GB300_H
 #define SS_GB300_H

@@ -29,6 +29,7 @@
 // at that depth (Section 5.4, "LCPs for free"), computed in k_boundary once all
 // strings are placed.
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -45,12 +46,12 @@ namespace ss {
 // --------------------------------------------------------------- helpers
 
 __host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size, uint32_t target) {
-    // v + 1 = 2^d about size / target, d in [2, 10]
+    // v + 1 = 2^d about size / target, d in [2, kLevelD]
     uint32_t q = (size + target - 1) / target;
     uint32_t d = 0;
     while ((1u << d) < q) d++;
     if (d < 2) d = 2;
-    if (d > (uint32_t)kMaxD) d = kMaxD;
+    if (d > (uint32_t)kLevelD) d = kLevelD;
     return d;
 }
 
@@ -372,10 +373,11 @@ __global__ void __launch_bounds__(kThreads) k_pick_only(const uint64_t *sample, 
 
 // ------------------------------------------------------------ k_classify
 
+template <int D>
 struct ClassifySmem {
-    uint64_t t[kMaxV + 1];   // level order, one-based (t[0] unused)
-    uint64_t x[kMaxV + 1];   // in order, x[v] unused
-    uint32_t cnt[kMaxB + 1];
+    uint64_t t[(1 << D)];   // level order, one-based (t[0] unused)
+    uint64_t x[(1 << D)];   // in order, x[v] unused
+    uint32_t cnt[(2 << D)];
     uint16_t j[1 << kJumpBits];   // jump table (CLS_JUMP segments only)
 };
 
@@ -474,6 +476,7 @@ __device__ __forceinline__ void emit_bucket(uint32_t *cnt, uint16_t *obuf, uint3
 
 // The classifier is the segment's request's (or `cls` for all segments when
 // reqs is NULL); jt holds the jump tables of CLS_JUMP segments.
+template <int D>
 __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict__ segs, uint32_t nseg,
                                                        const ReqDesc *__restrict__ reqs, uint32_t cls_all,
                                                        const uint64_t *__restrict__ key,
@@ -481,7 +484,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict_
                                                        const uint16_t *__restrict__ jt,
                                                        uint16_t *__restrict__ obuf, uint32_t *__restrict__ counts) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ClassifySmem &S = *reinterpret_cast<ClassifySmem *>(smem_raw);
+    ClassifySmem<D> &S = *reinterpret_cast<ClassifySmem<D> *>(smem_raw);
     const uint32_t tile = blockIdx.x;
     const uint32_t si = find_seg(segs, nseg, tile, [](const BigSeg &s) { return s.tile_base; });
     const BigSeg sg = segs[si];
@@ -542,7 +545,7 @@ __global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict_
                 node[u] = 1;
             }
             if (cls == CLS_JUMP) {
-                uint32_t lmin = kMaxD;
+                uint32_t lmin = D;
 #pragma unroll
                 for (int u = 0; u < 4; u++) {
                     const uint64_t cu = c[it + u], cp = cu & pm;
@@ -683,18 +686,27 @@ __global__ void __launch_bounds__(kThreads) k_scan_down(uint32_t *a, const uint3
 
 // ------------------------------------------------------------ k_scatter
 
+template <int D>
 struct ScatterSmem {
-    uint32_t tbase[kMaxB + 1];   // global position of each bucket's first string from this tile
-    uint32_t lbase[kMaxB + 1];   // tile-local start of each bucket (exclusive scan of the tile's counts)
-    uint32_t binfo[kMaxB + 1];   // delta | final << 4 | done << 5 | first tile << 6 | nulpos << 8
+    static constexpr int MB = 2 * ((1 << D) - 1) + 1;   // buckets of a tree of depth D
     union {
-        uint16_t wpos[kWarps][kMaxB + 1];   // per warp: count, then running offset inside the tile's bucket
-        uint64_t stage[kTile];              // one payload array in tile-local bucket order
-        uint32_t stage32[kTile];
+        uint16_t wpos[kWarps][MB + 1];   // per warp: count, then running offset inside the tile's bucket
+        uint64_t buf[kTile + 2];            // after the ranks: the tile's keys, then its string offsets
     } u;
+    uint32_t sidx[kTile + 8];    // the tile's string indices (range rounded out to 16 bytes)
+    uint32_t tbase[MB + 1];   // global position of each bucket's first string from this tile
+    uint16_t lbase[MB + 1];   // tile-local start of each bucket (exclusive scan of the tile's counts)
+    uint16_t binfo[MB + 1];   // delta | final << 4 | done << 5 | first tile << 6 | nulpos << 8
     uint16_t slot_b[kTile];      // bucket of each tile-local slot
-    uint32_t wsum[kWarps];
+    uint16_t src[kTile];         // tile element held by each slot
+    uint32_t wcnt[kWarps];
+    uint64_t bar[3];             // completion of the index, key and offset copies
 };
+
+static_assert(offsetof(ScatterSmem<kMaxD>, sidx) % 16 == 0 && offsetof(ScatterSmem<kLevelD>, sidx) % 16 == 0,
+              "bulk copy targets 16-byte aligned");
+static_assert(offsetof(ScatterSmem<kMaxD>, bar) % 8 == 0 && offsetof(ScatterSmem<kLevelD>, bar) % 8 == 0,
+              "mbarriers 8-byte aligned");
 
 enum { MODE_SORT = 0, MODE_CLASSIFY = 1 };
 
@@ -707,31 +719,25 @@ __device__ __forceinline__ uint32_t bucket_start(const BigSeg &sg, const uint32_
     return b < B ? tile_pos(sg, scan, b, 0) : sg.begin + sg.size;
 }
 
-#ifndef SS_SCATTER_BATCH
-#define SS_SCATTER_BATCH 4
-#endif
 #ifndef SS_SCATTER_MINB
-#define SS_SCATTER_MINB 3
+#define SS_SCATTER_MINB 2
 #endif
-constexpr int kScatterBatch = SS_SCATTER_BATCH;   // elements whose reads are in flight together, per thread
 
 // Stable out-of-place redistribution of one tile (Section 4.3, the second hot
 // loop).  Each element's rank inside the tile is fixed first (lanes in order
-// inside a warp, warps in order inside the tile); then each payload array in
-// turn is reordered through shared memory into tile-local bucket order, so that
-// consecutive threads write the consecutive positions of a bucket's run.
-// Phase A's per-warp counts: 1 = one shared atomic per element; 0 = lanes
-// with equal buckets add once (warp match).  Ranks inside a warp step: 1 = the
-// lanes with the same bucket found by one vote per bucket bit (peers_of); 0 =
-// warp match.  The defaults measured fastest on GB300 on every workload.
-#ifndef SS_SCATTER_COUNT
-#define SS_SCATTER_COUNT 1
-#endif
-#ifndef SS_SCATTER_RANK
-#define SS_SCATTER_RANK 1
-#endif
-
-template <int MODE>
+// inside a warp, warps in order inside the tile), giving every element its
+// tile-local slot in bucket order.  The payload never passes through
+// registers: the tile's string indices are copied into shared memory by one
+// bulk copy issued at the start, its keys and then its string offsets by bulk
+// copies into the space the per-warp counts leave once the ranks are known;
+// each array is then written out slot by slot, so that consecutive threads
+// write the consecutive positions of a bucket's run.  Strings whose bucket is
+// final (one string, or all equal and complete) go straight to the output.
+// Strings whose bucket continues deeper keep their carried key only if the
+// depth stays; otherwise their next key is gathered afterwards (k_gather_new).
+// Phase A's per-warp counts are one shared atomic per element; the rank
+// inside a warp step comes from one vote per bucket bit (peers_of).
+template <int MODE, int D>
 __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const BigSeg *__restrict__ segs, uint32_t nseg,
                                                       const ReqDesc *__restrict__ reqs,
                                                       const uint32_t *__restrict__ idx_in,
@@ -743,7 +749,8 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
                                                       uint32_t *__restrict__ idx_out, uint64_t *__restrict__ soff_out,
                                                       uint64_t *__restrict__ key_out, uint32_t *counters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    ScatterSmem &S = *reinterpret_cast<ScatterSmem *>(smem_raw);
+    ScatterSmem<D> &S = *reinterpret_cast<ScatterSmem<D> *>(smem_raw);
+    constexpr int MB = ScatterSmem<D>::MB;
     const uint32_t tile = blockIdx.x;
     const uint32_t si = find_seg(segs, nseg, tile, [](const BigSeg &s) { return s.tile_base; });
     const BigSeg sg = segs[si];
@@ -755,7 +762,19 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     const uint32_t tcount = min((uint32_t)kTile, seg_end - tbeg);
     const uint32_t wbeg = tbeg + warp * kWarpSpan;
     const uint64_t *xs = splitters + (size_t)si * kMaxV;
+    // the tile's ranges rounded out to 16 bytes (the arrays start 256-byte aligned
+    // and are padded, so the rounded ranges stay inside the scratch block)
+    const uint32_t i0 = tbeg & ~3u, ioff = tbeg - i0;
+    const uint32_t ibytes = 4u * (((tbeg + tcount + 3u) & ~3u) - i0);
+    const uint32_t k0 = tbeg & ~1u, koff = tbeg - k0;
+    const uint32_t kbytes = 8u * (((tbeg + tcount + 1u) & ~1u) - k0);
 
+    if (MODE == MODE_SORT && threadIdx.x == 0) {
+        for (int k = 0; k < 3; k++) mbar_init(&S.bar[k], 1);
+        fence_mbar_init();
+        mbar_expect_tx(&S.bar[0], ibytes);
+        bulk_to_smem(S.sidx, idx_in + i0, ibytes, &S.bar[0]);
+    }
     // every bucket id of this thread in flight at once; kept in registers
     uint32_t bk[kItems];
 #pragma unroll
@@ -763,32 +782,25 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         uint32_t p = wbeg + u * 32 + lane;
         bk[u] = p < seg_end ? (uint32_t)obuf[p] : 0xFFFFu;
     }
-    for (uint32_t k = threadIdx.x; k < kWarps * (kMaxB + 1) / 2; k += blockDim.x)
+    for (uint32_t k = threadIdx.x; k < kWarps * (MB + 1) / 2; k += blockDim.x)
         reinterpret_cast<uint32_t *>(&S.u.wpos[0][0])[k] = 0;
     __syncthreads();
-    // phase A: per-warp bucket counts of its contiguous span
-#if SS_SCATTER_COUNT == 1
-    // one shared atomic per element on the 32-bit word holding the 16-bit count
-    // (a warp's span has 512 elements, so a count never carries into its neighbour)
+    // phase A: per-warp bucket counts of its contiguous span, one shared atomic
+    // per element on the 32-bit word holding the 16-bit count (a warp's span has
+    // 512 elements, so a count never carries into its neighbour)
 #pragma unroll
     for (int u = 0; u < kItems; u++)
         if (bk[u] != 0xFFFFu)
             atomicAdd(reinterpret_cast<uint32_t *>(&S.u.wpos[warp][bk[u] & ~1u]), 1u << (16 * (bk[u] & 1u)));
-#else
-#pragma unroll
-    for (int u = 0; u < kItems; u++) {
-        uint32_t peers = __match_any_sync(0xffffffffu, bk[u]);
-        if (bk[u] != 0xFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) S.u.wpos[warp][bk[u]] += (uint16_t)__popc(peers);
-        __syncwarp();
-    }
-#endif
     __syncthreads();
     // phase B: each warp's offset inside the tile's part of every bucket, the
     // tile's count of every bucket (in lbase for now) and the bucket facts.  The
     // counter and splitter reads of a half of this thread's buckets go out together.
-    constexpr int kHalf = (kMaxB + 1) / kThreads / 2;
+    static_assert(MB + 1 >= kThreads, "at least one bucket slot per thread");
+    constexpr int kPerT = (MB + 1) / kThreads;            // bucket slots per thread
+    constexpr int kHalf = kPerT >= 2 ? kPerT / 2 : 1;
 #pragma unroll
-    for (int half = 0; half < 2; half++) {
+    for (int half = 0; half < kPerT / kHalf; half++) {
         uint32_t tb[kHalf], st[kHalf], en[kHalf];
         uint64_t xr[kHalf], xl[kHalf];
 #pragma unroll
@@ -828,16 +840,16 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
                     }
                     uint32_t fin = (en[k] - st[k] == 1) || done;
                     uint32_t first = tb[k] == st[k];
-                    S.binfo[b] = delta | (fin << 4) | (done << 5) | (first << 6) | (np << 8);
+                    S.binfo[b] = (uint16_t)(delta | (fin << 4) | (done << 5) | (first << 6) | (np << 8));
                 }
             }
-            S.lbase[b] = run;
+            S.lbase[b] = (uint16_t)run;
         }
     }
     __syncthreads();
     // tile-local bucket starts: exclusive scan of the counts, 8 contiguous buckets per thread
     {
-        constexpr int kPer = (kMaxB + 1) / kThreads;
+        constexpr int kPer = (MB + 1) / kThreads;
         uint32_t c[kPer], sum = 0;
 #pragma unroll
         for (int k = 0; k < kPer; k++) { c[k] = S.lbase[threadIdx.x * kPer + k]; sum += c[k]; }
@@ -847,106 +859,61 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
             uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
             if (lane >= (uint32_t)o) incl += y;
         }
-        if (lane == 31) S.wsum[warp] = incl;
+        if (lane == 31) S.wcnt[warp] = incl;
         __syncthreads();
         uint32_t base = incl - sum;
-        for (uint32_t w = 0; w < warp; w++) base += S.wsum[w];
+        for (uint32_t w = 0; w < warp; w++) base += S.wcnt[w];
 #pragma unroll
-        for (int k = 0; k < kPer; k++) { S.lbase[threadIdx.x * kPer + k] = base; base += c[k]; }
+        for (int k = 0; k < kPer; k++) { S.lbase[threadIdx.x * kPer + k] = (uint16_t)base; base += c[k]; }
     }
     __syncthreads();
-    // ranks: tile-local slot of every element
-    uint32_t lp[kItems];
+    // ranks: tile-local slot of every element, and the element of every slot
 #pragma unroll
     for (int u = 0; u < kItems; u++) {
         const uint32_t b = bk[u];
         const bool ok = b != 0xFFFFu;
-#if SS_SCATTER_RANK == 1
         uint32_t peers = peers_of(b, d + 1);
-#else
-        uint32_t peers = __match_any_sync(0xffffffffu, b);
-#endif
         uint32_t rank = __popc(peers & lanemask_lt());
         uint32_t off = ok ? S.u.wpos[warp][b] : 0u;
-        lp[u] = ok ? S.lbase[b] + off + rank : 0u;
+        const uint32_t lp = ok ? S.lbase[b] + off + rank : 0u;
         __syncwarp();
         if (ok && lane == (uint32_t)(__ffs(peers) - 1)) S.u.wpos[warp][b] = (uint16_t)(off + __popc(peers));
         __syncwarp();
-        if (ok) S.slot_b[lp[u]] = (uint16_t)b;
-    }
-    __syncthreads();   // wpos is dead from here: its space holds the staged payload
-
-    if (MODE == MODE_SORT) {
-        const ReqDesc &R = reqs[sg.req];
-        // keys: the carried key, or the gather at the new depth
-#pragma unroll
-        for (int it = 0; it < kItems; it += kScatterBatch) {
-            uint32_t id[kScatterBatch], info[kScatterBatch];
-            uint64_t so[kScatterBatch], nk[kScatterBatch];
-#pragma unroll
-            for (int u = 0; u < kScatterBatch; u++) {
-                const uint32_t b = bk[it + u];
-                const uint32_t p = wbeg + (it + u) * 32 + lane;
-                info[u] = b != 0xFFFFu ? S.binfo[b] : 16u;
-                const bool carry = !(info[u] & 16u);
-                const bool gather = carry && (info[u] & 15u) != 0;
-                id[u] = gather ? idx_in[p] : 0u;
-                so[u] = gather ? soff_in[p] : 0ull;
-                nk[u] = (carry && !gather) ? key_in[p] : 0ull;
-            }
-#pragma unroll
-            for (int u = 0; u < kScatterBatch; u++)
-                if (!(info[u] & 16u) && (info[u] & 15u) != 0) nk[u] = load_key_o(R, id[u], so[u], sg.depth + (info[u] & 15u));
-#pragma unroll
-            for (int u = 0; u < kScatterBatch; u++)
-                if (!(info[u] & 16u)) S.u.stage[lp[it + u]] = nk[u];
+        if (ok) {
+            S.slot_b[lp] = (uint16_t)b;
+            S.src[lp] = (uint16_t)(warp * kWarpSpan + u * 32 + lane);
         }
-        __syncthreads();
+    }
+    fence_proxy_async();   // this thread's accesses of the count space come before the key copy into it
+    __syncthreads();       // wpos is dead from here: its space takes the keys, then the offsets
+    if (MODE == MODE_CLASSIFY) {
         for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
             const uint32_t b = S.slot_b[s];
-            if (S.binfo[b] & 16u) continue;
             const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
             if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
-            key_out[q] = S.u.stage[s];
+            idx_out[q - sg.begin] = tl * kTile + S.src[s];
         }
-        __syncthreads();
-        // string offsets
-#pragma unroll
-        for (int u = 0; u < kItems; u++) {
-            const uint32_t b = bk[u];
-            const uint32_t p = wbeg + u * 32 + lane;
-            if (b != 0xFFFFu && !(S.binfo[b] & 16u)) S.u.stage[lp[u]] = soff_in[p];
-        }
-        __syncthreads();
-        for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
-            const uint32_t b = S.slot_b[s];
-            if (S.binfo[b] & 16u) continue;
-            const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
-            if (q < sg.begin || q >= seg_end) continue;
-            soff_out[q] = S.u.stage[s];
-        }
-        __syncthreads();
+        return;
     }
-    // string indices; finished strings go straight to the output
-#pragma unroll
-    for (int u = 0; u < kItems; u++) {
-        const uint32_t p = wbeg + u * 32 + lane;
-        if (bk[u] != 0xFFFFu) S.u.stage32[lp[u]] = MODE == MODE_SORT ? idx_in[p] : p - sg.begin;
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&S.bar[1], kbytes);
+        bulk_to_smem(S.u.buf, key_in + k0, kbytes, &S.bar[1]);
     }
-    __syncthreads();
+    // string indices; strings whose bucket is final go straight to the output
+    if (!__syncthreads_and(mbar_wait(&S.bar[0], 0))) {
+        if (threadIdx.x == 0) set_error(counters, E_COPY_TIMEOUT, tile);
+        mbar_wait(&S.bar[1], 0);
+        return;
+    }
+    const ReqDesc &R = reqs[sg.req];
     for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
         const uint32_t b = S.slot_b[s];
         const uint32_t lo = s - S.lbase[b];
         const uint32_t q = S.tbase[b] + lo;
         if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
-        const uint32_t id = S.u.stage32[s];
-        if (MODE == MODE_CLASSIFY) {
-            idx_out[q - sg.begin] = id;
-            continue;
-        }
+        const uint32_t id = S.sidx[ioff + S.src[s]];
         const uint32_t info = S.binfo[b];
         if (info & 16u) {
-            const ReqDesc &R = reqs[sg.req];
             const uint32_t local = q - R.base;
             R.perm_out[local] = id;
             // all equal and complete: every string but the bucket's first has the whole key in common
@@ -954,6 +921,36 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         } else {
             idx_out[q] = id;
         }
+    }
+    // keys: the carried key where the depth stays (others are gathered later)
+    if (!__syncthreads_and(mbar_wait(&S.bar[1], 0))) {
+        if (threadIdx.x == 0) set_error(counters, E_COPY_TIMEOUT, tile);
+        return;
+    }
+    for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
+        const uint32_t b = S.slot_b[s];
+        const uint32_t info = S.binfo[b];
+        if (info & 31u) continue;   // final, or a new depth
+        const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
+        if (q < sg.begin || q >= seg_end) continue;
+        key_out[q] = S.u.buf[koff + S.src[s]];
+    }
+    fence_proxy_async();
+    __syncthreads();   // every key read from the buffer: it takes the offsets next
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(&S.bar[2], kbytes);
+        bulk_to_smem(S.u.buf, soff_in + k0, kbytes, &S.bar[2]);
+    }
+    if (!__syncthreads_and(mbar_wait(&S.bar[2], 0))) {
+        if (threadIdx.x == 0) set_error(counters, E_COPY_TIMEOUT, tile);
+        return;
+    }
+    for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
+        const uint32_t b = S.slot_b[s];
+        if (S.binfo[b] & 16u) continue;
+        const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
+        if (q < sg.begin || q >= seg_end) continue;
+        soff_out[q] = S.u.buf[koff + S.src[s]];
     }
 }
 
@@ -966,11 +963,16 @@ __device__ __forceinline__ void push_small(const TaskLists &tl, uint32_t *counte
     if (k < tl.cap[c]) tl.l[c][k] = t; else set_error(counters, E_SMALL_OVERFLOW, k);
 }
 
+// Child segments of every (segment, bucket) pair.  A bucket whose strings
+// continue at a new depth needs their keys there: buckets of more than 32
+// strings get gather chunks (k_gather_new loads the keys right after this
+// level), smaller ones become warp tasks that load their own keys.
 __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32_t nseg, const ReqDesc *reqs,
                                                       const uint32_t *npairs_dev,
                                                       const uint32_t *scan, const uint64_t *splitters,
                                                       uint32_t next_parity, BigSeg *next_big, TaskLists tl,
-                                                      Boundary *bounds, Caps caps, uint32_t *counters) {
+                                                      Boundary *bounds, GatherChunk *gchunks, Caps caps,
+                                                      uint32_t *counters) {
     uint32_t pr = blockIdx.x * blockDim.x + threadIdx.x;
     if (pr >= *npairs_dev) return;
     uint32_t si = find_seg(segs, nseg, pr, [](const BigSeg &s) { return s.bkt_base; });
@@ -997,6 +999,17 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
         delta = even_delta(r > 0 ? xs[r - 1] : 0ull, r < v ? xs[r] : 0ull, r, v, req_min_step(reqs[sg.req]));
     }
     uint32_t depth = sg.depth + delta;
+    const bool regather = delta != 0;
+    if (regather && size > kTinyMax) {
+        const uint32_t nch = (size + kGatherChunk - 1) / kGatherChunk;
+        const uint32_t k = atomicAdd(counters + C_NGATHER, nch);
+        if (k + nch <= caps.gather) {
+            for (uint32_t j = 0; j < nch; j++)
+                gchunks[k + j] = GatherChunk{st + j * kGatherChunk, min(en, st + (j + 1) * kGatherChunk), sg.req, depth};
+        } else {
+            set_error(counters, E_GATHER_OVERFLOW, k);
+        }
+    }
     if (size > kSmallMax) {
         uint32_t k = atomicAdd(counters + C_NBIG, 1u);
         if (k < caps.big) {
@@ -1012,7 +1025,33 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
             set_error(counters, E_BIG_OVERFLOW, k);
         }
     } else {
-        push_small(tl, counters, SmallTask{st, size, depth, sg.req, next_parity, 0});
+        push_small(tl, counters, SmallTask{st, size, depth, sg.req, next_parity, (regather && size <= kTinyMax) ? 1u : 0u});
+    }
+}
+
+// the next keys of every gather chunk of the level (a fixed grid walks the
+// chunk list, whose length is read on the device)
+__global__ void __launch_bounds__(256) k_gather_new(const GatherChunk *__restrict__ gchunks, const uint32_t *nchunks_dev,
+                                                    const ReqDesc *__restrict__ reqs, const uint32_t *__restrict__ idx,
+                                                    const uint64_t *__restrict__ soff, uint64_t *__restrict__ key) {
+    const uint32_t nch = *nchunks_dev;
+    for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
+        const GatherChunk g = gchunks[c];
+        const ReqDesc &R = reqs[g.req];
+        constexpr int U = kGatherChunk / 256;
+        uint32_t id[U];
+        uint64_t so[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t p = g.begin + u * 256 + threadIdx.x;
+            id[u] = p < g.end ? idx[p] : 0u;
+            so[u] = p < g.end ? soff[p] : 0ull;
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const uint32_t p = g.begin + u * 256 + threadIdx.x;
+            if (p < g.end) key[p] = load_key_o(R, id[u], so[u], g.depth);
+        }
     }
 }
 
@@ -1127,9 +1166,11 @@ static cudaError_t ensure_attrs() {
     cudaError_t e;
     if ((e = set_smem(k_build_trees, sizeof(TreeSmem)))) return e;
     if ((e = set_smem(k_pick_only, sizeof(TreeSmem)))) return e;
-    if ((e = set_smem(k_classify, sizeof(ClassifySmem)))) return e;
-    if ((e = set_smem(k_scatter<MODE_SORT>, sizeof(ScatterSmem)))) return e;
-    if ((e = set_smem(k_scatter<MODE_CLASSIFY>, sizeof(ScatterSmem)))) return e;
+    if ((e = set_smem(k_classify<kLevelD>, sizeof(ClassifySmem<kLevelD>)))) return e;
+    if ((e = set_smem(k_classify<kMaxD>, sizeof(ClassifySmem<kMaxD>)))) return e;
+    if ((e = set_smem_max(k_scatter<MODE_SORT, kLevelD>, sizeof(ScatterSmem<kLevelD>)))) return e;
+    if ((e = set_smem_max(k_scatter<MODE_CLASSIFY, kLevelD>, sizeof(ScatterSmem<kLevelD>)))) return e;
+    if ((e = set_smem_max(k_scatter<MODE_CLASSIFY, kMaxD>, sizeof(ScatterSmem<kMaxD>)))) return e;
     if ((e = set_smem_max(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>)))) return e;
     if ((e = set_smem_max(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>)))) return e;
     if ((e = set_smem_max(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>)))) return e;
@@ -1169,6 +1210,9 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
         caps.small[c] = (uint32_t)(N / least + nreq + 1);
     }
     caps.bound = (uint32_t)(N + 1);
+    // gather chunks of one level: buckets of more than kTinyMax strings, one
+    // chunk per kGatherChunk of them
+    caps.gather = (uint32_t)(N / (kTinyMax + 1) + N / kGatherChunk + nreq + 2);
     // sum over big segments of B * tiles <= 2047 (N / kTile + big) + 8 big
     caps.counts = (uint32_t)std::min<size_t>(0xFFFFFFF0ull, (size_t)kMaxB * ((size_t)N / kTile + caps.big) + (size_t)caps.big * 8 + 4096);
     np = caps.counts / kScanChunk + 2;
@@ -1184,6 +1228,7 @@ static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
     c.take<BigSeg>(caps.big); c.take<BigSeg>(caps.big);
     for (int k = 0; k < kClasses; k++) c.take<SmallTask>(caps.small[k]);
     c.take<Boundary>(caps.bound);
+    c.take<GatherChunk>(caps.gather);
     c.take<uint32_t>(C_NUM);
     c.take<ReqDesc>(nreq);
     c.take<uint32_t>(nreq);
@@ -1253,6 +1298,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         tl.cap[k] = caps.small[k];
     }
     Boundary *bounds = c.take<Boundary>(caps.bound);
+    GatherChunk *gchunks = c.take<GatherChunk>(caps.gather);
     uint32_t *counters = c.take<uint32_t>(C_NUM);
     ReqDesc *dreqs = c.take<ReqDesc>(nreq);
     uint32_t *shared = c.take<uint32_t>(nreq);   // characters shared by all strings of each large request
@@ -1354,19 +1400,22 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             SS_LAUNCH_U("setup_big", st, nbig, k_setup_big<<<1, 1024, 0, st>>>(big[cur], nbig, counters + C_LVL_COUNTS));
             if (any_jump)
                 SS_LAUNCH_U("jump_tables", st, nbig, k_jump_tables<<<nbig, kThreads, 0, st>>>(big[cur], dreqs, splitters, jt));
-            SS_LAUNCH_U("classify", st, nelems, k_classify<<<ntiles, kThreads, sizeof(ClassifySmem), st>>>(
+            SS_LAUNCH_U("classify", st, nelems, k_classify<kLevelD><<<ntiles, kThreads, sizeof(ClassifySmem<kLevelD>), st>>>(
                 big[cur], nbig, dreqs, 0u, key[cur], splitters, jt, obuf, counts));
             TRY(cudaGetLastError(), "classify launch");
             if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) goto done;
-            SS_LAUNCH_U("scatter", st, nelems, k_scatter<MODE_SORT><<<ntiles, kThreads, sizeof(ScatterSmem), st>>>(
+            SS_LAUNCH_U("scatter", st, nelems, k_scatter<MODE_SORT, kLevelD><<<ntiles, kThreads, sizeof(ScatterSmem<kLevelD>), st>>>(
                 big[cur], nbig, dreqs, idx[cur], soff[cur], key[cur], obuf, counts, splitters, idx[nxt], soff[nxt],
                 key[nxt], counters));
             TRY(cudaMemsetAsync(counters + C_NBIG, 0, sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_TILES, 0, 3 * sizeof(uint32_t), st), "reset");
             TRY(cudaMemsetAsync(counters + C_ELEMS, 0, sizeof(uint32_t), st), "reset");
+            TRY(cudaMemsetAsync(counters + C_NGATHER, 0, sizeof(uint32_t), st), "reset");
             SS_LAUNCH_U("buckets", st, npairs, k_buckets<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(
-                big[cur], nbig, dreqs, counters + C_LVL_PAIRS, counts, splitters, nxt, big[nxt], tl, bounds, caps,
-                counters));
+                big[cur], nbig, dreqs, counters + C_LVL_PAIRS, counts, splitters, nxt, big[nxt], tl, bounds, gchunks,
+                caps, counters));
+            SS_LAUNCH_U("gather_new", st, nelems, k_gather_new<<<sm_count() * 8, 256, 0, st>>>(
+                gchunks, counters + C_NGATHER, dreqs, idx[nxt], soff[nxt], key[nxt]));
             TRY(cudaGetLastError(), "level launch");
             TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
             TRY(cudaStreamSynchronize(st), "level sync");
@@ -1499,12 +1548,23 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
         if (n) {
             if (classifier == CLS_JUMP)
                 SS_LAUNCH("jump_tables", st, k_jump_tables<<<1, kThreads, 0, st>>>(seg, nullptr, spl, jt));
-            SS_LAUNCH("classify", st, k_classify<<<tiles, kThreads, sizeof(ClassifySmem), st>>>(
-                seg, 1, nullptr, classifier, keys, spl, jt, bucket_out, counts));
+            // the tree's depth picks the smallest kernel variant that holds it
+            if (d <= (uint32_t)kLevelD) {
+                SS_LAUNCH("classify", st, k_classify<kLevelD><<<tiles, kThreads, sizeof(ClassifySmem<kLevelD>), st>>>(
+                    seg, 1, nullptr, classifier, keys, spl, jt, bucket_out, counts));
+            } else {
+                SS_LAUNCH("classify", st, k_classify<kMaxD><<<tiles, kThreads, sizeof(ClassifySmem<kMaxD>), st>>>(
+                    seg, 1, nullptr, classifier, keys, spl, jt, bucket_out, counts));
+            }
             if ((e = cudaGetLastError())) break;
             if ((rc = launch_scan(counts, ncounts, counters + C_LVL_COUNTS, partial, st)) != SS_OK) break;
-            SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY><<<tiles, kThreads, sizeof(ScatterSmem), st>>>(
-                seg, 1, nullptr, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, nullptr, counters));
+            if (d <= (uint32_t)kLevelD) {
+                SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY, kLevelD><<<tiles, kThreads, sizeof(ScatterSmem<kLevelD>), st>>>(
+                    seg, 1, nullptr, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, nullptr, counters));
+            } else {
+                SS_LAUNCH("scatter", st, k_scatter<MODE_CLASSIFY, kMaxD><<<tiles, kThreads, sizeof(ScatterSmem<kMaxD>), st>>>(
+                    seg, 1, nullptr, nullptr, nullptr, nullptr, bucket_out, counts, spl, order_out, nullptr, nullptr, counters));
+            }
             if ((e = cudaGetLastError())) break;
             SS_LAUNCH("bucket_begin", st, k_bucket_begin<<<1, 256, 0, st>>>(seg, counts, bucket_begin_out));
         } else {

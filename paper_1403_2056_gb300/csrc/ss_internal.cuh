@@ -26,10 +26,14 @@ constexpr int kWarps = kThreads / 32;
 #ifndef SS_MAX_D
 #define SS_MAX_D 10
 #endif
+#ifndef SS_LEVEL_D
+#define SS_LEVEL_D 8
+#endif
 constexpr int kItems = SS_ITEMS;               // elements per thread in a tile
 constexpr int kTile = kThreads * kItems;       // 4096 elements per tile
 constexpr int kWarpSpan = kTile / kWarps;      // 512 contiguous elements per warp
-constexpr int kMaxD = SS_MAX_D;                // tree depth: v = 2^d - 1 <= 1023
+constexpr int kMaxD = SS_MAX_D;                // largest tree depth of any entry point: v = 2^d - 1 <= 1023
+constexpr int kLevelD = SS_LEVEL_D;            // largest tree depth of a sort's levels: v <= 255
 constexpr int kMaxV = (1 << kMaxD) - 1;
 constexpr int kMaxB = 2 * kMaxV + 1;           // 2047 buckets
 #ifndef SS_SMALL_MAX
@@ -132,6 +136,7 @@ enum Counter : int {
     C_NTASK = 10,     // base-case tasks of class c at C_NTASK + c
     C_ETASK = 14,     // their strings at C_ETASK + c
     C_QHEAD = 18,     // next task of class c's work queue at C_QHEAD + c
+    C_NGATHER = 22,   // chunks of strings whose next key is gathered after the scatter
     C_NUM = 24
 };
 
@@ -153,12 +158,21 @@ enum DevError : uint32_t {
     E_BOUND_OVERFLOW = 3,
     E_BAD_BUCKET = 4,
     E_BAD_POS = 5,
+    E_COPY_TIMEOUT = 6,   // a bulk copy into shared memory did not complete within its wait budget
+    E_GATHER_OVERFLOW = 7,
 };
 
 struct Caps {                   // capacities of the scratch lists
     uint32_t big, bound, counts;
     uint32_t small[kClasses];
+    uint32_t gather;            // gather chunks of one level
 };
+
+// a run of positions [begin, end) of one request whose keys are loaded anew at depth
+struct GatherChunk {
+    uint32_t begin, end, req, depth;
+};
+constexpr uint32_t kGatherChunk = 2048;   // positions per gather chunk
 
 // ------------------------------------------------------------ device math
 __device__ __forceinline__ uint64_t bswap64(uint64_t x) {
@@ -190,7 +204,10 @@ __device__ __forceinline__ uint32_t lcp8(uint64_t a, uint64_t b) {
 
 // chars_h: 8 bytes of string i (starting at byte `off` of chars) at depth h,
 // big-endian, zero past the end.  Reads the aligned word holding byte h, and
-// the next aligned word only when the string continues into it.
+// the next aligned word when the string continues into it.  For a terminated
+// string that is known only once the first word has arrived, so the next word
+// is read together with it whenever both lie in the same 4 KiB page (mapped
+// whenever the first word is); bytes after the terminator are masked off.
 __device__ __forceinline__ uint64_t load_key_o(const ReqDesc &R, uint32_t i, uint64_t off, uint32_t h) {
     uint64_t rem = ~0ULL;   // bytes of the string left from depth h (terminated: unknown)
     if (R.lengths) {
@@ -205,14 +222,17 @@ __device__ __forceinline__ uint64_t load_key_o(const ReqDesc &R, uint32_t i, uin
     uintptr_t a = (uintptr_t)p;
     const uint64_t *w = (const uint64_t *)(a & ~(uintptr_t)7);
     uint32_t sh = (uint32_t)(a & 7) * 8;
-    // a known length decides the second word before the first arrives: both in flight
+    // a known length decides the second word before the first arrives, and so
+    // does a second word in the first one's page: both in flight
     const bool known = rem != ~0ULL;
-    uint64_t w1 = (sh && known && rem > (uint64_t)(8 - (a & 7))) ? __ldg(w + 1) : 0ull;
+    const bool same_page = ((uintptr_t)(w + 1) & 4095u) != 0;
+    const bool ahead = sh && (known ? rem > (uint64_t)(8 - (a & 7)) : same_page);
+    uint64_t w1 = ahead ? __ldg(w + 1) : 0ull;
     uint64_t w0 = __ldg(w);
     uint64_t v = w0 >> sh;   // memory bytes p[0 .. 8 - (a&7)) in the low bytes
     if (sh) {
-        // terminated: continue only if no 0 byte among the valid bytes
-        if (!known && !has_zero(v | (~0ULL << (64 - sh)))) w1 = __ldg(w + 1);
+        // terminated, second word in the next page: continue only if no 0 byte among the valid bytes
+        if (!known && !same_page && !has_zero(v | (~0ULL << (64 - sh)))) w1 = __ldg(w + 1);
         v |= w1 << (64 - sh);
     }
     uint64_t key = bswap64(v);
@@ -235,8 +255,9 @@ __device__ __forceinline__ uint64_t keep_bytes(uint64_t key, uint32_t k) {
 }
 
 // chars_h for 16 characters: k0 = bytes [h, h+8), k1 = [h+8, h+16), zero past
-// the end.  Each further aligned word is read only when the string continues
-// into it, so no read leaves the string and its terminator.
+// the end.  Each further aligned word is read when the string continues into
+// it or, for a terminated string, ahead of that test when it lies in the first
+// word's 4 KiB page, so no read touches a page the string does not.
 __device__ __forceinline__ void load_key2_o(const ReqDesc &R, uint32_t i, uint64_t off, uint32_t h, uint64_t &k0,
                                             uint64_t &k1) {
     uint64_t rem = ~0ULL;
@@ -253,19 +274,26 @@ __device__ __forceinline__ void load_key2_o(const ReqDesc &R, uint32_t i, uint64
     const uint64_t *w = (const uint64_t *)(a & ~(uintptr_t)7);
     const uint32_t sh = (uint32_t)(a & 7) * 8;
     const uint64_t avail0 = 8 - (a & 7);   // bytes of the string's window in the first word
-    uint64_t w0 = __ldg(w);
     bool more1, more2;
-    uint64_t w1 = 0, w2 = 0;
+    uint64_t w0, w1 = 0, w2 = 0;
     if (rem == ~0ULL) {
+        const uintptr_t pg = (uintptr_t)w >> 12;
+        const bool a1 = ((uintptr_t)(w + 1) >> 12) == pg;
+        const bool a2 = sh && ((uintptr_t)(w + 2) >> 12) == pg;
+        if (a1) w1 = __ldg(w + 1);
+        if (a2) w2 = __ldg(w + 2);
+        w0 = __ldg(w);
         more1 = !has_zero((w0 >> sh) | (sh ? (~0ULL << (64 - sh)) : 0ULL));
-        if (more1) w1 = __ldg(w + 1);
+        if (more1 && !a1) w1 = __ldg(w + 1);
         more2 = more1 && sh && !has_zero(w1);
+        if (more2 && !a2) w2 = __ldg(w + 2);
     } else {
+        w0 = __ldg(w);
         more1 = rem > avail0;
         if (more1) w1 = __ldg(w + 1);
         more2 = sh && rem > avail0 + 8;
+        if (more2) w2 = __ldg(w + 2);
     }
-    if (more2) w2 = __ldg(w + 2);
     uint64_t v0 = sh ? ((w0 >> sh) | (w1 << (64 - sh))) : w0;
     uint64_t v1 = sh ? ((w1 >> sh) | (w2 << (64 - sh))) : w1;
     k0 = bswap64(v0);
@@ -297,6 +325,67 @@ __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finalise
 
 __device__ __forceinline__ void set_error(uint32_t *counters, uint32_t code, uint32_t info) {
     if (atomicCAS(counters + C_ERROR, 0u, code) == 0u) counters[C_ERRINFO] = info;
+}
+
+// ----------------------------------------- bulk copies into shared memory
+// One-dimensional bulk copies (cp.async.bulk, the TMA unit's untiled form):
+// global and shared addresses 16-byte aligned, size a multiple of 16, and
+// completion counted in bytes on an mbarrier in shared memory.
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t arrivals) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(arrivals) : "memory");
+}
+
+// makes the initialisation of this thread's mbarriers visible to the bulk-copy unit
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// orders this thread's earlier shared-memory accesses before later bulk copies
+// into shared memory (every thread that touched the space runs it, then a CTA
+// barrier, then one thread issues the copy)
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+// one arrival that also announces `bytes` of copies completing on the barrier
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void bulk_to_smem(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Waits for phase `parity` of the barrier to complete, for at most
+// kCopyWaitCycles SM clock cycles (about a second); returns false when the
+// budget ran out (the caller records E_COPY_TIMEOUT and skips the data).
+constexpr long long kCopyWaitCycles = 2000000000ll;
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    if (mbar_test(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_test(bar, parity))
+        if (clock64() - t0 > kCopyWaitCycles) return false;
+    return true;
 }
 
 // ------------------------------------------------------- host-side helpers
