@@ -193,6 +193,41 @@ def library_radix_context(P, torch, dev, stream, chars, offsets, n, reps=5):
                     "8 characters only, no LCPs; context, not a target"}
 
 
+def compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb, perm, lcp, reps=5):
+    """The step's merge with each method of ss_merge_ex (pairwise rounds, the
+    default; one pass with LCP loser trees): median time of the call, the
+    kernels' times from the library's launch events, and whether the outputs
+    equal the default's (which perm / lcp hold on entry)."""
+    ref = torch.cat([perm, lcp]).clone()
+    out = {}
+    for method, name in ((P.MERGE_PAIRWISE, "pairwise_rounds"), (P.MERGE_LOSER_TREE, "loser_tree")):
+        def m():
+            P.ss_merge_ex(chars, offsets, None, 0, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], method=method,
+                          stream=stream)
+        m()
+        torch.cuda.synchronize(dev)
+        ts = []
+        for _ in range(reps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            m()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(e0.elapsed_time(e1))
+        P.profile_reset()
+        P.profile_enable(True)
+        m()
+        torch.cuda.synchronize(dev)
+        P.profile_enable(False)
+        prof = P.profile_read()
+        out[name] = {"ms": float(np.median(ts)), "kernels_ms": {k: round(v[1], 4) for k, v in prof.items()},
+                     "outputs_equal_default": bool(torch.equal(torch.cat([perm, lcp]), ref))}
+    perm.copy_(ref[:perm.shape[0]])
+    lcp.copy_(ref[perm.shape[0]:])
+    return out
+
+
 CLASSIFIERS = ("unroll", "equal", "jump")
 
 
@@ -868,6 +903,9 @@ def main():
                        "equals_device_result": bool(same)}
 
     if rank == 0 and not args.no_extra:
+        line["merge_methods"] = dict(what="the step's merge of its runs by each method of ss_merge_ex",
+                                     **compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb,
+                                                             perm, lcp))
         line["classifiers"] = dict(what="the step's 4 runs sorted by one ss_sort_batch_tuned call per classifier",
                                    **compare_classifiers(P, torch, dev, stream, reqs))
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)

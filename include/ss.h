@@ -210,6 +210,29 @@ int ss_merge(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32
              const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
              uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
 
+/* merge methods of ss_merge_ex */
+#define SS_MERGE_PAIRWISE 0u    /* ceil(log2 K) rounds of pairwise LCP merges (ss_merge's method) */
+#define SS_MERGE_LOSER_TREE 1u  /* one pass with an LCP loser tree per job, up to 8 runs */
+
+/*
+ * ss_merge_ex -- ss_merge with the merge method chosen (same arguments,
+ * order, results and completion; the output is the same for every method).
+ *   method : SS_MERGE_PAIRWISE -- as ss_merge.
+ *            SS_MERGE_LOSER_TREE -- the K-way LCP-merge of Algorithm 4
+ *            (Section 5.2) in one pass: the output is cut into jobs at
+ *            splitter strings taken from the runs (every 128th string of
+ *            every run, placed in the other runs by binary search, Section
+ *            5.3), and each job is merged by one thread with an LCP-aware
+ *            tournament tree (LCP-Compare, Algorithm 2, with the cached
+ *            characters of Section 5.4).  Applies to 2..8 non-empty runs;
+ *            with more, the pairwise rounds are used.
+ *   Errors: as ss_merge; an unknown method returns SS_ERR_INVALID.
+ */
+int ss_merge_ex(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32_t *lengths_dev,
+                uint32_t fixed_len, const uint32_t *run_perm_dev, const uint32_t *run_lcp_dev,
+                const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K, uint32_t method,
+                uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
+
 /*
  * ss_merge_noalloc -- ss_merge that allocates nothing, for callers that
  * cannot let a library allocate: a process whose device memory is reserved

@@ -20,7 +20,8 @@ from . import build as _build
 
 __all__ = [
     "SortError", "lib", "library_path",
-    "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge",
+    "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_ex",
+    "MERGE_PAIRWISE", "MERGE_LOSER_TREE",
     "ss_merge_noalloc", "ss_gather_keys", "ss_splitters", "ss_classify", "ss_classify_ex",
     "CLASSIFIER_UNROLL", "CLASSIFIER_EQUAL", "CLASSIFIER_JUMP",
     "profile_enable", "profile_reset", "profile_read", "launch_count",
@@ -29,6 +30,8 @@ __all__ = [
 
 # classifiers (SS_CLASSIFIER_* of the C header)
 CLASSIFIER_UNROLL, CLASSIFIER_EQUAL, CLASSIFIER_JUMP = 0, 1, 2
+# merge methods (SS_MERGE_* of the C header)
+MERGE_PAIRWISE, MERGE_LOSER_TREE = 0, 1
 
 STATUS = {0: "SS_OK", -1: "SS_ERR_INVALID", -2: "SS_ERR_OOM", -3: "SS_ERR_CUDA", -4: "SS_ERR_TIMEOUT",
           -5: "SS_ERR_TOO_LARGE", -6: "SS_ERR_UNIMPLEMENTED", -7: "SS_ERR_INTERNAL", -8: "SS_ERR_CANCELLED"}
@@ -65,6 +68,7 @@ def lib():
     L.ss_sort_batch.argtypes = [vp, u32, vp]
     L.ss_merge.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, u32, vp, vp, vp]
     L.ss_merge_noalloc.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, u32, vp, vp, vp]
+    L.ss_merge_ex.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, u32, u32, vp, vp, vp]
     L.ss_gather_keys.argtypes = [vp, vp, vp, u32, u32, vp, vp, vp]
     L.ss_splitters.argtypes = [vp, u32, u32, vp, vp]
     L.ss_classify.argtypes = [vp, u32, vp, u32, vp, vp, vp, vp]
@@ -85,7 +89,8 @@ def lib():
     L.ss_debug_fail_allocs.argtypes = [u32, u32]
     L.ss_scratch_bytes.argtypes = [u32]
     L.ss_scratch_bytes.restype = u64
-    for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_noalloc", "ss_gather_keys",
+    for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_ex", "ss_merge_noalloc",
+                 "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_classify_ex", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
                  "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
                  "ss_server_submit_host", "ss_sort_batch_tuned", "ss_autotune", "ss_server_cancel",
@@ -399,6 +404,15 @@ def ss_merge(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, p
     args, keep = _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
                              run_base)
     _check(lib().ss_merge(*args, _stream(stream)))
+    del keep
+
+
+def ss_merge_ex(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+                run_base=None, method=MERGE_PAIRWISE, stream=None):
+    """ss_merge with the merge method chosen (MERGE_PAIRWISE or MERGE_LOSER_TREE)."""
+    args, keep = _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+                             run_base)
+    _check(lib().ss_merge_ex(*args[:9], int(method), *args[9:], _stream(stream)))
     del keep
 
 

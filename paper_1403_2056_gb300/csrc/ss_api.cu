@@ -448,7 +448,19 @@ int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *
 int ss_merge(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
              const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
              const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
+    return ss_merge_ex(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin_host, run_base_host, K,
+                       SS_MERGE_PAIRWISE, perm_out, lcp_out, stream);
+}
+
+int ss_merge_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
+                const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
+                const uint32_t *run_base_host, uint32_t K, uint32_t method, uint32_t *perm_out, uint32_t *lcp_out,
+                ss_stream_t stream) {
     t_detail.clear();
+    if (method != SS_MERGE_PAIRWISE && method != SS_MERGE_LOSER_TREE) {
+        set_error_detail("ss_merge_ex: unknown merge method %u", method);
+        return SS_ERR_INVALID;
+    }
     if (K == 0 || !run_begin_host) {
         set_error_detail("ss_merge: K must be >= 1 with run_begin_host[K+1]");
         return SS_ERR_INVALID;
@@ -470,7 +482,8 @@ int ss_merge(const uint8_t *chars, const uint64_t *offsets, const uint32_t *leng
         return SS_ERR_INVALID;
     }
     ReqDesc set = make_req(chars, offsets, lengths, fixed_len, 0, nullptr, nullptr, nullptr);
-    return merge_runs(set, run_perm, run_lcp, run_begin_host, run_base_host, K, perm_out, lcp_out, as_stream(stream));
+    return merge_runs(set, run_perm, run_lcp, run_begin_host, run_base_host, K, perm_out, lcp_out, as_stream(stream),
+                      method);
 }
 
 int ss_gather_keys(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,

@@ -424,9 +424,18 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
 int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t stream);
 int engine_gather(const ReqDesc &r, const uint32_t *depth, uint64_t *keys_out, cudaStream_t stream);
 
+// merge methods (SS_MERGE_* of the C header)
+enum MergeMethod : uint32_t { MERGE_PAIRWISE = 0, MERGE_LOSER_TREE = 1 };
+constexpr uint32_t kKwayMaxRuns = 8;   // runs the loser-tree method merges in one pass
+// one-pass K-way merge of 2..kKwayMaxRuns non-empty runs (ss_kway.cu)
+int merge_kway(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *rb,
+               const uint32_t *base, uint32_t R, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t stream);
+size_t merge_kway_scratch(uint32_t total, uint32_t R, const uint32_t *rb);
+
 // merge (ss_merge.cu)
 int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
-               const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t stream);
+               const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t stream,
+               uint32_t method = 0);
 
 }  // namespace ss
 

@@ -609,7 +609,8 @@ __global__ void k_copy_run(const uint32_t *in_perm, const uint32_t *in_lcp, uint
 }
 
 int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
-               const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t st) {
+               const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t st,
+               uint32_t method) {
     uint32_t total = run_begin_host[K];
     // drop empty runs (they merge as nothing)
     std::vector<uint32_t> rb{0}, rbase;
@@ -619,6 +620,10 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             rbase.push_back(run_base_host ? run_base_host[k] : 0u);
         }
     uint32_t R = (uint32_t)rb.size() - 1;
+    // the loser-tree method: one pass over up to kKwayMaxRuns runs (ss_kway.cu);
+    // more runs go through the pairwise rounds below
+    if (method == MERGE_LOSER_TREE && R >= 2 && R <= kKwayMaxRuns)
+        return merge_kway(set, run_perm, run_lcp, rb.data(), rbase.data(), R, perm_out, lcp_out, st);
     size_t rounds = 0;
     for (uint32_t r = R; r > 1; r = (r + 1) / 2) rounds++;
     // window table: at most total / kCoarse + 2 entries per pair

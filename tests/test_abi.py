@@ -131,6 +131,10 @@ def test_merge_run_tables_checked_in_the_binding():
         P.ss_merge(1, 1, None, 0, 1, 1, [0, 2, 4], 1, 1, run_base=[0])
     with pytest.raises(ValueError):
         P.ss_merge_noalloc(1, 1, None, 0, 1, 1, [], 1, 1)
+    # an unknown merge method is refused by the library before any device work
+    with pytest.raises(P.SortError) as ei:
+        P.ss_merge_ex(1, 1, None, 0, 1, 1, [0, 1, 2], 1, 1, method=7, stream=0)
+    assert ei.value.status == -1 and "method" in ei.value.detail
 
 
 def test_device_buffer_length_rule():

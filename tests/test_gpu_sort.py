@@ -332,10 +332,13 @@ def test_merge_runs(K):
         rl = torch.from_numpy(run_lcp.view(np.int32)).cuda()
         perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
         lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
-        P.ss_merge(chars, offsets, lengths, ss.fixed_len, rp, rl, rb, perm, lcp)
         want_perm, want_lcp = oracle.sort(ss)
-        assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
-        assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
+        for method in (P.MERGE_PAIRWISE, P.MERGE_LOSER_TREE):
+            perm.fill_(-1)
+            lcp.fill_(-1)
+            P.ss_merge_ex(chars, offsets, lengths, ss.fixed_len, rp, rl, rb, perm, lcp, method=method)
+            assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm), method
+            assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp), method
 
 
 @pytest.mark.parametrize("K", [2, 4])
@@ -472,3 +475,39 @@ def test_readme_example():
     lcp = torch.empty(4, dtype=torch.int32, device="cuda")
     P.ss_sort(chars, offsets, 4, perm, lcp)
     assert perm.tolist() == [1, 3, 0, 2] and lcp.tolist() == [0, 5, 0, 0]
+
+
+@pytest.mark.parametrize("K", [2, 3, 5, 8])
+def test_loser_tree_merge_edge_cases(K):
+    """The loser-tree merge on runs of equal strings across runs (ties by run
+    order), runs of one string, empty runs between full ones, and runs longer
+    than the sparse splitter spacing, against the oracle."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    rng = np.random.default_rng(100 + K)
+    words = [b"", b"a", b"ab", b"abc", b"b", b"ba", b"http://x/y", b"http://x/y/z"]
+    strs = [words[int(i)] for i in rng.integers(0, len(words), 30_000)]
+    ss = W.from_bytes_list(strs)
+    sizes = rng.integers(0, 2 * ss.n // K, K)
+    sizes[0] = 1
+    if K > 2:
+        sizes[1] = 0
+    cuts = np.minimum(np.cumsum(sizes), ss.n)
+    cuts[-1] = ss.n
+    rb = np.concatenate([[0], cuts]).astype(np.uint32)
+    run_perm = np.empty(ss.n, np.uint32)
+    run_lcp = np.empty(ss.n, np.uint32)
+    for k in range(K):
+        b, e = int(rb[k]), int(rb[k + 1])
+        p, l = oracle.sort(W.subset(ss, np.arange(b, e)))
+        run_perm[b:e] = p
+        run_lcp[b:e] = l
+    chars, offsets, lengths = to_device(ss)
+    rp = torch.from_numpy(run_perm.view(np.int32)).cuda()
+    rl = torch.from_numpy(run_lcp.view(np.int32)).cuda()
+    perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    P.ss_merge_ex(chars, offsets, None, 0, rp, rl, rb, perm, lcp, run_base=rb[:-1], method=P.MERGE_LOSER_TREE)
+    want_perm, want_lcp = oracle.sort(ss)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
+    assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
