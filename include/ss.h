@@ -152,16 +152,28 @@ int ss_sort_batch(const ss_request *reqs_host, uint32_t count, ss_stream_t strea
 /*
  * Tuning of one request (0 fields: the library's defaults).  child_target:
  * the segment size the splitter tree aims its children at (a power of two in
- * [32, 65536]; the tree has about size / child_target leaves, at most 1024);
+ * [32, 65536]; the tree has about size / child_target leaves, at most 256);
  * min_step: the smallest depth step an even bucket takes (in [1, 9]; 9: it
- * never steps and keeps its key); classifier: one of SS_CLASSIFIER_*.  None
- * changes any result.
+ * never steps and keeps its key); classifier: one of SS_CLASSIFIER_*.
+ * alphabet: alphabet compression (Section 8.1) for a request of fixed-length
+ * strings (lengths NULL, fixed_len > 0) whose characters all belong to an
+ * alphabet of at most four bytes: SS_ALPHABET(a0, a1, a2, a3) with
+ * 1 <= a0 <= a1 <= a2 <= a3 (repeat the last byte for fewer), e.g.
+ * SS_ALPHABET('A', 'C', 'G', 'T').  Keys then hold 32 characters of 2 bits
+ * instead of 8 bytes; depths and LCPs stay in characters.  The library does
+ * not check the strings' bytes: a byte outside the alphabet gives an
+ * unspecified order.  0: bytes.  None of the fields changes any result.
  */
 typedef struct {
     uint32_t child_target;
     uint32_t min_step;
     uint32_t classifier;
+    uint32_t alphabet;
 } ss_tuning;
+
+#define SS_ALPHABET(a0, a1, a2, a3) \
+    ((uint32_t)(uint8_t)(a0) | ((uint32_t)(uint8_t)(a1) << 8) | ((uint32_t)(uint8_t)(a2) << 16) | \
+     ((uint32_t)(uint8_t)(a3) << 24))
 
 /*
  * ss_sort_batch_tuned -- ss_sort_batch with one tuning per request

@@ -23,7 +23,7 @@ __all__ = [
     "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_ex",
     "MERGE_PAIRWISE", "MERGE_LOSER_TREE",
     "ss_merge_noalloc", "ss_gather_keys", "ss_splitters", "ss_classify", "ss_classify_ex",
-    "CLASSIFIER_UNROLL", "CLASSIFIER_EQUAL", "CLASSIFIER_JUMP",
+    "CLASSIFIER_UNROLL", "CLASSIFIER_EQUAL", "CLASSIFIER_JUMP", "alphabet",
     "profile_enable", "profile_reset", "profile_read", "launch_count",
     "STATUS",
 ]
@@ -107,7 +107,17 @@ class HostRequest(C.Structure):
 
 
 class Tuning(C.Structure):
-    _fields_ = [("child_target", C.c_uint32), ("min_step", C.c_uint32), ("classifier", C.c_uint32)]
+    _fields_ = [("child_target", C.c_uint32), ("min_step", C.c_uint32), ("classifier", C.c_uint32),
+                ("alphabet", C.c_uint32)]
+
+
+def alphabet(symbols: bytes) -> int:
+    """SS_ALPHABET of up to four bytes (sorted, the last repeated for fewer)."""
+    b = sorted(set(symbols))
+    if not 1 <= len(b) <= 4 or b[0] == 0:
+        raise ValueError("an alphabet holds 1..4 non-zero bytes")
+    b = b + [b[-1]] * (4 - len(b))
+    return b[0] | (b[1] << 8) | (b[2] << 16) | (b[3] << 24)
 
 
 class Request(C.Structure):
@@ -255,7 +265,8 @@ def _request(q):
 
 
 def ss_sort_batch_tuned(requests, tunings=None, stream=None):
-    """As ss_sort_batch, with one (child_target, min_step[, classifier]) tuple per request (0: default)."""
+    """As ss_sort_batch, with one (child_target, min_step[, classifier[, alphabet]]) tuple per request
+    (0: default; alphabet from alphabet(b"ACGT") for fixed-length requests over at most four bytes)."""
     arr = (Request * max(1, len(requests)))()
     for k, q in enumerate(requests):
         arr[k] = _request(q)
@@ -263,7 +274,7 @@ def ss_sort_batch_tuned(requests, tunings=None, stream=None):
     if tunings is not None:
         tarr = (Tuning * max(1, len(requests)))()
         for k, t in enumerate(tunings):
-            tarr[k] = Tuning(int(t[0]), int(t[1]), int(t[2]) if len(t) > 2 else 0)
+            tarr[k] = Tuning(int(t[0]), int(t[1]), int(t[2]) if len(t) > 2 else 0, int(t[3]) if len(t) > 3 else 0)
     _check(lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
                                       len(requests), _stream(stream)))
 

@@ -290,7 +290,7 @@ int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *off
 
 extern "C" {
 
-int ss_version(void) { return 100; }
+int ss_version(void) { return 101; }
 
 int ss_last_error_detail(char *buf, size_t len) {
     const std::string &d = t_detail;
@@ -333,8 +333,22 @@ int ss_sort_batch(const ss_request *reqs, uint32_t count, ss_stream_t stream) {
     return engine_sort(v.data(), count, as_stream(stream));
 }
 
-// tuning of one request, packed as in ReqDesc::tune
-static int pack_tuning(const ss_tuning &t, uint32_t &out, const char *who) {
+// tuning of one request, packed as in ReqDesc::tune (and ReqDesc::alpha)
+static int pack_tuning(const ss_tuning &t, ReqDesc &r, const char *who) {
+    uint32_t &out = r.tune;
+    if (t.alphabet) {
+        const uint32_t a0 = t.alphabet & 0xFFu, a1 = (t.alphabet >> 8) & 0xFFu, a2 = (t.alphabet >> 16) & 0xFFu,
+                       a3 = t.alphabet >> 24;
+        if (!(a0 >= 1 && a0 <= a1 && a1 <= a2 && a2 <= a3)) {
+            set_error_detail("%s: alphabet bytes must satisfy 1 <= a0 <= a1 <= a2 <= a3", who);
+            return SS_ERR_INVALID;
+        }
+        if (r.lengths || r.fixed_len == 0) {
+            set_error_detail("%s: alphabet compression needs fixed-length strings (lengths NULL, fixed_len > 0)", who);
+            return SS_ERR_INVALID;
+        }
+        r.alpha = t.alphabet;
+    }
     uint32_t s = 0;
     if (t.child_target) {
         if (t.child_target < 32 || t.child_target > 65536 || (t.child_target & (t.child_target - 1))) {
@@ -367,7 +381,7 @@ int ss_sort_batch_tuned(const ss_request *reqs, const ss_tuning *tunings, uint32
         const ss_request &q = reqs[i];
         v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
         int rc = check_req(v[i], "ss_sort_batch_tuned");
-        if (rc == SS_OK && tunings) rc = pack_tuning(tunings[i], v[i].tune, "ss_sort_batch_tuned");
+        if (rc == SS_OK && tunings) rc = pack_tuning(tunings[i], v[i], "ss_sort_batch_tuned");
         if (rc != SS_OK) return rc;
     }
     return engine_sort(v.data(), count, as_stream(stream));
@@ -384,7 +398,7 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
     int rc = check_req(r, "ss_autotune");
     if (rc != SS_OK) return rc;
     const uint32_t n = std::min<uint32_t>(req->n, sample_n ? sample_n : 2000000u);
-    *best_out = ss_tuning{0, 0, 0};
+    *best_out = ss_tuning{0, 0, 0, 0};
     if (best_ms_out) *best_ms_out = 0;
     if (n < 2) return SS_OK;
     cudaStream_t st = as_stream(stream);
@@ -403,7 +417,7 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
     double best = -1;
     // one candidate: a warm sort (pool, caches), then a timed one
     auto try_one = [&](const ss_tuning &t) -> bool {
-        if ((rc = pack_tuning(t, r.tune, "ss_autotune")) != SS_OK) return false;
+        if ((rc = pack_tuning(t, r, "ss_autotune")) != SS_OK) return false;
         if ((rc = engine_sort(&r, 1, st)) != SS_OK) return false;
         if ((e = cudaEventRecord(e0, st))) return false;
         if ((rc = engine_sort(&r, 1, st)) != SS_OK) return false;
@@ -423,11 +437,11 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
         bool ok = true;
         for (uint32_t ct : targets)
             for (uint32_t ms : steps)
-                if (ok) ok = try_one(ss_tuning{ct, ms, CLS_UNROLL});
+                if (ok) ok = try_one(ss_tuning{ct, ms, CLS_UNROLL, 0});
         // the other classifiers with the best tree shape
         const ss_tuning shape = *best_out;
-        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_EQUAL});
-        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_JUMP});
+        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_EQUAL, 0});
+        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_JUMP, 0});
     } while (0);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

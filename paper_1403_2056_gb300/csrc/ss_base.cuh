@@ -53,9 +53,11 @@ __device__ __forceinline__ WElem shfl_xor_welem(const WElem &e, int m) {
 // (string offset `off`) and its 16 characters at `depth`.  Writes perm and lcp
 // of R-local positions out .. out + m - 1 (not the lcp of position `out`,
 // which the caller owns).
+template <bool A>
 __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t off,
                                             uint64_t k0, uint64_t k1, uint32_t out) {
     const uint32_t lane = threadIdx.x & 31;
+    const uint32_t kc = key_chars(R);   // characters per key
     WElem e;
     if (lane < m) { e.g = 0; e.i = id; e.o = off; e.k0 = k0; e.k1 = k1; }
     else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.o = 0; e.k0 = ~0ull; e.k1 = ~0ull; }
@@ -76,10 +78,10 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
         uint64_t p1 = __shfl_up_sync(0xffffffffu, e.k1, 1);
         bool start = true;
         if (lane > 0 && lane < m && pg == e.g) {
-            if (p0 != e.k0) lcp = depth + lcp8(p0, e.k0);
-            else if (has_zero(e.k0)) lcp = depth + nulpos(e.k0);
-            else if (p1 != e.k1) lcp = depth + 8 + lcp8(p1, e.k1);
-            else if (has_zero(e.k1)) lcp = depth + 8 + nulpos(e.k1);
+            if (p0 != e.k0) lcp = depth + key_lcp<A>(R, p0, e.k0);
+            else if (key_ends<A>(R, e.k0, depth)) lcp = depth + key_len<A>(R, e.k0, depth);
+            else if (p1 != e.k1) lcp = depth + kc + key_lcp<A>(R, p1, e.k1);
+            else if (key_ends<A>(R, e.k1, depth + kc)) lcp = depth + kc + key_len<A>(R, e.k1, depth + kc);
             else start = false;
         }
         if (lane >= m) start = true;
@@ -93,8 +95,8 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
         bool active = lane < m && !(start && next_start);
         if (lane < m) e.g = sg;
         if (!__any_sync(0xffffffffu, active)) break;
-        depth += 16;
-        if (active) load_key2_o(R, e.i, e.o, depth, e.k0, e.k1);
+        depth += 2 * kc;
+        if (active) key2_at<A>(R, e.i, e.o, depth, e.k0, e.k1);
     }
     if (lane < m) {
         R.perm_out[out + lane] = e.i;
@@ -104,6 +106,7 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32
 
 // Tiny base cases (2..32 strings), one warp each.  The task count is read on
 // the device: the CTA base cases below append groups to the same list.
+template <bool A>
 __global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, const uint32_t *ntask_dev,
                                                          const ReqDesc *reqs, ElemBufs eb) {
     const uint32_t lane = threadIdx.x & 31;
@@ -122,13 +125,13 @@ __global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks,
             id = idx[t.begin + lane];
             off = soff[t.begin + lane];
             if (t.gather) {
-                load_key2_o(R, id, off, t.depth, k0, k1);
+                key2_at<A>(R, id, off, t.depth, k0, k1);
             } else {
                 k0 = key[t.begin + lane];
-                k1 = has_zero(k0) ? 0ull : load_key_o(R, id, off, t.depth + 8);
+                k1 = key_ends<A>(R, k0, t.depth) ? 0ull : key_at<A>(R, id, off, t.depth + key_chars(R));
             }
         }
-        warp_finish(R, t.size, t.depth, id, off, k0, k1, t.begin - R.base);
+        warp_finish<A>(R, t.size, t.depth, id, off, k0, k1, t.begin - R.base);
     }
 }
 
@@ -376,7 +379,7 @@ __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32
 // that hold the end of the string), the sorted keys still in registers give
 // every LCP and the task ends there; only segments with equal keys that
 // continue past these 8 characters go through the group rounds below.
-template <int NT, int ITEMS>
+template <int NT, int ITEMS, bool A>
 __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const uint32_t *ntask_dev, uint32_t *next_task,
                                                  const ReqDesc *reqs, ElemBufs eb, SmallTask *tiny, uint32_t tiny_cap,
                                                  uint32_t *counters) {
@@ -425,14 +428,14 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const u
             bool open = false;   // some neighbours share all 8 characters and continue
             for (uint32_t s = tid + 1; s < m; s += NT) {
                 const uint64_t a = S.SK[s - 1], b = S.SK[s];
-                open = open || (a == b && !has_zero(b));
+                open = open || (a == b && !key_ends<A>(R, b, depth));
             }
             if (!__syncthreads_or(open)) {
                 for (uint32_t s = tid; s < m; s += NT) {
                     R.perm_out[lbase + s] = S.SI[S.SP[s]];
                     if (s > 0) {
                         const uint64_t a = S.SK[s - 1], b = S.SK[s];
-                        R.lcp_out[lbase + s] = a != b ? depth + lcp8(a, b) : depth + nulpos(b);
+                        R.lcp_out[lbase + s] = a != b ? depth + key_lcp<A>(R, a, b) : depth + key_len<A>(R, b, depth);
                     }
                 }
                 finished = true;
@@ -508,8 +511,8 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const u
                     const uint64_t a = j ? k[j - 1] : prev, b = k[j];
                     lc[j] = 0;
                     if (s > 0 && s < M) {
-                        if (a != b) lc[j] = depth + lcp8(a, b);
-                        else if (has_zero(b)) lc[j] = depth + nulpos(b);
+                        if (a != b) lc[j] = depth + key_lcp<A>(R, a, b);
+                        else if (key_ends<A>(R, b, depth)) lc[j] = depth + key_len<A>(R, b, depth);
                         else open = true;
                     }
                 }
@@ -534,8 +537,8 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const u
                 uint32_t st = 1;
                 if (pos != S.SG[pos]) {   // not the first position of its group
                     uint64_t a = S.SK[pos - 1], b = S.SK[pos];
-                    if (a != b) R.lcp_out[lbase + pos] = depth + lcp8(a, b);
-                    else if (has_zero(b)) R.lcp_out[lbase + pos] = depth + nulpos(b);
+                    if (a != b) R.lcp_out[lbase + pos] = depth + key_lcp<A>(R, a, b);
+                    else if (key_ends<A>(R, b, depth)) R.lcp_out[lbase + pos] = depth + key_len<A>(R, b, depth);
                     else st = 0;
                 }
                 S.MG[s] = st ? pos : 0u;
@@ -584,7 +587,7 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const u
                     uint32_t pos = spos[j];
                     S.ACT[S.MG[s]] = (uint16_t)pos;
                     uint32_t orig = S.SP[pos];
-                    S.SK[pos] = load_key_o(R, S.SI[orig], soff[t.begin + orig], depth + 8);
+                    S.SK[pos] = key_at<A>(R, S.SI[orig], soff[t.begin + orig], depth + key_chars(R));
                 }
             }
             // groups of 2..32 strings go to the warp kernel: their string indices in
@@ -606,14 +609,14 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const u
                 }
                 if (lane == 0) {
                     uint32_t k = S.wbase + w;
-                    if (k < tiny_cap) tiny[k] = SmallTask{t.begin + s0, sz, depth + 8, t.req, t.parity ^ 1u, 1u};
+                    if (k < tiny_cap) tiny[k] = SmallTask{t.begin + s0, sz, depth + key_chars(R), t.req, t.parity ^ 1u, 1u};
                     else set_error(counters, E_SMALL_OVERFLOW, k);
                 }
             }
             __syncthreads();
             if (tid == 0) { S.nwl = 0; S.nws = 0; }
             M = M2;
-            depth += 8;
+            depth += key_chars(R);
             __syncthreads();
         }
         // positions that ended as groups of one

@@ -36,6 +36,7 @@
 #include <algorithm>
 #include <atomic>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "ss_internal.cuh"
@@ -61,9 +62,10 @@ __host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size, uint32_t ta
 // the key it carries, which still holds at least 8 - min_step + 1 unresolved
 // characters, and the random gather of a new key is saved.  Any depth up to
 // the shared prefix gives the same result.
-__device__ __forceinline__ uint32_t even_delta(uint64_t xl, uint64_t xr, uint32_t r, uint32_t v, uint32_t min_step) {
+__device__ __forceinline__ uint32_t even_delta(const ReqDesc &R, uint64_t xl, uint64_t xr, uint32_t r, uint32_t v,
+                                               uint32_t min_step) {
     if (r == 0 || r == v) return 0u;
-    uint32_t l = lcp8(xl, xr);
+    uint32_t l = key_lcp(R, xl, xr);
     return l >= min_step ? l : 0u;
 }
 
@@ -100,6 +102,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 
 // every element starts as (string index, string offset, key at depth 0); the
 // offset travels with the index so later gathers need one random load, not two
+template <bool A>
 __global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t *idx0, uint64_t *soff0, uint64_t *key0,
                        uint64_t *next0) {
     for (uint32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < N; g += gridDim.x * blockDim.x) {
@@ -111,8 +114,9 @@ __global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t 
         soff0[g] = off;
         // characters 0..15: the second word serves the shared-prefix step below
         // (it lives in the other parity's key buffer until the first scatter)
-        uint64_t k0, k1;
-        load_key2_o(R, i, off, 0, k0, k1);
+        uint64_t k0, k1 = 0;
+        if (A && R.alpha) k0 = key_at<A>(R, i, off, 0);   // no shared-prefix step for compressed keys
+        else load_key2_o(R, i, off, 0, k0, k1);
         key0[g] = k0;
         next0[g] = k1;
         if (i == 0) {
@@ -696,7 +700,7 @@ struct ScatterSmem {
     uint32_t sidx[kTile + 8];    // the tile's string indices (range rounded out to 16 bytes)
     uint32_t tbase[MB + 1];   // global position of each bucket's first string from this tile
     uint16_t lbase[MB + 1];   // tile-local start of each bucket (exclusive scan of the tile's counts)
-    uint16_t binfo[MB + 1];   // delta | final << 4 | done << 5 | first tile << 6 | nulpos << 8
+    uint16_t binfo[MB + 1];   // delta | final << 6 | done << 7 | first tile << 8 | key length << 9
     uint16_t slot_b[kTile];      // bucket of each tile-local slot
     uint16_t src[kTile];         // tile element held by each slot
     uint32_t wcnt[kWarps];
@@ -709,6 +713,13 @@ static_assert(offsetof(ScatterSmem<kMaxD>, bar) % 8 == 0 && offsetof(ScatterSmem
               "mbarriers 8-byte aligned");
 
 enum { MODE_SORT = 0, MODE_CLASSIFY = 1 };
+
+// bucket facts of the scatter (ScatterSmem::binfo): the depth step (up to the
+// 32 characters of a compressed key), final (placed now), done (all equal and
+// complete), the bucket's first tile, and the characters of the string in the
+// equality bucket's key
+constexpr uint32_t BI_DELTA = 0x3Fu, BI_FIN = 1u << 6, BI_DONE = 1u << 7, BI_FIRST = 1u << 8;
+constexpr int BI_NP = 9;
 
 // position of (bucket b, tile tl) from the scanned counters
 __device__ __forceinline__ uint32_t tile_pos(const BigSeg &sg, const uint32_t *scan, uint32_t b, uint32_t tl) {
@@ -829,18 +840,20 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
                 }
                 S.tbase[b] = tb[k];
                 if (MODE == MODE_SORT) {
+                    const ReqDesc &RQ = reqs[sg.req];
                     uint32_t r = b >> 1;
                     uint32_t delta, done = 0, np = 0;
                     if (b & 1) {
-                        np = nulpos(xr[k]);
-                        done = np < 8;   // equal keys that hold the end of the string: all equal
-                        delta = 8;
+                        np = key_len(RQ, xr[k], sg.depth);
+                        done = key_ends(RQ, xr[k], sg.depth);   // equal keys that hold the end of the string: all equal
+                        delta = key_chars(RQ);
                     } else {
-                        delta = even_delta(xl[k], xr[k], r, v, req_min_step(reqs[sg.req]));
+                        delta = even_delta(RQ, xl[k], xr[k], r, v, req_min_step(RQ));
                     }
                     uint32_t fin = (en[k] - st[k] == 1) || done;
                     uint32_t first = tb[k] == st[k];
-                    S.binfo[b] = (uint16_t)(delta | (fin << 4) | (done << 5) | (first << 6) | (np << 8));
+                    S.binfo[b] = (uint16_t)(delta | (fin ? BI_FIN : 0u) | (done ? BI_DONE : 0u) | (first ? BI_FIRST : 0u) |
+                                            (np << BI_NP));
                 }
             }
             S.lbase[b] = (uint16_t)run;
@@ -913,11 +926,11 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
         const uint32_t id = S.sidx[ioff + S.src[s]];
         const uint32_t info = S.binfo[b];
-        if (info & 16u) {
+        if (info & BI_FIN) {
             const uint32_t local = q - R.base;
             R.perm_out[local] = id;
             // all equal and complete: every string but the bucket's first has the whole key in common
-            if ((info & 32u) && (!(info & 64u) || lo > 0)) R.lcp_out[local] = sg.depth + (info >> 8);
+            if ((info & BI_DONE) && (!(info & BI_FIRST) || lo > 0)) R.lcp_out[local] = sg.depth + (info >> BI_NP);
         } else {
             idx_out[q] = id;
         }
@@ -930,7 +943,7 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
         const uint32_t b = S.slot_b[s];
         const uint32_t info = S.binfo[b];
-        if (info & 31u) continue;   // final, or a new depth
+        if (info & (BI_FIN | BI_DELTA)) continue;   // final, or a new depth
         const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
         if (q < sg.begin || q >= seg_end) continue;
         key_out[q] = S.u.buf[koff + S.src[s]];
@@ -947,7 +960,7 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     }
     for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
         const uint32_t b = S.slot_b[s];
-        if (S.binfo[b] & 16u) continue;
+        if (S.binfo[b] & BI_FIN) continue;
         const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
         if (q < sg.begin || q >= seg_end) continue;
         soff_out[q] = S.u.buf[koff + S.src[s]];
@@ -991,12 +1004,13 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
     uint32_t size = en - st;
     if (size == 1) return;
     const uint64_t *xs = splitters + (size_t)si * kMaxV;
+    const ReqDesc &RQ = reqs[sg.req];
     uint32_t r = b >> 1, delta;
     if (b & 1) {
-        if (has_zero(xs[r])) return;   // all equal and complete: placed by k_scatter
-        delta = 8;
+        if (key_ends(RQ, xs[r], sg.depth)) return;   // all equal and complete: placed by k_scatter
+        delta = key_chars(RQ);
     } else {
-        delta = even_delta(r > 0 ? xs[r - 1] : 0ull, r < v ? xs[r] : 0ull, r, v, req_min_step(reqs[sg.req]));
+        delta = even_delta(RQ, r > 0 ? xs[r - 1] : 0ull, r < v ? xs[r] : 0ull, r, v, req_min_step(RQ));
     }
     uint32_t depth = sg.depth + delta;
     const bool regather = delta != 0;
@@ -1031,6 +1045,7 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
 
 // the next keys of every gather chunk of the level (a fixed grid walks the
 // chunk list, whose length is read on the device)
+template <bool A>
 __global__ void __launch_bounds__(256) k_gather_new(const GatherChunk *__restrict__ gchunks, const uint32_t *nchunks_dev,
                                                     const ReqDesc *__restrict__ reqs, const uint32_t *__restrict__ idx,
                                                     const uint64_t *__restrict__ soff, uint64_t *__restrict__ key) {
@@ -1050,7 +1065,7 @@ __global__ void __launch_bounds__(256) k_gather_new(const GatherChunk *__restric
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const uint32_t p = g.begin + u * 256 + threadIdx.x;
-            if (p < g.end) key[p] = load_key_o(R, id[u], so[u], g.depth);
+            if (p < g.end) key[p] = key_at<A>(R, id[u], so[u], g.depth);
         }
     }
 }
@@ -1059,14 +1074,15 @@ __global__ void __launch_bounds__(256) k_gather_new(const GatherChunk *__restric
 
 // ------------------------------------------------------------ k_boundary
 
+template <bool A>
 __global__ void k_boundary(const Boundary *bounds, uint32_t nb, const ReqDesc *reqs) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
         Boundary b = bounds[k];
         const ReqDesc &R = reqs[b.req];
         uint32_t lp = b.pos - R.base;
         uint32_t sa = R.perm_out[lp - 1], sb = R.perm_out[lp];
-        uint64_t ka = load_key(R, sa, b.depth), kb = load_key(R, sb, b.depth);
-        R.lcp_out[lp] = b.depth + lcp8(ka, kb);
+        uint64_t ka = key_at<A>(R, sa, __ldg(R.offsets + sa), b.depth), kb = key_at<A>(R, sb, __ldg(R.offsets + sb), b.depth);
+        R.lcp_out[lp] = b.depth + key_lcp<A>(R, ka, kb);
     }
 }
 
@@ -1130,7 +1146,30 @@ static std::atomic<bool> g_attrs_done[64];
 static std::mutex g_attrs_mu;
 // CTAs of each base-case class that are resident on the device at once
 // (occupancy of its kernel times the SMs), set with the attributes
-static uint32_t g_base_grid[kClasses];
+static uint32_t g_base_grid[2][kClasses];   // [some request compressed][class]
+
+// runs f with std::true_type when some request of the call uses alphabet
+// compression, with std::false_type otherwise (the kernels' template choice)
+template <typename F>
+static void with_alpha(bool any_alpha, F f) {
+    if (any_alpha) f(std::true_type{});
+    else f(std::false_type{});
+}
+
+template <bool A>
+static cudaError_t base_attrs() {
+    cudaError_t e;
+    if ((e = set_smem_max(k_base_cta<SS_C1_NT, 256 / SS_C1_NT, A>, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>)))) return e;
+    if ((e = set_smem_max(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT, A>, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>)))) return e;
+    if ((e = set_smem_max(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT, A>, sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>))))
+        return e;
+    g_base_grid[A][1] = resident_grid(k_base_cta<SS_C1_NT, 256 / SS_C1_NT, A>, SS_C1_NT, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>));
+    g_base_grid[A][2] = resident_grid(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT, A>, SS_C2_NT,
+                                      sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>));
+    g_base_grid[A][3] = resident_grid(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT, A>, SS_C3_NT,
+                                      sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>));
+    return cudaSuccess;
+}
 
 template <typename K>
 static uint32_t resident_grid(K kernel, int threads, size_t smem) {
@@ -1171,13 +1210,8 @@ static cudaError_t ensure_attrs() {
     if ((e = set_smem_max(k_scatter<MODE_SORT, kLevelD>, sizeof(ScatterSmem<kLevelD>)))) return e;
     if ((e = set_smem_max(k_scatter<MODE_CLASSIFY, kLevelD>, sizeof(ScatterSmem<kLevelD>)))) return e;
     if ((e = set_smem_max(k_scatter<MODE_CLASSIFY, kMaxD>, sizeof(ScatterSmem<kMaxD>)))) return e;
-    if ((e = set_smem_max(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>)))) return e;
-    if ((e = set_smem_max(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>)))) return e;
-    if ((e = set_smem_max(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>)))) return e;
-    g_base_grid[1] = resident_grid(k_base_cta<SS_C1_NT, 256 / SS_C1_NT>, SS_C1_NT, sizeof(BaseSmem<SS_C1_NT, 256 / SS_C1_NT>));
-    g_base_grid[2] = resident_grid(k_base_cta<SS_C2_NT, 1024 / SS_C2_NT>, SS_C2_NT, sizeof(BaseSmem<SS_C2_NT, 1024 / SS_C2_NT>));
-    g_base_grid[3] = resident_grid(k_base_cta<SS_C3_NT, kSmallMax / SS_C3_NT>, SS_C3_NT,
-                                   sizeof(BaseSmem<SS_C3_NT, kSmallMax / SS_C3_NT>));
+    if ((e = base_attrs<false>())) return e;
+    if ((e = base_attrs<true>())) return e;
     if (dev < 64) g_attrs_done[dev] = true;
     return cudaSuccess;
 }
@@ -1307,9 +1341,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     int rc = SS_OK;
     bool any_status = false;   // some request wants its status written on the device
     bool any_jump = false;     // some request classifies with jump tables
+    bool any_alpha = false;    // some request uses alphabet compression
     for (const ReqDesc &q : reqs) {
         any_status = any_status || q.status_out;
         any_jump = any_jump || req_classifier(q) == CLS_JUMP;
+        any_alpha = any_alpha || q.alpha;
     }
     // initial segments: one per request
     std::vector<BigSeg> big0;
@@ -1342,9 +1378,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         cudaError_t _e = (x);                            \
         if (_e != cudaSuccess) { rc = cuda_fail(_e, what); goto done; } \
     } while (0)
-    for (const BigSeg &b : big0)
+    for (const BigSeg &b : big0) {
+        if (reqs[b.req].alpha) continue;   // compressed keys start at depth 0
         for (uint32_t x = 0; x < b.size; x += kPrefChunk)
             pchunk_host.push_back(make_uint4(b.begin + x, b.begin + std::min(b.size, x + kPrefChunk), b.req, 0));
+    }
     // Everything the first launches read goes up from one pinned staging
     // buffer, asynchronously; the counter readbacks land in its own tail.
     uint32_t *hc;
@@ -1373,8 +1411,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
     }
     {
         uint32_t grid = (uint32_t)std::min<uint64_t>((N + 255) / 256, (uint64_t)sm_count() * 8);
-        SS_LAUNCH_U("init", st, N, k_init<<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0], key[0], key[1]));
-        if (!big0.empty()) {
+        with_alpha(any_alpha, [&](auto A) {
+            SS_LAUNCH_U("init", st, N, k_init<decltype(A)::value><<<grid, 256, 0, st>>>(dreqs, nreq, N, idx[0], soff[0],
+                                                                                        key[0], key[1]));
+        });
+        if (!pchunk_host.empty()) {
             const uint32_t nch = (uint32_t)pchunk_host.size();
             TRY(cudaMemsetAsync(shared, 0xFF, sizeof(uint32_t) * nreq, st), "reset shared prefix");
             SS_LAUNCH_U("shared_prefix", st, elems0, k_shared_prefix<<<nch, 256, 0, st>>>(pchunks, dreqs, key[0], shared));
@@ -1414,8 +1455,10 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
             SS_LAUNCH_U("buckets", st, npairs, k_buckets<<<(npairs + kThreads - 1) / kThreads, kThreads, 0, st>>>(
                 big[cur], nbig, dreqs, counters + C_LVL_PAIRS, counts, splitters, nxt, big[nxt], tl, bounds, gchunks,
                 caps, counters));
-            SS_LAUNCH_U("gather_new", st, nelems, k_gather_new<<<sm_count() * 8, 256, 0, st>>>(
-                gchunks, counters + C_NGATHER, dreqs, idx[nxt], soff[nxt], key[nxt]));
+            with_alpha(any_alpha, [&](auto A) {
+                SS_LAUNCH_U("gather_new", st, nelems, k_gather_new<decltype(A)::value><<<sm_count() * 8, 256, 0, st>>>(
+                    gchunks, counters + C_NGATHER, dreqs, idx[nxt], soff[nxt], key[nxt]));
+            });
             TRY(cudaGetLastError(), "level launch");
             TRY(cudaMemcpyAsync(hc, counters, sizeof(uint32_t) * C_NUM, cudaMemcpyDeviceToHost, st), "readback");
             TRY(cudaStreamSynchronize(st), "level sync");
@@ -1456,21 +1499,33 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         // tasks from the class's work queue (head in the counters)
         if (uint32_t n3 = hc[C_NTASK + 3]) {
             constexpr int NT = SS_C3_NT, IT = (int)(kSmallMax / SS_C3_NT);
-            uint32_t grid = std::min<uint32_t>(n3, g_base_grid[3]);
-            SS_LAUNCH_U("base_c3", st, hc[C_ETASK + 3], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), st>>>(
-                L[3], counters + C_NTASK + 3, counters + C_QHEAD + 3, dreqs, eb, L[0], tl.cap[0], counters)));
+            uint32_t grid = std::min<uint32_t>(n3, g_base_grid[any_alpha][3]);
+            with_alpha(any_alpha, [&](auto A) {
+                SS_LAUNCH_U("base_c3", st, hc[C_ETASK + 3],
+                            (k_base_cta<NT, IT, decltype(A)::value><<<grid, NT, sizeof(BaseSmem<NT, IT>), st>>>(
+                                L[3], counters + C_NTASK + 3, counters + C_QHEAD + 3, dreqs, eb, L[0], tl.cap[0],
+                                counters)));
+            });
         }
         if (uint32_t n2 = hc[C_NTASK + 2]) {
             constexpr int NT = SS_C2_NT, IT = (int)(1024 / SS_C2_NT);
-            uint32_t grid = std::min<uint32_t>(n2, g_base_grid[2]);
-            SS_LAUNCH_U("base_c2", s1, hc[C_ETASK + 2], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s1>>>(
-                L[2], counters + C_NTASK + 2, counters + C_QHEAD + 2, dreqs, eb, L[0], tl.cap[0], counters)));
+            uint32_t grid = std::min<uint32_t>(n2, g_base_grid[any_alpha][2]);
+            with_alpha(any_alpha, [&](auto A) {
+                SS_LAUNCH_U("base_c2", s1, hc[C_ETASK + 2],
+                            (k_base_cta<NT, IT, decltype(A)::value><<<grid, NT, sizeof(BaseSmem<NT, IT>), s1>>>(
+                                L[2], counters + C_NTASK + 2, counters + C_QHEAD + 2, dreqs, eb, L[0], tl.cap[0],
+                                counters)));
+            });
         }
         if (uint32_t n1 = hc[C_NTASK + 1]) {
             constexpr int NT = SS_C1_NT, IT = (int)(256 / SS_C1_NT);
-            uint32_t grid = std::min<uint32_t>(n1, g_base_grid[1]);
-            SS_LAUNCH_U("base_c1", s2, hc[C_ETASK + 1], (k_base_cta<NT, IT><<<grid, NT, sizeof(BaseSmem<NT, IT>), s2>>>(
-                L[1], counters + C_NTASK + 1, counters + C_QHEAD + 1, dreqs, eb, L[0], tl.cap[0], counters)));
+            uint32_t grid = std::min<uint32_t>(n1, g_base_grid[any_alpha][1]);
+            with_alpha(any_alpha, [&](auto A) {
+                SS_LAUNCH_U("base_c1", s2, hc[C_ETASK + 1],
+                            (k_base_cta<NT, IT, decltype(A)::value><<<grid, NT, sizeof(BaseSmem<NT, IT>), s2>>>(
+                                L[1], counters + C_NTASK + 1, counters + C_QHEAD + 1, dreqs, eb, L[0], tl.cap[0],
+                                counters)));
+            });
         }
         if (fork) {
             TRY(cudaEventRecord(ax.ev[1], s1), "join");
@@ -1480,12 +1535,17 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st) {
         }
         if (hc[C_NTASK + 0] || hc[C_NTASK + 1] || hc[C_NTASK + 2] || hc[C_NTASK + 3]) {
             uint32_t grid = sms * 8;
-            SS_LAUNCH_U("base_warp", st, hc[C_ETASK + 0], k_small_warp<<<grid, kThreads, 0, st>>>(L[0], counters + C_NTASK + 0, dreqs, eb));
+            with_alpha(any_alpha, [&](auto A) {
+                SS_LAUNCH_U("base_warp", st, hc[C_ETASK + 0], k_small_warp<decltype(A)::value><<<grid, kThreads, 0, st>>>(
+                    L[0], counters + C_NTASK + 0, dreqs, eb));
+            });
         }
         TRY(cudaGetLastError(), "base case launch");
         if (nb) {
             uint32_t grid = std::min<uint32_t>((nb + 255) / 256, sms * 8);
-            SS_LAUNCH_U("boundary", st, nb, k_boundary<<<grid, 256, 0, st>>>(bounds, nb, dreqs));
+            with_alpha(any_alpha, [&](auto A) {
+                SS_LAUNCH_U("boundary", st, nb, k_boundary<decltype(A)::value><<<grid, 256, 0, st>>>(bounds, nb, dreqs));
+            });
             TRY(cudaGetLastError(), "boundary launch");
         }
         if (any_status) {

@@ -71,6 +71,8 @@ struct ReqDesc {
     uint32_t *perm_out;
     uint32_t *lcp_out;
     int32_t *status_out;
+    uint32_t alpha;            // 0: keys of 8 bytes; else the sorted alphabet a0..a3 (bytes 0..3, a0 >= 1) of a
+                               // fixed-length request: keys of 32 characters, 2 bits each (alphabet compression)
 };
 
 // Per-request tuning: the segment size the tree depth aims at for children,
@@ -202,6 +204,45 @@ __device__ __forceinline__ uint32_t lcp8(uint64_t a, uint64_t b) {
     return x ? (uint32_t)(__clzll(x) >> 3) : 8u;
 }
 
+// 2-bit codes of 4 bytes (byte 0 = first character) against the sorted
+// alphabet a0 <= a1 <= a2 (each replicated in 4 bytes): code = #{a_i < c},
+// first character in bits 7..6
+__device__ __forceinline__ uint32_t code8(uint32_t x, uint32_t a0, uint32_t a1, uint32_t a2) {
+    const uint32_t m = (__vcmpgtu4(x, a0) & 0x01010101u) + (__vcmpgtu4(x, a1) & 0x01010101u) +
+                       (__vcmpgtu4(x, a2) & 0x01010101u);
+    return ((m & 3u) << 6) | ((m >> 4) & 0x30u) | ((m >> 14) & 0x0Cu) | ((m >> 24) & 0x03u);
+}
+
+// Alphabet-compressed key of a fixed-length string: characters [h, h + 32) as
+// 2-bit codes, first character in the top bits; positions past the end get
+// code 0, the same for every string of the request (all have the same length).
+// Reads the aligned words that hold the characters, at most five.
+__device__ __forceinline__ uint64_t load_key_packed(const ReqDesc &R, uint64_t off, uint32_t h) {
+    const uint32_t L = R.fixed_len;
+    if (h >= L) return 0ull;
+    const uint32_t nb = min(32u, L - h);
+    const uintptr_t a = (uintptr_t)(R.chars + off + h);
+    const uint64_t *w = (const uint64_t *)(a & ~(uintptr_t)7);
+    const uint32_t lead = (uint32_t)(a & 7), span = lead + nb, sh = 8 * lead;
+    uint64_t W[5];
+#pragma unroll
+    for (int j = 0; j < 5; j++) W[j] = (uint32_t)(8 * j) < span ? __ldg(w + j) : 0ull;
+    const uint32_t a0 = (R.alpha & 0xFFu) * 0x01010101u, a1 = ((R.alpha >> 8) & 0xFFu) * 0x01010101u,
+                   a2 = ((R.alpha >> 16) & 0xFFu) * 0x01010101u;
+    uint64_t key = 0;
+#pragma unroll
+    for (int i = 0; i < 4; i++) {
+        uint64_t v = sh ? (W[i] >> sh) | (W[i + 1] << (64 - sh)) : W[i];   // bytes 8i .. 8i+7 of the window
+        const int left = (int)nb - 8 * i;                                   // of which this many belong to the string
+        if (left < 8) {
+            const uint64_t keep = left <= 0 ? 0ull : (~0ull >> (64 - 8 * left));
+            v = (v & keep) | ((uint64_t)a0 * 0x100000001ull & ~keep);      // past the end: code 0
+        }
+        key = (key << 16) | (code8((uint32_t)v, a0, a1, a2) << 8) | code8((uint32_t)(v >> 32), a0, a1, a2);
+    }
+    return key;
+}
+
 // chars_h: 8 bytes of string i (starting at byte `off` of chars) at depth h,
 // big-endian, zero past the end.  Reads the aligned word holding byte h, and
 // the next aligned word when the string continues into it.  For a terminated
@@ -314,6 +355,57 @@ __device__ __forceinline__ void load_key2_o(const ReqDesc &R, uint32_t i, uint64
 
 __device__ __forceinline__ void load_key2(const ReqDesc &R, uint32_t i, uint32_t h, uint64_t &k0, uint64_t &k1) {
     load_key2_o(R, i, __ldg(R.offsets + i), h, k0, k1);
+}
+
+// Keys of a request that may use alphabet compression.  Kernels that load keys
+// take A = true only when some request of the call is compressed, so byte-key
+// calls run code without the compressed path.
+template <bool A>
+__device__ __forceinline__ uint64_t key_at(const ReqDesc &R, uint32_t i, uint64_t off, uint32_t h) {
+    if (A && R.alpha) return load_key_packed(R, off, h);
+    return load_key_o(R, i, off, h);
+}
+
+// two consecutive keys: 16 bytes, or 64 compressed characters
+template <bool A>
+__device__ __forceinline__ void key2_at(const ReqDesc &R, uint32_t i, uint64_t off, uint32_t h, uint64_t &k0,
+                                        uint64_t &k1) {
+    if (A && R.alpha) {
+        k0 = load_key_packed(R, off, h);
+        k1 = load_key_packed(R, off, h + 32);
+        return;
+    }
+    load_key2_o(R, i, off, h, k0, k1);
+}
+
+// ------------------------------------------------- key width of a request
+// Characters per key: 8 bytes, or 32 two-bit codes for a request with an
+// alphabet of at most four characters (alphabet compression, Section 8.1).
+// Depths and LCPs stay in characters either way.
+// With A = false the request is known to use byte keys (the kernel variant
+// for calls without compressed requests), so no test of R.alpha is made.
+template <bool A = true>
+__host__ __device__ __forceinline__ uint32_t key_chars(const ReqDesc &R) { return (A && R.alpha) ? 32u : 8u; }
+
+// characters two keys at the same depth have in common (key_chars if equal)
+template <bool A = true>
+__device__ __forceinline__ uint32_t key_lcp(const ReqDesc &R, uint64_t a, uint64_t b) {
+    const uint64_t x = a ^ b;
+    if (!x) return key_chars<A>(R);
+    return (uint32_t)__clzll((long long)x) >> ((A && R.alpha) ? 1 : 3);
+}
+
+// the key of a string at `depth` reaches the string's end
+template <bool A = true>
+__device__ __forceinline__ bool key_ends(const ReqDesc &R, uint64_t key, uint32_t depth) {
+    return (A && R.alpha) ? depth + 32u >= R.fixed_len : has_zero(key);
+}
+
+// characters of the string inside its key at `depth` (key_chars if it goes on)
+template <bool A = true>
+__device__ __forceinline__ uint32_t key_len(const ReqDesc &R, uint64_t key, uint32_t depth) {
+    if (!(A && R.alpha)) return nulpos(key);
+    return depth >= R.fixed_len ? 0u : min(32u, R.fixed_len - depth);
 }
 
 __device__ __forceinline__ uint64_t mix64(uint64_t z) {   // splitmix64 finaliser

@@ -28,7 +28,7 @@ def test_library_builds_and_exports_all_symbols():
     lib = ctypes.CDLL(so)
     for name in _declared():
         assert hasattr(lib, name), name
-    assert lib.ss_version() == 100
+    assert lib.ss_version() == 101
 
 
 def test_binding_has_same_names():
@@ -68,7 +68,9 @@ def test_tuning_ranges_checked_on_the_host():
     import paper_1403_2056_gb300 as P
     q = P.Request(1, 1, None, 0, 5, 1, 1, None)   # pointers are never dereferenced: the check fails first
     arr = (P.Request * 1)(q)
-    for bad in [(48, 0, 0), (16, 0, 0), (1 << 17, 0, 0), (0, 10, 0), (0, 0, 3)]:
+    # alphabets: unsorted, a zero byte, or a request that is not fixed-length (q is NUL-terminated)
+    for bad in [(48, 0, 0), (16, 0, 0), (1 << 17, 0, 0), (0, 10, 0), (0, 0, 3), (0, 0, 0, 0x41434700),
+                (0, 0, 0, 0x41474341), (0, 0, 0, 0x54474341)]:
         t = (P.Tuning * 1)(P.Tuning(*bad))
         rc = P.lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), C.cast(t, C.c_void_p), 1, None)
         assert rc == -1, bad

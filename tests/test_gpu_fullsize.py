@@ -95,3 +95,22 @@ def test_batch_of_mixed_requests():
         want_perm, want_lcp = oracle.sort(ss)
         assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm), ss.name
         assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp), ss.name
+
+
+def test_dna_windows_20m_alphabet_compressed():
+    """The same 20,000,000 DNA windows with alphabet compression (2-bit codes,
+    32 characters per key): every position checked, and the arrays equal the
+    byte-key sort's."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = W.dna_windows(n=20_000_000, text_len=400_000_000, window=100, seed=3)
+    chars, offsets, _ = to_device(ss)
+    perm, lcp = gpu_sort(ss, chars, offsets, None)
+    cp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    cl = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    P.ss_sort_batch_tuned([dict(chars=chars, offsets=offsets, lengths=None, fixed_len=100, n=ss.n, perm_out=cp,
+                                lcp_out=cl)], [(0, 0, 0, P.alphabet(b"ACGT"))])
+    torch.cuda.synchronize()
+    cperm, clcp = cp.cpu().numpy().view(np.uint32), cl.cpu().numpy().view(np.uint32)
+    _assert_sorted(ss, cperm, clcp)
+    assert np.array_equal(cperm, perm) and np.array_equal(clcp, lcp)

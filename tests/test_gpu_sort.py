@@ -511,3 +511,54 @@ def test_loser_tree_merge_edge_cases(K):
     want_perm, want_lcp = oracle.sort(ss)
     assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
     assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
+
+
+def _sort_tuned(reqs_ss, tunings):
+    import torch
+    import paper_1403_2056_gb300 as P
+    reqs, outs = [], []
+    for ss in reqs_ss:
+        chars, offsets, lengths = to_device(ss)
+        perm = torch.full((max(ss.n, 1),), -1, dtype=torch.int32, device="cuda:0")
+        lcp = torch.full((max(ss.n, 1),), -1, dtype=torch.int32, device="cuda:0")
+        reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=ss.n,
+                         perm_out=perm, lcp_out=lcp))
+        outs.append((perm, lcp))
+    P.ss_sort_batch_tuned(reqs, tunings)
+    torch.cuda.synchronize()
+    return [(p[:ss.n].cpu().numpy().view(np.uint32), l[:ss.n].cpu().numpy().view(np.uint32))
+            for (p, l), ss in zip(outs, reqs_ss)]
+
+
+@pytest.mark.parametrize("window", [1, 7, 31, 32, 33, 64, 65, 100])
+def test_alphabet_compressed_dna_windows(window):
+    """Alphabet compression (2-bit codes, 32 characters per key) on DNA windows
+    whose length falls below, on and across key boundaries, with many
+    duplicate windows (short text), against the oracle."""
+    import paper_1403_2056_gb300 as P
+    ss = W.dna_windows(60_000, 3_000 + window, window, seed=window)
+    (perm, lcp), = _sort_tuned([ss], [(0, 0, 0, P.alphabet(b"ACGT"))])
+    want_perm, want_lcp = oracle.sort(ss)
+    assert np.array_equal(perm, want_perm)
+    assert np.array_equal(lcp, want_lcp)
+
+
+def test_alphabet_compressed_small_alphabets_and_mixed_batch():
+    """One batch mixing compressed requests (alphabets of 2 and 4 bytes, windows
+    over one text) with plain ones (the same windows without compression, a
+    URL-like set, tiny requests): every request equals the oracle's sort."""
+    import paper_1403_2056_gb300 as P
+    rng = np.random.default_rng(7)
+    text = np.frombuffer(b"AC", np.uint8)[rng.integers(0, 2, 20_000)]
+    two = W.StringSet(np.concatenate([text, np.zeros(16, np.uint8)]),
+                      rng.integers(0, text.size - 40, 30_000).astype(np.uint64), None, 40, "ac_windows")
+    dna = W.dna_windows(50_000, 200_000, 100, seed=11)
+    url = W.url_like(40_000, seed=12)
+    tiny = W.dna_windows(3, 50, 20, seed=13)
+    sets = [two, dna, url, dna, tiny]
+    tun = [(0, 0, 0, P.alphabet(b"AC")), (0, 0, 0, P.alphabet(b"ACGT")), (0, 0, 0, 0), (0, 0, 0, 0),
+           (0, 0, 0, P.alphabet(b"ACGT"))]
+    for (perm, lcp), ss in zip(_sort_tuned(sets, tun), sets):
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(perm, want_perm), ss.name
+        assert np.array_equal(lcp, want_lcp), ss.name
