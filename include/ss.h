@@ -15,9 +15,17 @@
  *     library never frees or retains them past the call.  Pointers named
  *     *_host are host pointers.
  *   - `stream` is a cudaStream_t (may be NULL for the legacy default stream).
- *     Work is ordered on that stream.  The sort entry points read small
- *     counters back between recursion levels, so they return only after the
- *     sort has finished on `stream`; outputs are then complete.
+ *     Work is ordered on that stream.  ss_sort_batch_async only queues its
+ *     sort on `stream` and returns: the recursion is driven on the device (a
+ *     scheduler kernel launches every level's kernels from the device, the
+ *     paper's job queue of Section 4.5 kept in device memory), outputs are
+ *     complete when `stream` reaches that point, and a device-side failure is
+ *     written to each request's status_out and recorded for ss_device_error.
+ *     The other sort entry points drive the levels from the host, reading a
+ *     few counters back between levels, and return when the sort is done: on
+ *     GB300 that measured faster at every size (kernels launched from the
+ *     device start about 12 us after the one before).  ss_merge, ss_merge_ex,
+ *     ss_autotune and the single-step entry points return when done.
  *   - Scratch memory comes from a stream-ordered pool owned by the library
  *     (one per device, kept between calls); it is returned to the pool at the
  *     end of each call.
@@ -104,7 +112,8 @@ int ss_sort_host(const uint8_t *chars_host, uint64_t chars_len_host, const uint6
  * One independent sort request of a batch.  Fields as in ss_sort_ex; all
  * pointers are device pointers.  status_out may be NULL; otherwise the
  * library writes an int32 ss_status there on the device, in stream order:
- * SS_OK when the request's outputs are complete, SS_ERR_INTERNAL when a
+ * SS_OK when the request's outputs are complete, SS_ERR_TIMEOUT when a
+ * bounded device-side wait of the batch gave up, SS_ERR_INTERNAL when a
  * device-side check of the batch failed.  Argument errors are reported by
  * the return value alone, before anything is written.
  */
@@ -181,6 +190,19 @@ typedef struct {
  * for a tuning outside the ranges above.
  */
 int ss_sort_batch_tuned(const ss_request *reqs_host, const ss_tuning *tunings_host, uint32_t count,
+                        ss_stream_t stream);
+
+/*
+ * ss_sort_batch_async -- ss_sort_batch_tuned (tunings_host may be NULL) that
+ * returns as soon as the sort is queued on `stream`, with no host wait inside:
+ * every recursion level is launched from the device by a scheduler kernel,
+ * from the segment and task lists in device memory.  Results are those of
+ * ss_sort_batch.  Each request's status_out (if given) receives SS_OK,
+ * SS_ERR_TIMEOUT or SS_ERR_INTERNAL in stream order; ss_device_error reports
+ * a failure of any request afterwards.  While kernel timing is on
+ * (ss_profile_enable) it behaves as ss_sort_batch_tuned.
+ */
+int ss_sort_batch_async(const ss_request *reqs_host, const ss_tuning *tunings_host, uint32_t count,
                         ss_stream_t stream);
 
 /*
@@ -389,6 +411,28 @@ uint64_t ss_scratch_bytes(uint32_t n);
  * count = 0 switches injection off.  Nothing is injected on the device.
  */
 int ss_debug_fail_allocs(uint32_t skip, uint32_t count);
+
+/*
+ * ss_device_error -- the first device-side failure (SS_ERR_TIMEOUT or
+ * SS_ERR_INTERNAL) of any asynchronous sort since the last call, or SS_OK;
+ * the record is cleared.  Synchronize the sorts' streams first.  One record
+ * for the whole process: with sorts on several streams or threads it tells
+ * that one of them failed, each request's status_out tells which.
+ */
+int ss_device_error(int32_t *status_out_host);
+
+/*
+ * ss_debug_copy_wait -- for tests of the timeout path: the budget of every
+ * bounded wait for a bulk copy into shared memory in the distribution step
+ * (SM clock cycles; 0 restores the default of about a second), and, with
+ * withhold != 0, those copies are not issued at all, so every such wait runs
+ * out, the tile writes nothing, the sort stops after that level, the call
+ * returns SS_ERR_TIMEOUT (ss_sort_batch_async: its requests' status_out does)
+ * and each request's status_out reads it.  Nothing faults or hangs: no later
+ * kernel reads what the tile did not write.  Affects every sort of the
+ * process.
+ */
+int ss_debug_copy_wait(uint64_t budget_cycles, uint32_t withhold);
 
 /* Kernel timing: when enabled, the library records CUDA events around each of
  * its kernel launches (on the launch stream) and accumulates per-kernel time.

@@ -20,11 +20,11 @@ from . import build as _build
 
 __all__ = [
     "SortError", "lib", "library_path",
-    "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_ex",
+    "ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_sort_batch_async", "ss_merge", "ss_merge_ex",
     "MERGE_PAIRWISE", "MERGE_LOSER_TREE",
     "ss_merge_noalloc", "ss_gather_keys", "ss_splitters", "ss_classify", "ss_classify_ex",
     "CLASSIFIER_UNROLL", "CLASSIFIER_EQUAL", "CLASSIFIER_JUMP", "alphabet",
-    "profile_enable", "profile_reset", "profile_read", "launch_count",
+    "profile_enable", "profile_reset", "profile_read", "launch_count", "ss_device_error", "ss_debug_copy_wait",
     "STATUS",
 ]
 
@@ -83,18 +83,22 @@ def lib():
     L.ss_server_wait.argtypes = [vp, u64, C.POINTER(i32), C.POINTER(C.c_double)]
     L.ss_server_submit_host.argtypes = [vp, vp, C.POINTER(u64)]
     L.ss_sort_batch_tuned.argtypes = [vp, vp, u32, vp]
+    L.ss_sort_batch_async.argtypes = [vp, vp, u32, vp]
     L.ss_autotune.argtypes = [vp, u32, C.POINTER(Tuning), C.POINTER(C.c_double), vp]
     L.ss_server_destroy.argtypes = [vp]
     L.ss_server_cancel.argtypes = [vp, u64, C.POINTER(i32)]
     L.ss_debug_fail_allocs.argtypes = [u32, u32]
+    L.ss_debug_copy_wait.argtypes = [u64, u32]
+    L.ss_device_error.argtypes = [C.POINTER(i32)]
     L.ss_scratch_bytes.argtypes = [u32]
     L.ss_scratch_bytes.restype = u64
     for name in ("ss_sort", "ss_sort_ex", "ss_sort_host", "ss_sort_batch", "ss_merge", "ss_merge_ex", "ss_merge_noalloc",
                  "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_classify_ex", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
                  "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
-                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_autotune", "ss_server_cancel",
-                 "ss_debug_fail_allocs"):
+                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_sort_batch_async", "ss_autotune",
+                 "ss_server_cancel",
+                 "ss_debug_fail_allocs", "ss_debug_copy_wait", "ss_device_error"):
         getattr(L, name).restype = i32
     _lib = L
     return L
@@ -264,6 +268,27 @@ def _request(q):
                    _dev(q.get("status_out"), "int32", "status_out", 1))
 
 
+def _tuned_args(requests, tunings):
+    arr = (Request * max(1, len(requests)))()
+    for k, q in enumerate(requests):
+        arr[k] = _request(q)
+    tarr = None
+    if tunings is not None:
+        tarr = (Tuning * max(1, len(requests)))()
+        for k, t in enumerate(tunings):
+            tarr[k] = Tuning(int(t[0]), int(t[1]), int(t[2]) if len(t) > 2 else 0, int(t[3]) if len(t) > 3 else 0)
+    return arr, tarr
+
+
+def ss_sort_batch_async(requests, tunings=None, stream=None):
+    """As ss_sort_batch_tuned, but only queues the sort (levels launched from
+    the device): outputs and each request's status_out are complete when the
+    stream reaches this point.  The caller keeps the tensors alive until then."""
+    arr, tarr = _tuned_args(requests, tunings)
+    _check(lib().ss_sort_batch_async(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
+                                      len(requests), _stream(stream)))
+
+
 def ss_sort_batch_tuned(requests, tunings=None, stream=None):
     """As ss_sort_batch, with one (child_target, min_step[, classifier[, alphabet]]) tuple per request
     (0: default; alphabet from alphabet(b"ACGT") for fixed-length requests over at most four bytes)."""
@@ -337,6 +362,20 @@ def ss_debug_fail_allocs(skip: int, count: int):
     """Host-side fault injection for tests: after `skip` successful scratch
     allocations, the next `count` fail as an exhausted pool would (0: off)."""
     _check(lib().ss_debug_fail_allocs(int(skip), int(count)))
+
+
+def ss_device_error() -> int:
+    """The first device-side failure (ss_status code) of any asynchronous sort
+    since the last call, 0 if none; synchronize the sorts' streams first."""
+    v = C.c_int32()
+    _check(lib().ss_device_error(C.byref(v)))
+    return int(v.value)
+
+
+def ss_debug_copy_wait(budget_cycles: int, withhold: bool):
+    """Test hook of the timeout path (see include/ss.h): wait budget of the
+    distribution step's bulk copies, and whether the copies are withheld."""
+    _check(lib().ss_debug_copy_wait(int(budget_cycles), 1 if withhold else 0))
 
 
 class Server:

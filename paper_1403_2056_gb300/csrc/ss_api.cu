@@ -280,6 +280,13 @@ int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *off
         if ((e = cudaMemcpyAsync(perm_host, d_perm, 4ull * n, cudaMemcpyDeviceToHost, st))) break;
         if ((e = cudaMemcpyAsync(lcp_host, d_lcp, 4ull * n, cudaMemcpyDeviceToHost, st))) break;
         e = cudaStreamSynchronize(st);
+        if (!e) {
+            const int32_t dev = engine_take_device_error();
+            if (dev != SS_OK) {
+                set_error_detail("ss_sort_host: device-side failure %d", dev);
+                rc = dev;
+            }
+        }
     } while (0);
     if (e && rc == SS_OK) rc = cuda_fail(e, "ss_sort_host");
     scratch_free(block, st);
@@ -367,6 +374,24 @@ static int pack_tuning(const ss_tuning &t, ReqDesc &r, const char *who) {
     }
     out = s | (t.min_step << 8) | (t.classifier << 16);
     return SS_OK;
+}
+
+int ss_sort_batch_async(const ss_request *reqs, const ss_tuning *tunings, uint32_t count, ss_stream_t stream) {
+    t_detail.clear();
+    if (count == 0) return SS_OK;
+    if (!reqs) {
+        set_error_detail("ss_sort_batch_async: NULL request array");
+        return SS_ERR_INVALID;
+    }
+    std::vector<ReqDesc> v(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const ss_request &q = reqs[i];
+        v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
+        int rc = check_req(v[i], "ss_sort_batch_async");
+        if (rc == SS_OK && tunings) rc = pack_tuning(tunings[i], v[i], "ss_sort_batch_async");
+        if (rc != SS_OK) return rc;
+    }
+    return engine_sort(v.data(), count, as_stream(stream), true);
 }
 
 int ss_sort_batch_tuned(const ss_request *reqs, const ss_tuning *tunings, uint32_t count, ss_stream_t stream) {
@@ -557,6 +582,7 @@ int ss_profile_reset(void) {
     std::lock_guard<std::mutex> lk(g_prof_mu);
     g_prof.clear();
     g_launches.store(0);
+    engine_reset_device_launches();
     return SS_OK;
 }
 
@@ -578,7 +604,22 @@ int ss_profile_read(char *names48, uint64_t *launches, double *total_ms, uint64_
     return (int)g_prof.size();
 }
 
-uint64_t ss_launch_count(void) { return g_launches.load(); }
+uint64_t ss_launch_count(void) { return g_launches.load() + engine_device_launches(); }
+
+int ss_device_error(int32_t *status_out) {
+    t_detail.clear();
+    if (!status_out) {
+        set_error_detail("ss_device_error: NULL status_out");
+        return SS_ERR_INVALID;
+    }
+    *status_out = engine_take_device_error();
+    return SS_OK;
+}
+
+int ss_debug_copy_wait(uint64_t budget_cycles, uint32_t withhold) {
+    t_detail.clear();
+    return engine_debug_copy_wait((long long)std::min<uint64_t>(budget_cycles, (uint64_t)INT64_MAX), withhold ? 1u : 0u);
+}
 
 int ss_debug_fail_allocs(uint32_t skip, uint32_t count) {
     std::lock_guard<std::mutex> lk(g_inject_mu);

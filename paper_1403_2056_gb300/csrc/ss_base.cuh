@@ -20,7 +20,7 @@
 
 #include "ss_internal.cuh"
 
-namespace ss {
+// (no namespace of its own: included by ss_kernels.cuh inside the includer's)
 
 // ----------------------------------------------------------- warp finish
 struct WElem {
@@ -628,5 +628,3 @@ __global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const u
         __syncthreads();
     }
 }
-
-}  // namespace ss

@@ -162,6 +162,7 @@ enum DevError : uint32_t {
     E_BAD_POS = 5,
     E_COPY_TIMEOUT = 6,   // a bulk copy into shared memory did not complete within its wait budget
     E_GATHER_OVERFLOW = 7,
+    E_LAUNCH = 8,         // a launch from the device failed (info: the CUDA error)
 };
 
 struct Caps {                   // capacities of the scratch lists
@@ -175,6 +176,26 @@ struct GatherChunk {
     uint32_t begin, end, req, depth;
 };
 constexpr uint32_t kGatherChunk = 2048;   // positions per gather chunk
+
+struct SortPlan {               // everything the scheduler launches with, by value
+    const ReqDesc *reqs;
+    uint32_t nreq, N;
+    ElemBufs eb;
+    uint16_t *obuf;
+    uint32_t *counts, *partial;
+    uint64_t *splitters;
+    uint16_t *jt;
+    BigSeg *big[2];
+    TaskLists tl;
+    Boundary *bounds;
+    GatherChunk *gchunks;
+    Caps caps;
+    uint32_t *counters;
+    uint32_t cur;               // parity of the level to run
+    uint32_t levels;            // levels run so far
+    uint32_t any_jump, any_status, sms;
+    uint32_t base_grid[kClasses];
+};
 
 // ------------------------------------------------------------ device math
 __device__ __forceinline__ uint64_t bswap64(uint64_t x) {
@@ -472,11 +493,11 @@ __device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
 // kCopyWaitCycles SM clock cycles (about a second); returns false when the
 // budget ran out (the caller records E_COPY_TIMEOUT and skips the data).
 constexpr long long kCopyWaitCycles = 2000000000ll;
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long budget = kCopyWaitCycles) {
     if (mbar_test(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_test(bar, parity))
-        if (clock64() - t0 > kCopyWaitCycles) return false;
+        if (clock64() - t0 > budget) return false;
     return true;
 }
 
@@ -507,7 +528,8 @@ cudaError_t scratch_free(void *p, cudaStream_t s);
 void *host_staging(size_t bytes);
 
 // engine entry points (ss_engine.cu)
-int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream);
+// async: levels driven by the device scheduler, the call returns at once
+int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream, bool async = false);
 size_t engine_scratch_bytes(size_t N, uint32_t nreq);
 int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host, const uint32_t *lengths_host,
               uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host, uint32_t *lcp_host, cudaStream_t st);
@@ -515,6 +537,18 @@ int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_
                     uint16_t *bucket_out, uint32_t *bucket_begin_out, uint32_t *order_out, cudaStream_t st);
 int engine_splitters(const uint64_t *sample, uint32_t a, uint32_t d, uint64_t *x_out, cudaStream_t stream);
 int engine_gather(const ReqDesc &r, const uint32_t *depth, uint64_t *keys_out, cudaStream_t stream);
+// the device-driven level scheduler (ss_sched.cu): launches it for the sort the
+// plan describes (its base_grid is filled there), and its device words
+int sched_start(SortPlan plan, bool any_alpha, cudaStream_t stream);
+uint64_t sched_device_launches();
+void sched_reset_device_launches();
+int32_t sched_take_device_error();
+cudaError_t sched_copy_wait(long long budget_cycles, uint32_t withhold);
+uint64_t engine_device_launches();        // kernels launched from the device so far
+void engine_reset_device_launches();
+int32_t engine_take_device_error();       // first device-side failure since the last take (0: none)
+int engine_debug_copy_wait(long long budget_cycles, uint32_t withhold);
+void *async_staging(size_t bytes, cudaStream_t stream, cudaEvent_t *done);
 
 // merge methods (SS_MERGE_* of the C header)
 enum MergeMethod : uint32_t { MERGE_PAIRWISE = 0, MERGE_LOSER_TREE = 1 };

@@ -162,3 +162,44 @@ def test_undersized_device_buffers_refused_by_the_binding():
     P.ss_sort(chars, offsets, n, perm, lcp)
     torch.cuda.synchronize()
     assert _same(ss, perm, lcp)
+
+
+def test_bounded_copy_wait_runs_out_and_reports_timeout():
+    """The distribution step's waits for its bulk copies are bounded: with the
+    copies withheld (a flag nothing sets, as the test hook arranges) and a
+    short budget, every wait runs out and the sort stops after that level.
+    ss_sort_batch (levels driven from the host) returns SS_ERR_TIMEOUT and
+    writes it to the request's status; ss_sort_batch_async (levels driven from
+    the device) writes it to the status and ss_device_error reports it.  The
+    library sorts correctly once the hook is off."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    TIMEOUT = -4
+    ss = W.url_like(150_000, seed=71)
+    chars, offsets, _ = to_device(ss)
+    perm, lcp = _outs(torch, ss.n)
+    status = torch.full((1,), 99, dtype=torch.int32, device="cuda:0")
+    req = dict(chars=chars, offsets=offsets, n=ss.n, perm_out=perm, lcp_out=lcp, status_out=status)
+    P.ss_device_error()   # clear
+    try:
+        P.ss_debug_copy_wait(200_000, True)
+        P.ss_sort_batch_async([req])
+        torch.cuda.synchronize()
+        assert int(status.item()) == TIMEOUT
+        assert P.ss_device_error() == TIMEOUT
+        assert P.ss_device_error() == 0   # read and cleared
+        status.fill_(99)
+        with pytest.raises(P.SortError) as e:
+            P.ss_sort_batch([req])
+        assert e.value.status == TIMEOUT
+        torch.cuda.synchronize()
+        assert int(status.item()) == TIMEOUT
+    finally:
+        P.ss_debug_copy_wait(0, False)
+    for fn in (P.ss_sort_batch, P.ss_sort_batch_async):
+        status.fill_(99)
+        perm.fill_(-1)
+        fn([req])
+        torch.cuda.synchronize()
+        assert int(status.item()) == 0 and P.ss_device_error() == 0
+        assert _same(ss, perm, lcp)

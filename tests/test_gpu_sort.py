@@ -513,7 +513,7 @@ def test_loser_tree_merge_edge_cases(K):
     assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
 
 
-def _sort_tuned(reqs_ss, tunings):
+def _sort_tuned(reqs_ss, tunings, asynchronous=False):
     import torch
     import paper_1403_2056_gb300 as P
     reqs, outs = [], []
@@ -524,7 +524,7 @@ def _sort_tuned(reqs_ss, tunings):
         reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=ss.n,
                          perm_out=perm, lcp_out=lcp))
         outs.append((perm, lcp))
-    P.ss_sort_batch_tuned(reqs, tunings)
+    (P.ss_sort_batch_async if asynchronous else P.ss_sort_batch_tuned)(reqs, tunings)
     torch.cuda.synchronize()
     return [(p[:ss.n].cpu().numpy().view(np.uint32), l[:ss.n].cpu().numpy().view(np.uint32))
             for (p, l), ss in zip(outs, reqs_ss)]
@@ -562,3 +562,55 @@ def test_alphabet_compressed_small_alphabets_and_mixed_batch():
         want_perm, want_lcp = oracle.sort(ss)
         assert np.array_equal(perm, want_perm), ss.name
         assert np.array_equal(lcp, want_lcp), ss.name
+
+
+def test_async_sort_returns_before_the_sort_completes():
+    """ss_sort_batch_async only queues work: the recursion is driven by the
+    device, so the call returns well before the sort is done on the stream,
+    and the outputs are complete (and equal the oracle's) once the stream
+    reaches an event recorded after the call."""
+    import time
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = W.url_like(3_000_000, seed=73)
+    chars, offsets, _ = to_device(ss)
+    perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    stream = torch.cuda.current_stream()
+    status = torch.full((1,), 99, dtype=torch.int32, device="cuda:0")
+    req = [dict(chars=chars, offsets=offsets, n=ss.n, perm_out=perm, lcp_out=lcp, status_out=status)]
+    P.ss_sort_batch_async(req, stream=stream)   # warm-up: pool growth, attributes
+    torch.cuda.synchronize()
+    calls, gpu = [], []
+    for _ in range(3):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t0 = time.perf_counter()
+        P.ss_sort_batch_async(req, stream=stream)
+        calls.append((time.perf_counter() - t0) * 1e3)
+        e1.record(stream)
+        e1.synchronize()
+        gpu.append(e0.elapsed_time(e1))
+    assert min(calls) < 0.5 * min(gpu), (calls, gpu)
+    assert int(status.item()) == 0
+    want_perm, want_lcp = oracle.sort(ss)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
+    assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
+
+
+def test_device_and_host_driven_levels_agree():
+    """Levels driven by the device scheduler (ss_sort_batch_async) and by the
+    host (ss_sort_batch_tuned) give the same arrays, on a request that needs
+    many levels (long shared prefixes), URL-like and DNA-like requests, with
+    and without alphabet compression, and a batch of tiny requests."""
+    import paper_1403_2056_gb300 as P
+    sets = [W.from_bytes_list([b"p" * 200 + str(i % 977).encode() * 3 for i in range(20_000)]),
+            W.url_like(200_000, seed=74), W.dna_windows(100_000, 150_000, 100, seed=75),
+            W.dna_windows(100_000, 150_000, 100, seed=76)] + [W.random_lower(k, seed=k) for k in (0, 1, 2, 31, 300)]
+    tun = [(0, 0, 0, 0)] * 3 + [(0, 0, 0, P.alphabet(b"ACGT"))] + [(0, 0, 0, 0)] * 5
+    res = [_sort_tuned(sets, tun), _sort_tuned(sets, tun, asynchronous=True)]
+    for (p0, l0), (p1, l1), ss in zip(res[0], res[1], sets):
+        assert np.array_equal(p0, p1) and np.array_equal(l0, l1), ss.name
+        want_perm, want_lcp = oracle.sort(ss)
+        assert np.array_equal(p0, want_perm) and np.array_equal(l0, want_lcp), ss.name
