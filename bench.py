@@ -76,7 +76,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--n", type=int, default=10_000_000)
+    ap.add_argument("--workload", default="url_like", choices=sorted(WORKLOADS),
+                    help="the step's string set (default: the URL-like configuration)")
+    ap.add_argument("--n", type=int, default=0, help="strings (0: the workload's configuration size)")
     ap.add_argument("--runs", type=int, default=4)
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--no-e2e", action="store_true")
@@ -89,6 +91,9 @@ def parse():
     ap.add_argument("--e2e-inflight", type=int, default=6, help="host-request steps in flight end to end")
     ap.add_argument("--e2e-steps", type=int, default=0, help="steps of the end-to-end stream (0: max(30, --steps))")
     ap.add_argument("--serving-requests", type=int, default=20000)
+    ap.add_argument("--capture", action="store_true",
+                    help="for counter captures: only the warm-up steps, the timed steps and the profiled steps run "
+                         "(no sort-only calls), so every launch belongs to one of max(W, 3) + 2 K identical steps")
     return ap.parse_args()
 
 
@@ -137,13 +142,15 @@ def other_workloads(P, torch, dev, stream, peak):
         P.profile_enable(False)
         prof = P.profile_read()
         D, balg = d_and_balg(lcp.cpu().numpy().view(np.uint32))
-        dom = max(prof, key=lambda k: prof[k][1])
+        dom = max((k for k in prof if BYTES_PER_UNIT.get(k)), key=lambda k: prof[k][1])
         nl, tms, units = prof[dom]
         bpu = BYTES_PER_UNIT.get(dom)
         ach = units * bpu / (tms / 1e3) / 1e9 if bpu else None
         kinds = {"no_lcp_64Mi": "no_lcp", "dna_windows_20M": "dna_windows"}
         kern = {k: {"launches": v[0], "ms": v[1], "units": v[2]} for k, v in prof.items()}
         radix = library_radix_context(P, torch, dev, stream, chars, offsets, n) if name == "no_lcp_64Mi" else None
+        compressed = (alphabet_compressed(P, torch, dev, stream, chars, offsets, ss, perm, lcp)
+                      if name == "dna_windows_20M" else None)
         cls_cmp = compare_classifiers(P, torch, dev, stream, [dict(chars=chars, offsets=offsets, lengths=None,
                                                                    fixed_len=ss.fixed_len, n=n, perm_out=perm,
                                                                    lcp_out=lcp)])
@@ -160,9 +167,35 @@ def other_workloads(P, torch, dev, stream, peak):
                      "classifiers": cls_cmp}
         if radix:
             out[name]["library_radix_sort_context"] = radix
+        if compressed:
+            out[name]["alphabet_compressed"] = compressed
         del chars, offsets, perm, lcp
         torch.cuda.empty_cache()
     return out
+
+
+def alphabet_compressed(P, torch, dev, stream, chars, offsets, ss, perm, lcp, reps=5):
+    """The same DNA windows sorted with alphabet compression (keys of 32
+    two-bit characters, Section 8.1): median time, and whether the arrays
+    equal the byte-key sort's (which perm / lcp hold on entry)."""
+    ref = torch.cat([perm, lcp]).clone()
+    q = [dict(chars=chars, offsets=offsets, lengths=None, fixed_len=ss.fixed_len, n=ss.n, perm_out=perm, lcp_out=lcp)]
+    tun = [(0, 0, 0, P.alphabet(b"ACGT"))]
+    for _ in range(2):
+        P.ss_sort_batch_tuned(q, tun, stream=stream)
+    torch.cuda.synchronize(dev)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        P.ss_sort_batch_tuned(q, tun, stream=stream)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(e0.elapsed_time(e1))
+    ms = float(np.median(ts))
+    return {"ms": ms, "strings_per_s": ss.n / (ms / 1e3), "alphabet": "ACGT, 2 bits per character",
+            "outputs_equal_byte_keys": bool(torch.equal(torch.cat([perm, lcp]), ref))}
 
 
 def library_radix_context(P, torch, dev, stream, chars, offsets, n, reps=5):
@@ -193,7 +226,7 @@ def library_radix_context(P, torch, dev, stream, chars, offsets, n, reps=5):
                     "8 characters only, no LCPs; context, not a target"}
 
 
-def compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb, perm, lcp, reps=5):
+def compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb, perm, lcp, reps=5, fixed_len=0):
     """The step's merge with each method of ss_merge_ex (pairwise rounds, the
     default; one pass with LCP loser trees): median time of the call, the
     kernels' times from the library's launch events, and whether the outputs
@@ -202,7 +235,7 @@ def compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb
     out = {}
     for method, name in ((P.MERGE_PAIRWISE, "pairwise_rounds"), (P.MERGE_LOSER_TREE, "loser_tree")):
         def m():
-            P.ss_merge_ex(chars, offsets, None, 0, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], method=method,
+            P.ss_merge_ex(chars, offsets, None, fixed_len, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], method=method,
                           stream=stream)
         m()
         torch.cuda.synchronize(dev)
@@ -533,14 +566,30 @@ def load_peaks():
         return 6800.0, "fallback"
 
 
-def workload(n):
+WORKLOADS = {   # name: default n (the configuration's size)
+    "url_like": 10_000_000,
+    "no_lcp": 64 * 1024 * 1024,
+    "dna_windows": 20_000_000,
+}
+
+
+def workload(n, kind="url_like"):
     import workloads as W
+    if kind == "no_lcp":
+        return W.no_lcp(n=n, seed=5)
+    if kind == "dna_windows":
+        return W.dna_windows(n=n, text_len=20 * n, window=100, seed=3)
     return W.url_like(n, seed=2)
 
 
-def workload_name(n, runs):
-    return (f"url_like: n={n:,} strings 'http://' + host (2,000 hosts, Zipf s=1.1) + 1-6 path segments, "
-            f"5% duplicates, seed 2; sorted as {runs} runs + {runs}-way LCP merge")
+def workload_name(n, runs, kind="url_like"):
+    what = {
+        "url_like": (f"url_like: n={n:,} strings 'http://' + host (2,000 hosts, Zipf s=1.1) + 1-6 path segments, "
+                     f"5% duplicates, seed 2"),
+        "no_lcp": f"no_lcp: n={n:,} strings of 16 bytes U[1,255], NUL-terminated, seed 5",
+        "dna_windows": f"dna_windows: text of {20 * n:,} bytes U{{A,C,G,T}}, n={n:,} windows of 100 bytes, seed 3",
+    }[kind]
+    return f"{what}; sorted as {runs} runs + {runs}-way LCP merge"
 
 
 def d_and_balg(lcp: np.ndarray):
@@ -668,7 +717,7 @@ def run_reference(args):
     import oracle
     import workloads as W
     oracle.build()
-    ss = workload(args.n)
+    ss = workload(args.n, args.workload)
     m = min(ss.n, 1_000_000)
     sub = W.subset(ss, np.arange(m))
     for _ in range(max(0, args.warmup)):
@@ -681,7 +730,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-            "config": {"workload": workload_name(args.n, args.runs), "sample": m},
+            "config": {"workload": workload_name(args.n, args.runs, args.workload), "sample": m},
             "cpu_baseline": {"value": value, "unit": "strings/s", "cores": 1, "kind": "oracle",
                              "sample": f"first {m:,} strings of the workload per step"},
             "e2e": {"value": value, "unit": "strings/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -691,6 +740,8 @@ def run_reference(args):
 
 def main():
     args = parse()
+    if args.n <= 0:
+        args.n = WORKLOADS[args.workload]
     if args.impl == "reference":
         return run_reference(args)
 
@@ -709,7 +760,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
 
-    ss = workload(args.n)
+    ss = workload(args.n, args.workload)
     n, K = ss.n, args.runs
     chars = torch.from_numpy(ss.chars).to(dev)
     offsets = torch.from_numpy(ss.offsets.view(np.int64)).to(dev)
@@ -718,17 +769,18 @@ def main():
     rlcp = torch.empty(n, dtype=torch.int32, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     lcp = torch.empty(n, dtype=torch.int32, device=dev)
-    reqs = [dict(chars=chars, offsets=offsets[int(rb[k]):int(rb[k + 1])], lengths=None, fixed_len=0,
+    fl = ss.fixed_len
+    reqs = [dict(chars=chars, offsets=offsets[int(rb[k]):int(rb[k + 1])], lengths=None, fixed_len=fl,
                  n=int(rb[k + 1] - rb[k]), perm_out=rperm[int(rb[k]):int(rb[k + 1])],
                  lcp_out=rlcp[int(rb[k]):int(rb[k + 1])]) for k in range(K)]
     stream = torch.cuda.current_stream(dev)
 
     def step():
         P.ss_sort_batch(reqs, stream=stream)
-        P.ss_merge(chars, offsets, None, 0, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], stream=stream)
+        P.ss_merge(chars, offsets, None, fl, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], stream=stream)
 
     def sort_only():
-        P.ss_sort(chars, offsets, n, perm, lcp, stream=stream)
+        P.ss_sort_ex(chars, offsets, None, fl, n, perm, lcp, stream=stream)
 
     def barrier():
         if dist is not None:
@@ -739,24 +791,25 @@ def main():
     torch.cuda.synchronize(dev)
 
     # sort only (rows a1-a9, one request) for context, before the timed region
-    for _ in range(2):
-        sort_only()
-    torch.cuda.synchronize(dev)
-    e0 = torch.cuda.Event(enable_timing=True)
-    e1 = torch.cuda.Event(enable_timing=True)
-    reps = max(3, args.steps // 2)
-    calls_ms = []
-    e0.record(stream)
-    for _ in range(reps):
-        t0 = time.perf_counter()
-        sort_only()
-        calls_ms.append((time.perf_counter() - t0) * 1e3)
-    e1.record(stream)
-    torch.cuda.synchronize(dev)
-    ms_sort = e0.elapsed_time(e1) / reps
-    for _ in range(2):
-        step()
-    torch.cuda.synchronize(dev)
+    ms_sort, calls_ms = None, []
+    if not args.capture:
+        for _ in range(2):
+            sort_only()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        reps = max(3, args.steps // 2)
+        e0.record(stream)
+        for _ in range(reps):
+            t0 = time.perf_counter()
+            sort_only()
+            calls_ms.append((time.perf_counter() - t0) * 1e3)
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms_sort = e0.elapsed_time(e1) / reps
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize(dev)
 
     # timed region: exactly K steps between a barrier and a synchronize on both
     # sides, CUDA events on the launch stream, clocks sampled
@@ -811,25 +864,32 @@ def main():
     tot = sum(v["ms_per_step"] for v in kernels.values()) or 1.0
     for v in kernels.values():
         v["share"] = v["ms_per_step"] / tot
-    dom = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    # the dominant kernel among those that move a step's data (a kernel that
+    # only searches, such as the merge's chunk starts, has no algorithmic bytes);
+    # the overall top kernel is named beside it
+    top = max(kernels, key=lambda k: kernels[k]["ms_per_step"]) if kernels else None
+    moving = [k for k in kernels if kernels[k]["bytes_per_unit"]]
+    dom = max(moving, key=lambda k: kernels[k]["ms_per_step"]) if moving else None
     roofline = None
     if dom:
         kd = kernels[dom]
         ach = kd["achieved_gbs"] or 0.0
         roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "peak_kind": peak_kind,
-                    "traffic": dram_traffic(dom, "url_like", kd["units_per_launch"]),
+                    "traffic": dram_traffic(dom, args.workload, kd["units_per_launch"]),
                     "units_per_launch": kd["units_per_launch"], "bytes_per_unit": kd["bytes_per_unit"],
                     "algorithmic_bytes_per_launch": kd["units_per_launch"] * (kd["bytes_per_unit"] or 0),
                     "launch_ms": kd["ms_per_step"] * args.steps / max(kd["launches"], 1),
                     "carried_bytes_per_unit": CARRIED_BYTES_PER_UNIT.get(dom, 0),
+                    "top_kernel": {"kernel": top, "share": kernels[top]["share"],
+                                   "bytes_per_unit": kernels[top]["bytes_per_unit"]},
                     "whole_step": {"algorithmic_bytes": balg, "frac": balg / (ms / 1e3) / 1e9 / peak}}
 
     line = {
         "metric": METRIC, "value": value, "unit": "strings/s", "n_gpus": world, "steps": args.steps,
         "warmup": max(args.warmup, 3), "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic",
-        "config": {"workload": workload_name(n, K), "n": n, "N_bytes": int(ss.chars.nbytes),
+        "config": {"workload": workload_name(n, K, args.workload), "n": n, "N_bytes": int(ss.chars.nbytes),
                    "mean_len": ss.meta.get("mean_len"), "runs": K, "parallelism": f"replicas x{world}",
                    "l2": (f"inputs larger than L2 (chars {ss.chars.nbytes / 1e9:.2f} GB + offsets "
                           f"{ss.offsets.nbytes / 1e6:.0f} MB per step)"
@@ -838,7 +898,7 @@ def main():
         "d_gb_per_s": D * (job_strings // n) / (ms / 1e3) / 1e9, "D": D,
         "whole_sort_roofline": {"algorithmic_bytes": balg, "achieved_gbs": balg / (ms / 1e3) / 1e9,
                                 "frac": balg / (ms / 1e3) / 1e9 / peak},
-        "sort_only": {"ms": ms_sort, "value": n / (ms_sort / 1e3), "unit": "strings/s",
+        "sort_only": {"ms": ms_sort, "value": (n / (ms_sort / 1e3)) if ms_sort else None, "unit": "strings/s",
                       "calls_ms": [round(x, 3) for x in calls_ms],
                       "what": "one ss_sort of the whole set (no runs, no merge)"},
         "roofline": roofline,
@@ -857,13 +917,13 @@ def main():
         hp = torch.empty(n, dtype=torch.int32).pin_memory()
         hl = torch.empty(n, dtype=torch.int32).pin_memory()
         for _ in range(2):
-            P.ss_sort_host(hc, ho, None, 0, hp, hl, runs=K, stream=stream)
+            P.ss_sort_host(hc, ho, None, fl, hp, hl, runs=K, stream=stream)
         barrier()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         reps = max(3, args.steps // 2)
         for _ in range(reps):
-            P.ss_sort_host(hc, ho, None, 0, hp, hl, runs=K, stream=stream)
+            P.ss_sort_host(hc, ho, None, fl, hp, hl, runs=K, stream=stream)
         torch.cuda.synchronize(dev)
         one_ms, _ = aggregate(dist, (time.perf_counter() - t0) / reps * 1e3, n, dev)
         same = np.array_equal(hp.numpy(), perm.cpu().numpy()) and np.array_equal(hl.numpy(), lcp.cpu().numpy())
@@ -875,7 +935,7 @@ def main():
         with P.Server(64 << 30, workers=args.e2e_workers) as srv:
             for k in range(2):
                 o = outs[k % len(outs)]
-                srv.wait(srv.submit_host(hc, ho, None, 0, o[0], o[1], runs=K))
+                srv.wait(srv.submit_host(hc, ho, None, fl, o[0], o[1], runs=K))
             barrier()
             torch.cuda.synchronize(dev)
             t0 = time.perf_counter()
@@ -886,7 +946,7 @@ def main():
                     st_, _ = srv.wait(inflight.pop(0))
                     same = same and st_ == 0
                 o = outs[i % len(outs)]
-                inflight.append(srv.submit_host(hc, ho, None, 0, o[0], o[1], runs=K))
+                inflight.append(srv.submit_host(hc, ho, None, fl, o[0], o[1], runs=K))
             for t_ in inflight:
                 st_, _ = srv.wait(t_)
                 same = same and st_ == 0
@@ -905,7 +965,7 @@ def main():
     if rank == 0 and not args.no_extra:
         line["merge_methods"] = dict(what="the step's merge of its runs by each method of ss_merge_ex",
                                      **compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb,
-                                                             perm, lcp))
+                                                             perm, lcp, fixed_len=fl))
         line["classifiers"] = dict(what="the step's 4 runs sorted by one ss_sort_batch_tuned call per classifier",
                                    **compare_classifiers(P, torch, dev, stream, reqs))
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)
@@ -923,7 +983,7 @@ def main():
                 "units_per_launch": nl_["dominant_kernel"]["units_per_launch"]}
     if rank == 0 and not args.no_batched:
         line["batched"] = batched_vs_plain(P, torch, dev, stream, nreq=args.batched_requests)
-        if not args.no_serving:
+        if not args.no_serving and args.workload == "url_like":   # the served mix takes the URL set as a pool
             line["serving"] = serving_vs_plain(P, torch, dev, chars, offsets,
                                                capacity_sps=line["batched"]["batched"]["strings_per_s"],
                                                nreq=args.serving_requests)
