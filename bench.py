@@ -551,7 +551,7 @@ def dram_traffic(kernel, workload_kind, units_per_launch):
         return None
     if tj.get("source_hash") != _source_hash():
         return None
-    k = tj.get("kernels", {}).get(kernel)
+    k = tj.get("kernels", {}).get(workload_kind, {}).get(kernel)
     if not k or k.get("workload_kind") != workload_kind:
         return None
     return float(k["dram_bytes_per_unit"]) * float(units_per_launch)

@@ -60,7 +60,7 @@ def test_dram_traffic_needs_matching_sources_and_workload(tmp_path, monkeypatch)
     prof = tmp_path / "profiles"
     prof.mkdir()
     tj = {"source_hash": bench._source_hash(),
-          "kernels": {"scatter": {"workload_kind": "url_like", "dram_bytes_per_unit": 50.0}}}
+          "kernels": {"url_like": {"scatter": {"workload_kind": "url_like", "dram_bytes_per_unit": 50.0}}}}
     (prof / "traffic.json").write_text(json.dumps(tj))
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     monkeypatch.setattr(bench, "_source_hash", lambda: tj["source_hash"])
@@ -69,3 +69,14 @@ def test_dram_traffic_needs_matching_sources_and_workload(tmp_path, monkeypatch)
     assert bench.dram_traffic("classify", "url_like", 1000) is None
     monkeypatch.setattr(bench, "_source_hash", lambda: "other")
     assert bench.dram_traffic("scatter", "url_like", 1000) is None
+
+
+def test_committed_traffic_file_has_every_workload_kind(monkeypatch):
+    """profiles/traffic.json holds DRAM bytes per unit for every workload kind
+    the bench can run, in the layout dram_traffic reads (checked as if the
+    sources still hashed to the capture's)."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        tj = json.load(f)
+    monkeypatch.setattr(bench, "_source_hash", lambda: tj["source_hash"])
+    for kind in bench.WORKLOADS:
+        assert bench.dram_traffic("scatter", kind, 1000) is not None, kind
