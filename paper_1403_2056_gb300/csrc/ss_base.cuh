@@ -273,23 +273,27 @@ struct BaseSmem {
     uint16_t ACT[CAP];       // positions still being sorted, in order
     uint32_t WL[CAP / 2];    // groups of 2..32 strings for the warps: start << 16 | size
     uint64_t wlast[NT / 32]; // last key of each warp's slots (first round's neighbour test)
+    uint64_t wmin[NT / 32], wmax[NT / 32];   // smallest and largest key of each warp's slots
     uint32_t wsum[NT / 32];
     uint32_t nwl, nws, wbase;   // small groups, their strings, first reserved list slot
     uint32_t task, next;     // task taken from the queue, and the one after it
 };
 
-// First round by one counting pass (the adaptivity of Section 8.1: when a few
-// key bits already spread a segment, distribute by them as radix sort does).
-// All keys of the segment share their leading cp bits (cp = clz of the OR of
-// every key xor the first); the next B bits (2^B >= m digit values) are a
-// digit that is monotone in the key.  One shared-memory histogram, scan and
-// placement put the segment in digit order; each digit's strings (at most
-// kRadixBucketMax, otherwise the merge sort below is used instead) are then
-// put in (key, original index) order by insertion sort.  kin holds the keys
-// of this thread's slots tid + r NT (SK holds all of them by position).  On
-// success SK / SP hold the segment sorted by (key, original index) by
-// position and true is returned; false leaves SK untouched and SP unset (all
-// keys equal, or a digit too full).  Every thread of the CTA calls this.
+// First round by one counting pass (the adaptivity of Section 8.1: when the
+// keys of a segment are spread, distribute by a digit as radix sort does).
+// The digit is the key's place in the segment's key range [kmin, kmax] scaled
+// to 2^B >= m values (fixed point, below: d < 2^B, monotone in the key); keys
+// spread evenly over their range (a bucket between two splitters) fill the
+// digits evenly wherever the range lies, where the bits after the keys' common
+// prefix would leave most digits empty when the range straddles a power of
+// two.  One shared-memory histogram, scan and placement put the segment in
+// digit order; each digit's strings (at most kRadixBucketMax, otherwise the
+// merge sort below is used instead) are then put in (key, original index)
+// order by insertion sort.  kin holds the keys of this thread's slots
+// tid + r NT (SK holds all of them by position).  On success SK / SP hold the
+// segment sorted by (key, original index) by position and true is returned;
+// false leaves SK untouched and SP unset (all keys equal, keys of a sparse
+// alphabet, or a digit too full).  Every thread of the CTA calls this.
 constexpr uint32_t kRadixBucketMax = 8;
 
 template <int NT, int ITEMS>
@@ -298,29 +302,54 @@ __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t k0 = S.SK[0];
     uint64_t k[ITEMS];
-    uint64_t x = 0;
+    uint64_t x = 0, kmn = ~0ull, kmx = 0;
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
         const uint32_t i = tid + r * NT;
         k[r] = i < m ? kin[r] : k0;
         x |= k[r] ^ k0;
+        kmn = min(kmn, k[r]);
+        kmx = max(kmx, k[r]);
     }
     const uint32_t xl = __reduce_or_sync(0xffffffffu, (uint32_t)x);
     const uint32_t xh = __reduce_or_sync(0xffffffffu, (uint32_t)(x >> 32));
-    if (lane == 0) S.wlast[warp] = ((uint64_t)xh << 32) | xl;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmn = min(kmn, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmn, o));
+        kmx = max(kmx, (uint64_t)__shfl_xor_sync(0xffffffffu, (unsigned long long)kmx, o));
+    }
+    if (lane == 0) {
+        S.wlast[warp] = ((uint64_t)xh << 32) | xl;
+        S.wmin[warp] = kmn;
+        S.wmax[warp] = kmx;
+    }
     __syncthreads();
     x = 0;
 #pragma unroll
-    for (int w = 0; w < NW; w++) x |= S.wlast[w];
+    for (int w = 0; w < NW; w++) {
+        x |= S.wlast[w];
+        kmn = min(kmn, S.wmin[w]);
+        kmx = max(kmx, S.wmax[w]);
+    }
     if (x == 0) return false;   // every key equal: nothing to distribute
     const uint32_t cp = (uint32_t)__clzll((long long)x);
     uint32_t B = 1;
     while ((1u << B) < m) B++;
     const uint32_t nb = 1u << B;   // <= NT * ITEMS
-    // the digit spreads the keys only if (nearly) all of its bits vary among
-    // them (characters of a small alphabet leave some bits of every byte
-    // fixed): otherwise the merge sort is used without trying
+    // keys of a small alphabet (some bits of every byte fixed) fill a digit
+    // space unevenly: when fewer than B - 1 of the B bits after the common
+    // prefix vary among the keys, the merge sort is used without trying
     if ((uint32_t)__popcll((x << cp) >> (64 - B)) + 1 < B) return false;
+    // the range normalised: span << L in [2^63, 2^64), sh its top 32 bits;
+    // M = 2^44 / (sh + 1) * (1 - 2^-20 + 2^-22) at most (the float quotient is
+    // within 2^-23 of the exact one), so ((t >> 32) * M) < 2^44 for every
+    // t = (key - kmin) << L <= span << L, and M >= 4094 keeps the digits even
+    // to 1 part in 4096
+    const uint64_t span = kmx - kmn;   // > 0: the keys are not all equal
+    const uint32_t L = (uint32_t)__clzll((long long)span);
+    const uint32_t sh = (uint32_t)((span << L) >> 32);
+    const uint32_t M = (uint32_t)__float2uint_rz(17592186044416.0f / (__uint2float_rn(sh) + 1.0f) *
+                                                 (1.0f - 1.0f / 1048576.0f));
     uint32_t *C = S.MG;
     for (uint32_t b = tid; b < nb; b += NT) C[b] = 0;
     __syncthreads();
@@ -328,7 +357,7 @@ __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
         const uint32_t i = tid + r * NT;
-        d[r] = (uint32_t)((k[r] << cp) >> (64 - B));
+        d[r] = (uint32_t)(((uint64_t)(uint32_t)(((k[r] - kmn) << L) >> 32) * M) >> (44 - B));
         rk[r] = i < m ? atomicAdd(&C[d[r]], 1u) : 0u;
     }
     __syncthreads();
@@ -379,8 +408,12 @@ __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32
 // that hold the end of the string), the sorted keys still in registers give
 // every LCP and the task ends there; only segments with equal keys that
 // continue past these 8 characters go through the group rounds below.
+// CTAs per SM the register budget must allow: as many as the shared memory
+// of each class lets in (BaseSmem: about 7, 28 and 56 KB)
+constexpr int base_min_ctas(int nt) { return nt >= 256 ? 4 : nt >= 128 ? 7 : 16; }
+
 template <int NT, int ITEMS, bool A>
-__global__ void __launch_bounds__(NT) k_base_cta(const SmallTask *tasks, const uint32_t *ntask_dev, uint32_t *next_task,
+__global__ void __launch_bounds__(NT, base_min_ctas(NT)) k_base_cta(const SmallTask *tasks, const uint32_t *ntask_dev, uint32_t *next_task,
                                                  const ReqDesc *reqs, ElemBufs eb, SmallTask *tiny, uint32_t tiny_cap,
                                                  uint32_t *counters) {
     constexpr uint32_t CAP = NT * ITEMS;

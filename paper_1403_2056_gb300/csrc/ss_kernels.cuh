@@ -290,12 +290,28 @@ struct TreeSmem {
     PickNode n0[(kMaxV + 1) / 2], n1[(kMaxV + 1) / 2];
 };
 
-// The sample has alpha * v + alpha - 1 keys (alpha = 2) for the tree size the
-// segment's length allows (choose_d); the tree actually built has just enough
-// levels for the distinct keys of the sample (adaptivity, Section 8.1): a
-// segment whose sample holds 27 distinct keys gets 31 splitters, not 1023.
-// The chosen depth is stored in the segment record; k_setup_big lays out the
-// counters from it.
+// The sample has alpha * v + alpha - 1 keys for the tree size the segment's
+// length allows (choose_d), and every alpha-th sample key becomes a splitter.
+// alpha = 2 while the tree can be as large as the segment asks for; when the
+// depth cap holds the tree back (buckets of more than child_target strings on
+// average) alpha grows to kAlphaCapped, so that the buckets are more even and
+// fewer of them miss the base-case size by chance (a bucket of an alpha-sample
+// splitter spans alpha sample gaps: its relative size has variance 1 / alpha).
+// The tree actually built has just enough levels for the distinct keys of the
+// sample (adaptivity, Section 8.1): a segment whose sample holds 27 distinct
+// keys gets 31 splitters, not 1023.  The chosen depth is stored in the segment
+// record; k_setup_big lays out the counters from it.
+#ifndef SS_ALPHA_CAPPED
+#define SS_ALPHA_CAPPED 8
+#endif
+constexpr uint32_t kAlphaCapped = SS_ALPHA_CAPPED;
+static_assert(kAlphaCapped >= 2 && (kAlphaCapped & (kAlphaCapped - 1)) == 0 &&
+                  kAlphaCapped * (1u << kLevelD) <= 2u * (kMaxV + 1),
+              "the sample of a capped tree fits the tree builder's buffer");
+
+__device__ __forceinline__ uint32_t sample_alpha(uint32_t size, uint32_t d, uint32_t target) {
+    return (d == (uint32_t)kLevelD && size / target > (1u << d)) ? kAlphaCapped : 2u;
+}
 __global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const ReqDesc *reqs, const uint64_t *key,
                                                            uint64_t *splitters) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -303,8 +319,9 @@ __global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const Re
     __shared__ uint32_t distinct;
     BigSeg sg = segs[blockIdx.x];
     const uint32_t dmax = choose_d(sg.size, req_child_target(reqs[sg.req]));
+    const uint32_t alpha = sample_alpha(sg.size, dmax, req_child_target(reqs[sg.req]));
     uint32_t v = (1u << dmax) - 1;
-    uint32_t a = 2 * v + 1;            // alpha * v + alpha - 1 with alpha = 2
+    uint32_t a = alpha * (v + 1) - 1;   // alpha * v + alpha - 1
     uint32_t P = a + 1;
     if (threadIdx.x == 0) distinct = 0;
     uint64_t seed = ((uint64_t)sg.begin << 32) ^ (uint64_t)sg.depth * 0x9E3779B97F4A7C15ULL;

@@ -388,7 +388,7 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
 }
 
 #ifndef SS_MERGE_TILE_THREADS
-#define SS_MERGE_TILE_THREADS 128
+#define SS_MERGE_TILE_THREADS 256
 #endif
 constexpr uint32_t kMergeTileThreads = SS_MERGE_TILE_THREADS;
 constexpr uint32_t kMergeTile = kMergeTileThreads * kMergeItems;   // outputs per CTA window
@@ -478,21 +478,19 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_starts(
 }
 
 struct MergeTileSmem {
-    uint32_t lcp[kMergeTile];    // the window's run entries: A's, then B's
-    uint64_t ck[kMergeTile];
-    uint32_t ckd[kMergeTile];
     uint32_t olcp[kMergeTile];   // per output: LCP with the output before it
-    uint16_t src[kMergeTile];    // per output: which staged entry it is
+    uint16_t src[kMergeTile];    // per output: which window entry it is
 };
 
 // One round of pairwise merges, one CTA per window of kMergeTile outputs of a
 // pair (windows do not straddle pairs; wbase[p] = first window of pair p).  The
-// window's run entries (LCPs and cached characters) are staged in shared memory
-// with coalesced reads; from its start (k_merge_starts) each thread runs the
-// binary LCP-merge (Algorithm 3) over kMergeItems outputs out of shared memory
-// and records which entry each output is; the CTA then writes all outputs with
-// coalesced stores.  Only the case-1 comparisons that the cached characters
-// leave open read strings here.
+// window's run entries (LCPs and cached characters) are read through L1, each
+// thread walking its own consecutive entries of both runs (not staged in
+// shared memory: that held the CTAs per SM to a third and measured slower);
+// from its start (k_merge_starts) each thread runs the binary LCP-merge
+// (Algorithm 3) over kMergeItems outputs and records which entry each output
+// is and its LCP; the CTA then writes all outputs with coalesced stores.  Only
+// the case-1 comparisons that the cached characters leave open read strings.
 __global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
     ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R, const uint32_t *rbase,
     const uint32_t *wbase, uint32_t npairs, uint32_t *out_perm, uint32_t *out_lcp, const Coarse *C,
@@ -511,14 +509,11 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
     const uint32_t dl = threadIdx.x * kMergeItems;
     MergeStart ms{0u, 0u, 0u, 0u};
     if (dl < nW) ms = starts[blockIdx.x * kMergeTileThreads + threadIdx.x];
-    // stage the window's entries
-    for (uint32_t x = threadIdx.x; x < nW; x += kMergeTileThreads) {
-        const uint32_t g = x < nA ? a0 + I0 + x : a0 + na + J0 + (x - nA);   // run-aligned position
-        T.lcp[x] = in_lcp[g];
-        T.ck[x] = ck ? ck[g] : 0ull;
-        T.ckd[x] = ck ? ckd[g] : ~0u;
-    }
-    __syncthreads();
+    // the window's entries: x < nA is A's entry I0 + x, else B's entry J0 + x - nA
+    auto gpos = [&](uint32_t x) { return x < nA ? a0 + I0 + x : a0 + na + J0 + (x - nA); };   // run-aligned position
+    auto e_lcp = [&](uint32_t x) { return __ldg(in_lcp + gpos(x)); };
+    auto e_ck = [&](uint32_t x) { return ck ? __ldg(ck + gpos(x)) : 0ull; };
+    auto e_ckd = [&](uint32_t x) { return ck ? __ldg(ckd + gpos(x)) : ~0u; };
     if (dl < nW) {
         const uint32_t diag = d0 + dl;
         const uint32_t stop = min(dl + kMergeItems, nW);
@@ -526,8 +521,8 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
         // fronts' cached characters (depth kd, ~0: none)
         uint32_t kdA = ~0u, kdB = ~0u;
         uint64_t kA = 0, kB = 0;
-        if (i < I1) { kdA = T.ckd[i - I0]; kA = T.ck[i - I0]; }
-        if (j < J1) { kdB = T.ckd[nA + j - J0]; kB = T.ck[nA + j - J0]; }
+        if (i < I1) { kdA = e_ckd(i - I0); kA = e_ck(i - I0); }
+        if (j < J1) { kdB = e_ckd(nA + j - J0); kB = e_ck(nA + j - J0); }
         for (uint32_t s = dl; s < stop; s++) {
             // the window holds exactly the entries its outputs take: a side past
             // its part of the window is exhausted here
@@ -571,16 +566,16 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
                 T.src[s] = (uint16_t)(i - I0);
                 T.olcp[s] = diag + (s - dl) == 0 ? 0u : ha;
                 i++;
-                ha = i < I1 ? T.lcp[i - I0] : 0u;
+                ha = i < I1 ? e_lcp(i - I0) : 0u;
                 if (both) hb = hp;
-                if (i < I1) { kdA = T.ckd[i - I0]; kA = T.ck[i - I0]; } else kdA = ~0u;
+                if (i < I1) { kdA = e_ckd(i - I0); kA = e_ck(i - I0); } else kdA = ~0u;
             } else {
                 T.src[s] = (uint16_t)(nA + j - J0);
                 T.olcp[s] = diag + (s - dl) == 0 ? 0u : hb;
                 j++;
-                hb = j < J1 ? T.lcp[nA + j - J0] : 0u;
+                hb = j < J1 ? e_lcp(nA + j - J0) : 0u;
                 if (both) ha = hp;
-                if (j < J1) { kdB = T.ckd[nA + j - J0]; kB = T.ck[nA + j - J0]; } else kdB = ~0u;
+                if (j < J1) { kdB = e_ckd(nA + j - J0); kB = e_ck(nA + j - J0); } else kdB = ~0u;
             }
         }
     }
@@ -589,13 +584,13 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
     for (uint32_t s = threadIdx.x; s < nW; s += kMergeTileThreads) {
         const uint32_t x = T.src[s];
         const bool fromA = x < nA;
-        const uint32_t g = fromA ? a0 + I0 + x : a0 + na + J0 + (x - nA);
+        const uint32_t g = gpos(x);
         const uint32_t o = a0 + d0 + s;
         const uint32_t id = in_perm[g] + (fromA ? v.baseA : v.baseB);
         out_perm[o] = id;
         out_lcp[o] = T.olcp[s];
         if (out_off) out_off[o] = in_off ? in_off[g] : __ldg(S.offsets + id);
-        if (out_ck) { out_ck[o] = T.ck[x]; out_ckd[o] = T.ckd[x]; }
+        if (out_ck) { out_ck[o] = e_ck(x); out_ckd[o] = e_ckd(x); }
     }
 }
 
