@@ -398,7 +398,8 @@ def batched_vs_plain(P, torch, dev, stream, nreq=4096, seed=4):
                   "launches": "one ss_sort per request, in arrival order"},
         "speedup": tp / tb,
         "autotuned": {"tunings_by_generator": {n_: {"child_target": t[0], "min_step": t[1],
-                                                    "classifier": ["unroll", "equal", "jump"][t[2]]}
+                                                    "classifier": ["unroll", "equal", "jump"][t[2]],
+                                                    "alphabet": t[3], "max_depth": t[4], "small_max": t[5]}
                                                 for n_, t in zip(["random", "url_like", "dna_like"], tuned)},
                       "ms": float(np.median(tt)), "strings_per_s": total / (float(np.median(tt)) / 1e3),
                       "how": "ss_autotune on a 1 M sample of each generator's pool, then one ss_sort_batch_tuned call",

@@ -171,13 +171,22 @@ int ss_sort_batch(const ss_request *reqs_host, uint32_t count, ss_stream_t strea
  * SS_ALPHABET('A', 'C', 'G', 'T').  Keys then hold 32 characters of 2 bits
  * instead of 8 bytes; depths and LCPs stay in characters.  The library does
  * not check the strings' bytes: a byte outside the alphabet gives an
- * unspecified order.  0: bytes.  None of the fields changes any result.
+ * unspecified order.  0: bytes.  max_depth: the largest splitter-tree depth
+ * of one distribution level (v = 2^max_depth - 1 splitters), in [2, 8];
+ * 0: 8.  small_max: segments of at most this many strings go to the base
+ * case, larger ones to another distribution level; a power of two in
+ * [64, 2048]; 0: 2048.  The sort's scratch holds about 10 KiB (a segment's
+ * splitters, jump table and records) per small_max + 1 strings of the batch's
+ * smallest small_max.
+ * None of the fields changes any result.
  */
 typedef struct {
     uint32_t child_target;
     uint32_t min_step;
     uint32_t classifier;
     uint32_t alphabet;
+    uint32_t max_depth;
+    uint32_t small_max;
 } ss_tuning;
 
 #define SS_ALPHABET(a0, a1, a2, a3) \
@@ -207,10 +216,14 @@ int ss_sort_batch_async(const ss_request *reqs_host, const ss_tuning *tunings_ho
 
 /*
  * ss_autotune -- picks a tuning for inputs like `req`'s: sorts its first
- * min(n, sample_n) strings (sample_n = 0: 2,000,000) with each of 18
- * candidate tunings (child_target 256..2048 x min_step 1, 3, 5, 9 with the
- * default classifier, then the best of those with SS_CLASSIFIER_EQUAL and
- * SS_CLASSIFIER_JUMP), once to warm and once timed with CUDA events on
+ * min(n, sample_n) strings (sample_n = 0: 2,000,000) with each of 22 or 23
+ * candidate tunings, each step keeping the fastest so far: child_target
+ * 256..2048 x min_step 1, 3, 5, 9 with the default classifier; that shape
+ * with SS_CLASSIFIER_EQUAL and SS_CLASSIFIER_JUMP; max_depth 6 and 7;
+ * small_max 512 and 1024; and, for fixed-length strings whose sampled bytes
+ * are at most four non-zero values, the alphabet of those bytes (keys of 32
+ * two-bit characters instead of 8 bytes).  Each runs once to warm and once
+ * timed with CUDA events on
  * `stream`, into scratch it allocates (req's outputs are not touched), and
  * writes the fastest to *best_out and its time in ms to *best_ms_out (may be
  * NULL).  Returns when done.

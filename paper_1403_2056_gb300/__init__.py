@@ -112,7 +112,7 @@ class HostRequest(C.Structure):
 
 class Tuning(C.Structure):
     _fields_ = [("child_target", C.c_uint32), ("min_step", C.c_uint32), ("classifier", C.c_uint32),
-                ("alphabet", C.c_uint32)]
+                ("alphabet", C.c_uint32), ("max_depth", C.c_uint32), ("small_max", C.c_uint32)]
 
 
 def alphabet(symbols: bytes) -> int:
@@ -276,7 +276,7 @@ def _tuned_args(requests, tunings):
     if tunings is not None:
         tarr = (Tuning * max(1, len(requests)))()
         for k, t in enumerate(tunings):
-            tarr[k] = Tuning(int(t[0]), int(t[1]), int(t[2]) if len(t) > 2 else 0, int(t[3]) if len(t) > 3 else 0)
+            tarr[k] = Tuning(*[int(t[f]) if len(t) > f else 0 for f in range(6)])
     return arr, tarr
 
 
@@ -299,17 +299,18 @@ def ss_sort_batch_tuned(requests, tunings=None, stream=None):
     if tunings is not None:
         tarr = (Tuning * max(1, len(requests)))()
         for k, t in enumerate(tunings):
-            tarr[k] = Tuning(int(t[0]), int(t[1]), int(t[2]) if len(t) > 2 else 0, int(t[3]) if len(t) > 3 else 0)
+            tarr[k] = Tuning(*[int(t[f]) if len(t) > f else 0 for f in range(6)])
     _check(lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
                                       len(requests), _stream(stream)))
 
 
 def ss_autotune(q, sample_n: int = 0, stream=None):
-    """((child_target, min_step, classifier), ms) fastest on the first sample_n strings of request q."""
+    """((child_target, min_step, classifier, alphabet, max_depth, small_max), ms): the tuning fastest
+    on the first sample_n strings of request q (a tuple in ss_tuning's field order)."""
     t = Tuning()
     ms = C.c_double()
     _check(lib().ss_autotune(C.byref(_request(q)), int(sample_n), C.byref(t), C.byref(ms), _stream(stream)))
-    return (t.child_target, t.min_step, t.classifier), ms.value
+    return (t.child_target, t.min_step, t.classifier, t.alphabet, t.max_depth, t.small_max), ms.value
 
 
 def ss_scratch_bytes(n: int) -> int:

@@ -372,7 +372,19 @@ static int pack_tuning(const ss_tuning &t, ReqDesc &r, const char *who) {
         set_error_detail("%s: classifier must be in [0, 2], got %u", who, t.classifier);
         return SS_ERR_INVALID;
     }
-    out = s | (t.min_step << 8) | (t.classifier << 16);
+    if (t.max_depth && (t.max_depth < 2 || t.max_depth > (uint32_t)kLevelD)) {
+        set_error_detail("%s: max_depth must be 0 or in [2, %d], got %u", who, kLevelD, t.max_depth);
+        return SS_ERR_INVALID;
+    }
+    uint32_t sm = 0;
+    if (t.small_max) {
+        if (t.small_max < 64 || t.small_max > kSmallMax || (t.small_max & (t.small_max - 1))) {
+            set_error_detail("%s: small_max must be 0 or a power of two in [64, %u], got %u", who, kSmallMax, t.small_max);
+            return SS_ERR_INVALID;
+        }
+        while ((1u << sm) < t.small_max) sm++;
+    }
+    out = s | (t.min_step << 8) | (t.classifier << 16) | (t.max_depth << 20) | (sm << 24);
     return SS_OK;
 }
 
@@ -423,7 +435,7 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
     int rc = check_req(r, "ss_autotune");
     if (rc != SS_OK) return rc;
     const uint32_t n = std::min<uint32_t>(req->n, sample_n ? sample_n : 2000000u);
-    *best_out = ss_tuning{0, 0, 0, 0};
+    *best_out = ss_tuning{0, 0, 0, 0, 0, 0};
     if (best_ms_out) *best_ms_out = 0;
     if (n < 2) return SS_OK;
     cudaStream_t st = as_stream(stream);
@@ -462,11 +474,40 @@ int ss_autotune(const ss_request *req, uint32_t sample_n, ss_tuning *best_out, d
         bool ok = true;
         for (uint32_t ct : targets)
             for (uint32_t ms : steps)
-                if (ok) ok = try_one(ss_tuning{ct, ms, CLS_UNROLL, 0});
+                if (ok) ok = try_one(ss_tuning{ct, ms, CLS_UNROLL, 0, 0, 0});
         // the other classifiers with the best tree shape
         const ss_tuning shape = *best_out;
-        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_EQUAL, 0});
-        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_JUMP, 0});
+        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_EQUAL, 0, 0, 0});
+        if (ok) ok = try_one(ss_tuning{shape.child_target, shape.min_step, CLS_JUMP, 0, 0, 0});
+        // smaller trees per level, then smaller base cases, each on the best so far
+        for (uint32_t md : {6u, 7u}) {
+            ss_tuning t = *best_out;
+            t.max_depth = md;
+            if (ok) ok = try_one(t);
+        }
+        for (uint32_t sm : {512u, 1024u}) {
+            ss_tuning t = *best_out;
+            t.small_max = sm;
+            if (ok) ok = try_one(t);
+        }
+        // key width: fixed-length strings over at most four bytes (none of
+        // them 0) take keys of 32 two-bit characters (alphabet compression)
+        if (ok && !r.lengths && r.fixed_len > 0) {
+            uint32_t mask[8];
+            if ((rc = engine_byte_set(r, n, mask, st)) != SS_OK) break;
+            uint32_t a[4], na = 0;
+            for (uint32_t c = 0; c < 256; c++)
+                if (mask[c >> 5] >> (c & 31) & 1u) {
+                    if (na < 4) a[na] = c;
+                    na++;
+                }
+            if (na >= 1 && na <= 4 && a[0] != 0) {
+                for (uint32_t k = na; k < 4; k++) a[k] = a[na - 1];
+                ss_tuning t = *best_out;
+                t.alphabet = a[0] | a[1] << 8 | a[2] << 16 | a[3] << 24;
+                ok = try_one(t);
+            }
+        }
     } while (0);
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);

@@ -409,11 +409,16 @@ __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32
 // every LCP and the task ends there; only segments with equal keys that
 // continue past these 8 characters go through the group rounds below.
 // CTAs per SM the register budget must allow: as many as the shared memory
-// of each class lets in (BaseSmem: about 7, 28 and 56 KB)
-constexpr int base_min_ctas(int nt) { return nt >= 256 ? 4 : nt >= 128 ? 7 : 16; }
+// (228 KB per SM, 1 KB of it reserved per CTA) and the 2048 threads of an SM
+// let in, but no fewer than 64 registers per thread
+constexpr int base_min_ctas(int nt, size_t smem) {
+    const int by_smem = (int)(233472 / (smem + 1024)), by_threads = 2048 / nt, by_regs = 65536 / (64 * nt);
+    const int m = by_smem < by_threads ? by_smem : by_threads;
+    return m < by_regs ? (m > 0 ? m : 1) : by_regs;
+}
 
 template <int NT, int ITEMS, bool A>
-__global__ void __launch_bounds__(NT, base_min_ctas(NT)) k_base_cta(const SmallTask *tasks, const uint32_t *ntask_dev, uint32_t *next_task,
+__global__ void __launch_bounds__(NT, base_min_ctas(NT, sizeof(BaseSmem<NT, ITEMS>))) k_base_cta(const SmallTask *tasks, const uint32_t *ntask_dev, uint32_t *next_task,
                                                  const ReqDesc *reqs, ElemBufs eb, SmallTask *tiny, uint32_t tiny_cap,
                                                  uint32_t *counters) {
     constexpr uint32_t CAP = NT * ITEMS;

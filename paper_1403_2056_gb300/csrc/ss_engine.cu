@@ -156,16 +156,18 @@ struct Carve {
     }
 };
 
-static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np);
+static size_t carve_size(size_t N, uint32_t nreq, uint32_t min_small, Caps &caps, size_t &np);
 
 size_t engine_scratch_bytes(size_t N, uint32_t nreq) {
     Caps caps;
     size_t np;
-    return carve_size(N, nreq, caps, np);
+    return carve_size(N, nreq, kSmallMax, caps, np);
 }
 
-static size_t carve_size(size_t N, uint32_t nreq, Caps &caps, size_t &np) {
-    caps.big = (uint32_t)(N / (kSmallMax + 1) + nreq + 1);
+// min_small: the smallest base-case threshold of the requests (a big segment
+// holds more strings than its request's threshold)
+static size_t carve_size(size_t N, uint32_t nreq, uint32_t min_small, Caps &caps, size_t &np) {
+    caps.big = (uint32_t)(N / (min_small + 1) + nreq + 1);
     for (int c = 0; c < kClasses; c++) {   // disjoint tasks of at least class_max(c - 1) + 1 strings
         size_t least = c == 0 ? 2 : class_max(c - 1) + 1;
         caps.small[c] = (uint32_t)(N / least + nreq + 1);
@@ -271,7 +273,9 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st, bool asy
     }
     Caps caps;
     size_t np;
-    size_t bytes = carve_size(N, nreq, caps, np);
+    uint32_t min_small = kSmallMax;
+    for (const auto &r : reqs) min_small = std::min(min_small, req_small_max(r));
+    size_t bytes = carve_size(N, nreq, min_small, caps, np);
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
     if (e != cudaSuccess) {
@@ -321,11 +325,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st, bool asy
     for (uint32_t r = 0; r < nreq; r++) {
         const ReqDesc &q = reqs[r];
         if (q.n < 2) continue;
-        if (q.n > kSmallMax) {
+        if (q.n > req_small_max(q)) {
             BigSeg s{};
             s.begin = q.base; s.size = q.n; s.depth = 0; s.req = r;
             big0.push_back(s);
-            uint32_t d = choose_d(q.n, req_child_target(q)), t = tiles_of(q.n), B = buckets_of(d);
+            uint32_t d = req_choose_d(q.n, q), t = tiles_of(q.n), B = buckets_of(d);
             tiles0 += t; counts0 += B * t; pairs0 += B;
         } else {
             SmallTask t{q.base, q.n, 0, r, 0, 0};
@@ -682,6 +686,47 @@ int engine_gather(const ReqDesc &r, const uint32_t *depth, uint64_t *keys_out, c
     cudaError_t e = cudaGetLastError();
     if (!e) e = cudaStreamSynchronize(st);
     return e ? cuda_fail(e, "gather") : SS_OK;
+}
+
+// byte set of the first n strings of a fixed-length request (the autotuner's
+// alphabet test): one string per thread, the warp's sets OR-ed together
+__global__ void __launch_bounds__(256) k_byte_set(ReqDesc r, uint32_t n, uint32_t *mask) {
+    uint32_t m[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint8_t *p = r.chars + r.offsets[i];
+        for (uint32_t j = 0; j < r.fixed_len; j++) {
+            const uint32_t c = p[j];
+            m[c >> 5] |= 1u << (c & 31);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 8; k++) {
+        const uint32_t v = __reduce_or_sync(0xffffffffu, m[k]);
+        if ((threadIdx.x & 31) == 0 && v) atomicOr(mask + k, v);
+    }
+}
+
+int engine_byte_set(const ReqDesc &r, uint32_t n, uint32_t mask[8], cudaStream_t st) {
+    for (int k = 0; k < 8; k++) mask[k] = 0;
+    if (n == 0 || r.fixed_len == 0 || r.lengths) return SS_OK;
+    void *block = nullptr;
+    cudaError_t e = scratch_alloc(&block, 256, st);
+    if (e) {
+        cudaGetLastError();
+        set_error_detail("byte set: scratch allocation failed");
+        return SS_ERR_OOM;
+    }
+    uint32_t *d_mask = (uint32_t *)block;
+    uint32_t grid = std::min<uint32_t>((n + 255) / 256, (uint32_t)sm_count() * 8);
+    do {
+        if ((e = cudaMemsetAsync(d_mask, 0, 32, st))) break;
+        SS_LAUNCH("byte_set", st, k_byte_set<<<grid, 256, 0, st>>>(r, n, d_mask));
+        if ((e = cudaGetLastError())) break;
+        if ((e = cudaMemcpyAsync(mask, d_mask, 32, cudaMemcpyDeviceToHost, st))) break;
+        e = cudaStreamSynchronize(st);
+    } while (0);
+    scratch_free(block, st);
+    return e ? cuda_fail(e, "byte set") : SS_OK;
 }
 
 }  // namespace ss

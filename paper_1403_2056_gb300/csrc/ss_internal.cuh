@@ -67,7 +67,8 @@ struct ReqDesc {
     uint32_t n;
     uint32_t base;             // global position of the request's first element
     uint32_t tune;             // log2 child target (bits 0..7) | minimum depth step (bits 8..15) |
-                               // classifier (bits 16..17); 0: defaults
+                               // classifier (bits 16..17) | largest tree depth of a level (bits 20..23) |
+                               // log2 base-case threshold (bits 24..27); 0 fields: defaults
     uint32_t *perm_out;
     uint32_t *lcp_out;
     int32_t *status_out;
@@ -84,6 +85,16 @@ __host__ __device__ __forceinline__ uint32_t req_child_target(const ReqDesc &r) 
 __host__ __device__ __forceinline__ uint32_t req_min_step(const ReqDesc &r) {
     const uint32_t m = (r.tune >> 8) & 0xFFu;
     return m ? m : (uint32_t)SS_MIN_STEP;
+}
+// Largest tree depth of a sort level (<= kLevelD) and the largest segment a
+// base case takes (<= kSmallMax; larger segments get another level).
+__host__ __device__ __forceinline__ uint32_t req_max_depth(const ReqDesc &r) {
+    const uint32_t d = (r.tune >> 20) & 0xFu;
+    return d ? d : (uint32_t)kLevelD;
+}
+__host__ __device__ __forceinline__ uint32_t req_small_max(const ReqDesc &r) {
+    const uint32_t s = (r.tune >> 24) & 0xFu;
+    return s ? (1u << s) : kSmallMax;
 }
 
 // How k_classify finds a key's bucket (every classifier gives the bucket of
@@ -531,6 +542,9 @@ void *host_staging(size_t bytes);
 // async: levels driven by the device scheduler, the call returns at once
 int engine_sort(const ReqDesc *reqs_host, uint32_t count, cudaStream_t stream, bool async = false);
 size_t engine_scratch_bytes(size_t N, uint32_t nreq);
+// the bytes of the first n strings of a fixed-length request, as a 256-bit
+// set (mask[c / 32] bit c % 32); returns when done
+int engine_byte_set(const ReqDesc &r, uint32_t n, uint32_t mask[8], cudaStream_t st);
 int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *offsets_host, const uint32_t *lengths_host,
               uint32_t fixed_len, uint32_t n, uint32_t runs, uint32_t *perm_host, uint32_t *lcp_host, cudaStream_t st);
 int engine_classify(const uint64_t *keys, uint32_t n, const uint64_t *x, uint32_t d, uint32_t classifier,

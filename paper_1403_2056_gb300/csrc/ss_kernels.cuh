@@ -13,14 +13,17 @@
 
 // --------------------------------------------------------------- helpers
 
-__host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size, uint32_t target) {
-    // v + 1 = 2^d about size / target, d in [2, kLevelD]
+__host__ __device__ __forceinline__ uint32_t choose_d(uint32_t size, uint32_t target, uint32_t cap) {
+    // v + 1 = 2^d about size / target, d in [2, cap], cap <= kLevelD
     uint32_t q = (size + target - 1) / target;
     uint32_t d = 0;
     while ((1u << d) < q) d++;
     if (d < 2) d = 2;
-    if (d > (uint32_t)kLevelD) d = kLevelD;
+    if (d > cap) d = cap;
     return d;
+}
+__host__ __device__ __forceinline__ uint32_t req_choose_d(uint32_t size, const ReqDesc &r) {
+    return choose_d(size, req_child_target(r), req_max_depth(r));
 }
 
 // Depth step of the even bucket between splitters x_{r-1} and x_r: its strings
@@ -310,7 +313,7 @@ static_assert(kAlphaCapped >= 2 && (kAlphaCapped & (kAlphaCapped - 1)) == 0 &&
               "the sample of a capped tree fits the tree builder's buffer");
 
 __device__ __forceinline__ uint32_t sample_alpha(uint32_t size, uint32_t d, uint32_t target) {
-    return (d == (uint32_t)kLevelD && size / target > (1u << d)) ? kAlphaCapped : 2u;
+    return size / target > (1u << d) ? kAlphaCapped : 2u;
 }
 __global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const ReqDesc *reqs, const uint64_t *key,
                                                            uint64_t *splitters) {
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kThreads) k_build_trees(BigSeg *segs, const Re
     TreeSmem &S = *reinterpret_cast<TreeSmem *>(smem_raw);
     __shared__ uint32_t distinct;
     BigSeg sg = segs[blockIdx.x];
-    const uint32_t dmax = choose_d(sg.size, req_child_target(reqs[sg.req]));
+    const uint32_t dmax = req_choose_d(sg.size, reqs[sg.req]);
     const uint32_t alpha = sample_alpha(sg.size, dmax, req_child_target(reqs[sg.req]));
     uint32_t v = (1u << dmax) - 1;
     uint32_t a = alpha * (v + 1) - 1;   // alpha * v + alpha - 1
@@ -464,8 +467,15 @@ __device__ __forceinline__ void emit_bucket(uint32_t *cnt, uint16_t *obuf, uint3
 
 // The classifier is the segment's request's (or `cls` for all segments when
 // reqs is NULL); jt holds the jump tables of CLS_JUMP segments.
+// CTAs per SM the classifier's registers must allow: 4 (64 registers, the 16
+// keys of a thread in flight) measured faster than the 2 that 95 registers
+// leave room for
+#ifndef SS_CLASSIFY_MINB
+#define SS_CLASSIFY_MINB 4
+#endif
+
 template <int D>
-__global__ void __launch_bounds__(kThreads) k_classify(const BigSeg *__restrict__ segs, uint32_t nseg,
+__global__ void __launch_bounds__(kThreads, SS_CLASSIFY_MINB) k_classify(const BigSeg *__restrict__ segs, uint32_t nseg,
                                                        const ReqDesc *__restrict__ reqs, uint32_t cls_all,
                                                        const uint64_t *__restrict__ key,
                                                        const uint64_t *__restrict__ splitters,
@@ -1017,13 +1027,13 @@ __global__ void __launch_bounds__(kThreads) k_buckets(const BigSeg *segs, uint32
             set_error(counters, E_GATHER_OVERFLOW, k);
         }
     }
-    if (size > kSmallMax) {
+    if (size > req_small_max(reqs[sg.req])) {
         uint32_t k = atomicAdd(counters + C_NBIG, 1u);
         if (k < caps.big) {
             BigSeg c{};
             c.begin = st; c.size = size; c.depth = depth; c.req = sg.req;
             next_big[k] = c;
-            uint32_t d = choose_d(size, req_child_target(reqs[sg.req])), t = tiles_of(size), Bc = buckets_of(d);
+            uint32_t d = req_choose_d(size, reqs[sg.req]), t = tiles_of(size), Bc = buckets_of(d);
             atomicAdd(counters + C_TILES, t);
             atomicAdd(counters + C_COUNTS, Bc * t);
             atomicAdd(counters + C_PAIRS, Bc);

@@ -69,8 +69,10 @@ def test_tuning_ranges_checked_on_the_host():
     q = P.Request(1, 1, None, 0, 5, 1, 1, None)   # pointers are never dereferenced: the check fails first
     arr = (P.Request * 1)(q)
     # alphabets: unsorted, a zero byte, or a request that is not fixed-length (q is NUL-terminated)
+    # max_depth outside [2, 8]; small_max not a power of two in [64, 2048]
     for bad in [(48, 0, 0), (16, 0, 0), (1 << 17, 0, 0), (0, 10, 0), (0, 0, 3), (0, 0, 0, 0x41434700),
-                (0, 0, 0, 0x41474341), (0, 0, 0, 0x54474341)]:
+                (0, 0, 0, 0x41474341), (0, 0, 0, 0x54474341), (0, 0, 0, 0, 1), (0, 0, 0, 0, 9),
+                (0, 0, 0, 0, 0, 32), (0, 0, 0, 0, 0, 4096), (0, 0, 0, 0, 0, 1000)]:
         t = (P.Tuning * 1)(P.Tuning(*bad))
         rc = P.lib().ss_sort_batch_tuned(C.cast(arr, C.c_void_p), C.cast(t, C.c_void_p), 1, None)
         assert rc == -1, bad

@@ -427,7 +427,8 @@ def test_batch_with_different_shared_prefixes():
 
 # ------------------------------------------------------------- tuning
 @pytest.mark.parametrize("tuning", [(256, 1), (2048, 9), (32, 3), (65536, 5), (0, 0), (0, 0, 1), (0, 0, 2),
-                                    (32, 1, 2), (2048, 9, 1)])
+                                    (32, 1, 2), (2048, 9, 1), (0, 0, 0, 0, 2), (0, 0, 0, 0, 6), (0, 0, 0, 0, 0, 64),
+                                    (256, 1, 0, 0, 3, 512), (0, 0, 2, 0, 7, 1024)])
 def test_tunings_do_not_change_results(tuning):
     """Any tuning gives the same order and LCPs (the oracle's)."""
     import torch
@@ -457,11 +458,32 @@ def test_autotune_picks_a_candidate_and_leaves_outputs():
     chars, offsets, _ = to_device(ss)
     perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
     lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
-    (ct, ms_step, cls), ms = P.ss_autotune(dict(chars=chars, offsets=offsets, lengths=None, fixed_len=0, n=ss.n,
-                                           perm_out=perm, lcp_out=lcp), sample_n=200_000)
+    (ct, ms_step, cls, alpha, md, sm), ms = P.ss_autotune(dict(chars=chars, offsets=offsets, lengths=None,
+                                                          fixed_len=0, n=ss.n, perm_out=perm, lcp_out=lcp),
+                                                     sample_n=200_000)
     assert ct in (256, 512, 1024, 2048) and ms_step in (1, 3, 5, 9) and cls in (0, 1, 2) and ms > 0
+    assert alpha == 0 and md in (0, 6, 7) and sm in (0, 512, 1024)   # NUL-terminated: no alphabet candidate
     torch.cuda.synchronize()
     assert int((perm != -1).sum().item()) == 0 and int((lcp != -1).sum().item()) == 0
+
+
+def test_autotune_tries_the_alphabet_of_fixed_length_strings():
+    """Fixed-length strings over four bytes: the alphabet candidate is found
+    from the sample's bytes; whatever is picked sorts like the oracle."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = W.dna_windows(200_000, 4_000_100, 100, seed=45)
+    chars, offsets, _ = to_device(ss)
+    perm = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    lcp = torch.full((ss.n,), -1, dtype=torch.int32, device="cuda:0")
+    q = dict(chars=chars, offsets=offsets, lengths=None, fixed_len=ss.fixed_len, n=ss.n, perm_out=perm, lcp_out=lcp)
+    best, ms = P.ss_autotune(q, sample_n=100_000)
+    assert best[3] in (0, P.alphabet(b"ACGT")) and ms > 0
+    P.ss_sort_batch_tuned([q], [best])
+    torch.cuda.synchronize()
+    want_perm, want_lcp = oracle.sort(ss)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
+    assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
 
 
 def test_readme_example():
