@@ -48,90 +48,108 @@ __device__ __forceinline__ WElem shfl_xor_welem(const WElem &e, int m) {
     return r;
 }
 
-// Sort one group of m <= 32 strings completely with one warp (all 32 lanes
-// call this), 16 characters per round.  Lane l < m holds string index `id`
-// (string offset `off`) and its 16 characters at `depth`.  Writes perm and lcp
-// of R-local positions out .. out + m - 1 (not the lcp of position `out`,
-// which the caller owns).
+// Sort groups of at most W strings completely, W in {4, 8, 16, 32}: the warp
+// holds 32 / W groups side by side, group s on lanes sW .. sW + W - 1, and
+// sorts them all at once, 16 characters per round (a group of a few strings
+// whose duplicates need many rounds no longer holds a whole warp).  Lane l
+// with l % W < m holds string index `id` (string offset `off`) and its 16
+// characters at `depth`; m, depth, out and R are its group's.  mmax, the
+// largest m of the warp, bounds the sorting network (all lanes call this).
+// Writes perm and lcp of R-local positions out .. out + m - 1 (not the lcp of
+// position `out`, which the caller owns).
 template <bool A>
-__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t m, uint32_t depth, uint32_t id, uint64_t off,
-                                            uint64_t k0, uint64_t k1, uint32_t out) {
-    const uint32_t lane = threadIdx.x & 31;
+__device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t W, uint32_t m, uint32_t mmax, uint32_t depth,
+                                            uint32_t id, uint64_t off, uint64_t k0, uint64_t k1, uint32_t out) {
+    const uint32_t lane = threadIdx.x & 31, ls = lane & (W - 1);
     const uint32_t kc = key_chars(R);   // characters per key
     WElem e;
-    if (lane < m) { e.g = 0; e.i = id; e.o = off; e.k0 = k0; e.k1 = k1; }
+    if (ls < m) { e.g = 0; e.i = id; e.o = off; e.k0 = k0; e.k1 = k1; }
     else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.o = 0; e.k0 = ~0ull; e.k1 = ~0ull; }
     uint32_t lcp = 0;
     for (;;) {
-        for (int k = 2; k <= 32; k <<= 1) {
-            if ((uint32_t)(k >> 1) >= m && k > 2) break;   // lanes >= m hold padding only
-            for (int j = k >> 1; j > 0; j >>= 1) {
-                WElem o = shfl_xor_welem(e, j);
-                bool up = (lane & k) == 0;
-                bool lower = (lane & j) == 0;
+        // bitonic network inside each group's lanes (xor partners below W stay
+        // in the group); after the stage of size k >= mmax the first k lanes of
+        // every group are ascending and hold all its strings
+        for (uint32_t k = 2; k <= W; k <<= 1) {
+            if ((k >> 1) >= mmax && k > 2) break;   // lanes >= m hold padding only
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                WElem o = shfl_xor_welem(e, (int)j);
+                bool up = (ls & k) == 0;
+                bool lower = (ls & j) == 0;
                 bool take_o = lower == up ? welem_less(o, e) : welem_less(e, o);
                 if (take_o) e = o;
             }
         }
-        uint32_t pg = __shfl_up_sync(0xffffffffu, e.g, 1);
-        uint64_t p0 = __shfl_up_sync(0xffffffffu, e.k0, 1);
-        uint64_t p1 = __shfl_up_sync(0xffffffffu, e.k1, 1);
+        const int w = (int)W;
+        uint32_t pg = __shfl_up_sync(0xffffffffu, e.g, 1, w);
+        uint64_t p0 = __shfl_up_sync(0xffffffffu, e.k0, 1, w);
+        uint64_t p1 = __shfl_up_sync(0xffffffffu, e.k1, 1, w);
         bool start = true;
-        if (lane > 0 && lane < m && pg == e.g) {
+        if (ls > 0 && ls < m && pg == e.g) {
             if (p0 != e.k0) lcp = depth + key_lcp<A>(R, p0, e.k0);
             else if (key_ends<A>(R, e.k0, depth)) lcp = depth + key_len<A>(R, e.k0, depth);
             else if (p1 != e.k1) lcp = depth + kc + key_lcp<A>(R, p1, e.k1);
             else if (key_ends<A>(R, e.k1, depth + kc)) lcp = depth + kc + key_len<A>(R, e.k1, depth + kc);
             else start = false;
         }
-        if (lane >= m) start = true;
-        uint32_t sg = start ? lane : 0;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            uint32_t y = __shfl_up_sync(0xffffffffu, sg, o);
-            if (lane >= (uint32_t)o) sg = max(sg, y);
+        if (ls >= m) start = true;
+        uint32_t sg = start ? ls : 0;
+        for (uint32_t o = 1; o < W; o <<= 1) {
+            uint32_t y = __shfl_up_sync(0xffffffffu, sg, o, w);
+            if (ls >= o) sg = max(sg, y);
         }
-        bool next_start = __shfl_down_sync(0xffffffffu, start, 1) || lane == 31;
-        bool active = lane < m && !(start && next_start);
-        if (lane < m) e.g = sg;
+        bool next_start = __shfl_down_sync(0xffffffffu, start, 1, w) || ls == W - 1;
+        bool active = ls < m && !(start && next_start);
+        if (ls < m) e.g = sg;
         if (!__any_sync(0xffffffffu, active)) break;
         depth += 2 * kc;
         if (active) key2_at<A>(R, e.i, e.o, depth, e.k0, e.k1);
     }
-    if (lane < m) {
-        R.perm_out[out + lane] = e.i;
-        if (lane > 0) R.lcp_out[out + lane] = lcp;
+    if (ls < m) {
+        R.perm_out[out + ls] = e.i;
+        if (ls > 0) R.lcp_out[out + ls] = lcp;
     }
 }
 
-// Tiny base cases (2..32 strings), one warp each.  The task count is read on
-// the device: the CTA base cases below append groups to the same list.
+// Tiny base cases (2..32 strings).  The task count is read on the device: the
+// CTA base cases below append groups to the same list.  A warp takes the tasks
+// in slots of 8: the largest of a slot sets the lanes per group W (4, 8, 16 or
+// 32), and the slot's tasks go through the warp 32 / W at a time.
 template <bool A>
 __global__ void __launch_bounds__(kThreads) k_small_warp(const SmallTask *tasks, const uint32_t *ntask_dev,
                                                          const ReqDesc *reqs, ElemBufs eb) {
+    constexpr uint32_t kSlot = 8;
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
     const uint32_t ntask = *ntask_dev;
-    for (uint32_t tk = gw; tk < ntask; tk += nw) {
-        SmallTask t = tasks[tk];
-        const uint32_t *idx = eb.idx[t.parity];
-        const uint64_t *soff = eb.soff[t.parity];
-        const uint64_t *key = eb.key[t.parity];
-        const ReqDesc &R = reqs[t.req];
-        uint32_t id = 0;
-        uint64_t off = 0, k0 = 0, k1 = 0;
-        if (lane < t.size) {
-            id = idx[t.begin + lane];
-            off = soff[t.begin + lane];
-            if (t.gather) {
-                key2_at<A>(R, id, off, t.depth, k0, k1);
-            } else {
-                k0 = key[t.begin + lane];
-                k1 = key_ends<A>(R, k0, t.depth) ? 0ull : key_at<A>(R, id, off, t.depth + key_chars(R));
+    for (uint32_t t0 = gw * kSlot; t0 < ntask; t0 += nw * kSlot) {
+        const uint32_t nt = min(kSlot, ntask - t0);
+        const uint32_t smax = __reduce_max_sync(0xffffffffu, lane < nt ? tasks[t0 + lane].size : 0u);
+        const uint32_t W = smax <= 4 ? 4u : smax <= 8 ? 8u : smax <= 16 ? 16u : 32u;
+        for (uint32_t b = 0; b < nt; b += 32 / W) {
+            const uint32_t q = b + lane / W, ls = lane & (W - 1);
+            SmallTask t{0u, 0u, 0u, 0u, 0u, 0u};
+            if (q < nt) t = tasks[t0 + q];
+            const uint32_t mmax = __reduce_max_sync(0xffffffffu, t.size);
+            const uint32_t *idx = eb.idx[t.parity];
+            const uint64_t *soff = eb.soff[t.parity];
+            const uint64_t *key = eb.key[t.parity];
+            const ReqDesc &R = reqs[t.req];
+            uint32_t id = 0;
+            uint64_t off = 0, k0 = 0, k1 = 0;
+            if (ls < t.size) {
+                id = idx[t.begin + ls];
+                off = soff[t.begin + ls];
+                if (t.gather) {
+                    key2_at<A>(R, id, off, t.depth, k0, k1);
+                } else {
+                    k0 = key[t.begin + ls];
+                    k1 = key_ends<A>(R, k0, t.depth) ? 0ull : key_at<A>(R, id, off, t.depth + key_chars(R));
+                }
             }
+            warp_finish<A>(R, W, t.size, mmax, t.depth, id, off, k0, k1, t.begin - R.base);
         }
-        warp_finish<A>(R, t.size, t.depth, id, off, k0, k1, t.begin - R.base);
     }
 }
 

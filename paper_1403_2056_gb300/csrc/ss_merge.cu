@@ -92,14 +92,36 @@ __device__ __forceinline__ PairView pair_view(const ReqDesc &S, uint32_t p, cons
 
 // merge path: number of strings taken from A among the first diag outputs
 // (A first on ties), searched in [lo, hi); all compared strings share h characters
-__device__ __forceinline__ uint32_t path_search(const ReqDesc &S, const PairView &v, uint32_t diag, uint32_t lo,
-                                                uint32_t hi, uint32_t h) {
+// Merge-path search on diagonal diag inside [lo, hi), comparing from depth h.
+// The probe that set the final lo (at i - 1, against B[diag - i]) and the one
+// that set the final hi (at i, against B[diag - i - 1]) leave their LCPs in
+// *la / *lb, each with a flag (false: that bound was never moved).
+struct PathEnd {
+    uint32_t i, la, lb;
+    bool has_la, has_lb;
+};
+__device__ __forceinline__ PathEnd path_search_lcp(const ReqDesc &S, const PairView &v, uint32_t diag, uint32_t lo,
+                                                   uint32_t hi, uint32_t h) {
+    PathEnd r{0u, 0u, 0u, false, false};
     while (lo < hi) {
         uint32_t mid = (lo + hi) / 2;
         uint32_t l, bj = diag - 1 - mid;
-        if (str_cmp_from(S, v.A(mid), v.OA(mid), v.B(bj), v.OB(bj), h, &l) <= 0) lo = mid + 1; else hi = mid;
+        if (str_cmp_from(S, v.A(mid), v.OA(mid), v.B(bj), v.OB(bj), h, &l) <= 0) {
+            lo = mid + 1;
+            r.la = l;
+            r.has_la = true;
+        } else {
+            hi = mid;
+            r.lb = l;
+            r.has_lb = true;
+        }
     }
-    return lo;
+    r.i = lo;
+    return r;
+}
+__device__ __forceinline__ uint32_t path_search(const ReqDesc &S, const PairView &v, uint32_t diag, uint32_t lo,
+                                                uint32_t hi, uint32_t h) {
+    return path_search_lcp(S, v, diag, lo, hi, h).i;
 }
 
 // string offset of every run entry, for the first round
@@ -435,10 +457,10 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_starts(
     uint32_t lo = diag > nb ? diag - nb : 0, hi = min(diag, na);
     const uint32_t k = diag / kCoarse, e = cbase[p] + k, dc = k * kCoarse;
     const uint32_t i0 = C[e].i, j0 = dc - i0;
-    uint32_t i1 = na, j1 = nb, hw = 0, i;
+    uint32_t i1 = na, j1 = nb, hw = 0;
+    PathEnd pe{i0, 0u, 0u, false, false};
     bool win = true;
     if (dc == diag) {
-        i = i0;
         win = false;   // exact cut: no search, no shared prefix needed
     } else {
         const uint32_t dce = min(dc + kCoarse, len);
@@ -447,17 +469,25 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_starts(
         hw = C[e].h;
         lo = max(lo, max(i0, diag > j1 ? diag - j1 : 0u));
         hi = min(hi, min(i1, diag - j0));
-        i = path_search(S, v, diag, lo, hi, hw);
+        pe = path_search_lcp(S, v, diag, lo, hi, hw);
     }
-    const uint32_t j = diag - i;
+    const uint32_t i = pe.i, j = diag - i;
     auto inA = [&](uint32_t x) { return win && x >= i0 && x < i1; };
     auto inB = [&](uint32_t y) { return win && y >= j0 && y < j1; };
     uint32_t ha = 0, hb = 0;
     if (diag > 0) {
-        bool last_is_b;
-        if (i == 0) last_is_b = true;
-        else if (j == 0) last_is_b = false;
-        else {
+        // which of A[i - 1] and B[j - 1] is output last.  The search's last
+        // probes give lb = lcp(A[i], B[j - 1]) (B[j - 1] < A[i]) and
+        // la = lcp(A[i - 1], B[j]) (A[i - 1] <= B[j]); with the run LCPs
+        // HA[i] = lcp(A[i - 1], A[i]) and HB[j] = lcp(B[j - 1], B[j]), of two
+        // strings below the same string the one that shares more with it is
+        // the larger, so unequal LCPs decide without reading a string
+        bool last_is_b = false, known = false;
+        if (i == 0) { last_is_b = true; known = true; }
+        else if (j == 0) { last_is_b = false; known = true; }
+        else if (pe.has_lb && i < na && v.HA[i] != pe.lb) { last_is_b = v.HA[i] < pe.lb; known = true; }
+        else if (pe.has_la && j < nb && v.HB[j] != pe.la) { last_is_b = v.HB[j] > pe.la; known = true; }
+        if (!known) {
             uint32_t l;
             uint32_t h0 = (inA(i - 1) && inB(j - 1)) ? hw : 0u;
             last_is_b = str_cmp_from(S, v.A(i - 1), v.OA(i - 1), v.B(j - 1), v.OB(j - 1), h0, &l) <= 0;   // ties: A then B
@@ -467,10 +497,12 @@ __global__ void __launch_bounds__(kMergeTileThreads) k_merge_starts(
         const bool prev_in = last_is_b ? inB(j - 1) : inA(i - 1);
         if (i < na) {
             if (!last_is_b) ha = v.HA[i];
+            else if (pe.has_lb) ha = pe.lb;   // lcp(B[j - 1], A[i]) from the probe at i
             else { uint32_t l; str_cmp_from(S, prev, prev_o, v.A(i), v.OA(i), (prev_in && inA(i)) ? hw : 0u, &l); ha = l; }
         }
         if (j < nb) {
             if (last_is_b) hb = v.HB[j];
+            else if (pe.has_la) hb = pe.la;   // lcp(A[i - 1], B[j]) from the probe at i - 1
             else { uint32_t l; str_cmp_from(S, prev, prev_o, v.B(j), v.OB(j), (prev_in && inB(j)) ? hw : 0u, &l); hb = l; }
         }
     }
