@@ -294,25 +294,33 @@ struct BaseSmem {
     uint64_t wmin[NT / 32], wmax[NT / 32];   // smallest and largest key of each warp's slots
     uint32_t wsum[NT / 32];
     uint32_t nwl, nws, wbase;   // small groups, their strings, first reserved list slot
+    uint32_t sigma;          // first round: distinct bytes after the keys' common prefix
     uint32_t task, next;     // task taken from the queue, and the one after it
 };
 
 // First round by one counting pass (the adaptivity of Section 8.1: when the
 // keys of a segment are spread, distribute by a digit as radix sort does).
-// The digit is the key's place in the segment's key range [kmin, kmax] scaled
-// to 2^B >= m values (fixed point, below: d < 2^B, monotone in the key); keys
-// spread evenly over their range (a bucket between two splitters) fill the
-// digits evenly wherever the range lies, where the bits after the keys' common
-// prefix would leave most digits empty when the range straddles a power of
-// two.  One shared-memory histogram, scan and placement put the segment in
+// The digit has 2^B >= m values and is monotone in the key: the key's place
+// in the segment's key range [kmin, kmax] (fixed point, below), or for keys
+// of a small alphabet the ranks of its bytes (below).  Keys spread evenly over
+// their range (a bucket between two splitters) fill the interpolation digits
+// evenly wherever the range lies, where the bits after the keys' common prefix
+// would leave most digits empty when the range straddles a power of two.
+// One shared-memory histogram, scan and placement put the segment in
 // digit order; each digit's strings (at most kRadixBucketMax, otherwise the
 // merge sort below is used instead) are then put in (key, original index)
 // order by insertion sort.  kin holds the keys of this thread's slots
 // tid + r NT (SK holds all of them by position).  On success SK / SP hold the
 // segment sorted by (key, original index) by position and true is returned;
-// false leaves SK untouched and SP unset (all keys equal, keys of a sparse
-// alphabet, or a digit too full).  Every thread of the CTA calls this.
+// false leaves SK untouched and SP unset (all keys equal, or a digit too
+// full).  Every thread of the CTA calls this.
 constexpr uint32_t kRadixBucketMax = 8;
+// 1: the rank digit for keys of a small alphabet, the interpolation digit
+// otherwise; 0: keys of a small alphabet go to the merge sort; 2: always the
+// rank digit
+#ifndef SS_RADIX_RANK
+#define SS_RADIX_RANK 1
+#endif
 
 template <int NT, int ITEMS>
 __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32_t m, const uint64_t (&kin)[ITEMS]) {
@@ -354,28 +362,78 @@ __device__ __forceinline__ bool radix_first_round(BaseSmem<NT, ITEMS> &S, uint32
     uint32_t B = 1;
     while ((1u << B) < m) B++;
     const uint32_t nb = 1u << B;   // <= NT * ITEMS
-    // keys of a small alphabet (some bits of every byte fixed) fill a digit
-    // space unevenly: when fewer than B - 1 of the B bits after the common
-    // prefix vary among the keys, the merge sort is used without trying
-    if ((uint32_t)__popcll((x << cp) >> (64 - B)) + 1 < B) return false;
-    // the range normalised: span << L in [2^63, 2^64), sh its top 32 bits;
-    // M = 2^44 / (sh + 1) * (1 - 2^-20 + 2^-22) at most (the float quotient is
-    // within 2^-23 of the exact one), so ((t >> 32) * M) < 2^44 for every
-    // t = (key - kmin) << L <= span << L, and M >= 4094 keeps the digits even
-    // to 1 part in 4096
-    const uint64_t span = kmx - kmn;   // > 0: the keys are not all equal
-    const uint32_t L = (uint32_t)__clzll((long long)span);
-    const uint32_t sh = (uint32_t)((span << L) >> 32);
-    const uint32_t M = (uint32_t)__float2uint_rz(17592186044416.0f / (__uint2float_rn(sh) + 1.0f) *
-                                                 (1.0f - 1.0f / 1048576.0f));
+    // Keys whose B bits after the common prefix nearly all vary get the
+    // interpolation digit.  Keys of a small alphabet (some bits of every byte
+    // fixed) would fill that digit space unevenly; they get a rank digit: each
+    // byte from the first differing one on is replaced by its rank among the
+    // byte values the segment's keys use there (b = ceil(log2 sigma) bits for
+    // sigma values), and the ranks, concatenated, give the top B bits.  Ranks
+    // keep the byte order, so the digit is monotone in the key.
+    uint32_t d[ITEMS];
+    const bool dense = (uint32_t)__popcll((x << cp) >> (64 - B)) + 1 >= B;
+    if (dense && SS_RADIX_RANK != 2) {
+        // the range normalised: span << L in [2^63, 2^64), sh its top 32 bits;
+        // M = 2^44 / (sh + 1) * (1 - 2^-20 + 2^-22) at most (the float quotient
+        // is within 2^-23 of the exact one), so ((t >> 32) * M) < 2^44 for
+        // every t = (key - kmin) << L <= span << L, and M >= 4094 keeps the
+        // digits even to 1 part in 4096
+        const uint64_t span = kmx - kmn;   // > 0: the keys are not all equal
+        const uint32_t L = (uint32_t)__clzll((long long)span);
+        const uint32_t sh = (uint32_t)((span << L) >> 32);
+        const uint32_t M = (uint32_t)__float2uint_rz(17592186044416.0f / (__uint2float_rn(sh) + 1.0f) *
+                                                     (1.0f - 1.0f / 1048576.0f));
+#pragma unroll
+        for (int r = 0; r < ITEMS; r++) d[r] = (uint32_t)(((uint64_t)(uint32_t)(((k[r] - kmn) << L) >> 32) * M) >> (44 - B));
+    } else {
+        const uint32_t c0 = cp >> 3;   // bytes before c0 are the same in every key
+        // an alphabet of at most 16 byte values varies in at most 4 bits of a
+        // byte (e.g. A C G T: 4); text varies in more, and its first round is
+        // left to the merge sort
+        if (SS_RADIX_RANK == 0 || (SS_RADIX_RANK == 1 && (uint32_t)__popcll((long long)x) > 4 * (8 - c0) + 1))
+            return false;
+        uint16_t *rank = S.GS;   // free until the group rounds
+        for (uint32_t v = tid; v < 256; v += NT) rank[v] = 0;
+        __syncthreads();
+#pragma unroll
+        for (int r = 0; r < ITEMS; r++)
+            if (tid + r * NT < m)
+                for (uint32_t j = c0; j < 8; j++) rank[(uint32_t)(k[r] >> (56 - 8 * j)) & 0xFFu] = 1;
+        __syncthreads();
+        if (warp == 0) {   // rank of a byte value: the used values below it
+            uint32_t f[8], c = 0;
+#pragma unroll
+            for (int t = 0; t < 8; t++) { f[t] = rank[8 * lane + t]; c += f[t]; }
+            uint32_t incl = c;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= (uint32_t)o) incl += y;
+            }
+            uint32_t base = incl - c;
+#pragma unroll
+            for (int t = 0; t < 8; t++) { rank[8 * lane + t] = (uint16_t)base; base += f[t]; }
+            if (lane == 31) S.sigma = incl;
+        }
+        __syncthreads();
+        uint32_t bw = 1;   // bits per rank; sigma >= 2 (the keys differ in byte c0)
+        while ((1u << bw) < S.sigma) bw++;
+#pragma unroll
+        for (int r = 0; r < ITEMS; r++) {
+            uint32_t dd = 0, nbits = 0;
+            for (uint32_t j = c0; j < 8 && nbits < B; j++) {
+                dd = (dd << bw) | rank[(uint32_t)(k[r] >> (56 - 8 * j)) & 0xFFu];
+                nbits += bw;
+            }
+            d[r] = nbits >= B ? dd >> (nbits - B) : dd << (B - nbits);
+        }
+    }
     uint32_t *C = S.MG;
     for (uint32_t b = tid; b < nb; b += NT) C[b] = 0;
     __syncthreads();
-    uint32_t d[ITEMS], rk[ITEMS];
+    uint32_t rk[ITEMS];
 #pragma unroll
     for (int r = 0; r < ITEMS; r++) {
         const uint32_t i = tid + r * NT;
-        d[r] = (uint32_t)(((uint64_t)(uint32_t)(((k[r] - kmn) << L) >> 32) * M) >> (44 - B));
         rk[r] = i < m ? atomicAdd(&C[d[r]], 1u) : 0u;
     }
     __syncthreads();
