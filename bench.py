@@ -3,10 +3,12 @@
 
 One step is one pass of the whole hot path over the URL-like workload
 (n = 10,000,000 strings, seed 2): the set is cut into K = 4 index-contiguous
-runs, ss_sort_batch sorts the runs together (key gathers, splitter trees,
-classification, histograms, prefix sums, scatter, recursion, base case,
-LCP output), then ss_merge LCP-merges the runs into the final permutation
-and LCP array.  The result is identical to one ss_sort of the whole set.
+runs, ss_sort_batch_cached sorts the runs together (key gathers, splitter
+trees, classification, histograms, prefix sums, scatter, recursion, base
+case, LCP output, and each position's string offset and distinguishing
+characters), then ss_merge_cached LCP-merges the runs from those into the
+final permutation and LCP array.  The result is identical to one ss_sort of
+the whole set.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -226,15 +228,24 @@ def library_radix_context(P, torch, dev, stream, chars, offsets, n, reps=5):
                     "8 characters only, no LCPs; context, not a target"}
 
 
-def compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb, perm, lcp, reps=5, fixed_len=0):
+def compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb, perm, lcp, reps=5, fixed_len=0,
+                          cache=None):
     """The step's merge with each method of ss_merge_ex (pairwise rounds, the
-    default; one pass with LCP loser trees): median time of the call, the
-    kernels' times from the library's launch events, and whether the outputs
-    equal the default's (which perm / lcp hold on entry)."""
+    default; one pass with LCP loser trees) and, given the runs' sort caches,
+    ss_merge_cached (the step's merge): median time of the call, the kernels'
+    times from the library's launch events, and whether the outputs equal the
+    default's (which perm / lcp hold on entry)."""
     ref = torch.cat([perm, lcp]).clone()
     out = {}
-    for method, name in ((P.MERGE_PAIRWISE, "pairwise_rounds"), (P.MERGE_LOSER_TREE, "loser_tree")):
+    methods = [(P.MERGE_PAIRWISE, "pairwise_rounds"), (P.MERGE_LOSER_TREE, "loser_tree")]
+    if cache is not None:
+        methods.append((None, "pairwise_from_sort_caches"))
+    for method, name in methods:
         def m():
+            if method is None:
+                P.ss_merge_cached(chars, offsets, None, fixed_len, rperm, rlcp, *cache, rb, perm, lcp,
+                                  run_base=rb[:-1], stream=stream)
+                return
             P.ss_merge_ex(chars, offsets, None, fixed_len, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], method=method,
                           stream=stream)
         m()
@@ -770,15 +781,21 @@ def main():
     rlcp = torch.empty(n, dtype=torch.int32, device=dev)
     perm = torch.empty(n, dtype=torch.int32, device=dev)
     lcp = torch.empty(n, dtype=torch.int32, device=dev)
+    roff = torch.empty(n, dtype=torch.int64, device=dev)   # the runs' caches, from their sort to the merge
+    rck = torch.empty(n, dtype=torch.int64, device=dev)
+    rckd = torch.empty(n, dtype=torch.int32, device=dev)
     fl = ss.fixed_len
     reqs = [dict(chars=chars, offsets=offsets[int(rb[k]):int(rb[k + 1])], lengths=None, fixed_len=fl,
                  n=int(rb[k + 1] - rb[k]), perm_out=rperm[int(rb[k]):int(rb[k + 1])],
                  lcp_out=rlcp[int(rb[k]):int(rb[k + 1])]) for k in range(K)]
+    caches = [(roff[int(rb[k]):int(rb[k + 1])], rck[int(rb[k]):int(rb[k + 1])], rckd[int(rb[k]):int(rb[k + 1])])
+              for k in range(K)]
     stream = torch.cuda.current_stream(dev)
 
     def step():
-        P.ss_sort_batch(reqs, stream=stream)
-        P.ss_merge(chars, offsets, None, fl, rperm, rlcp, rb, perm, lcp, run_base=rb[:-1], stream=stream)
+        P.ss_sort_batch_cached(reqs, caches, stream=stream)
+        P.ss_merge_cached(chars, offsets, None, fl, rperm, rlcp, roff, rck, rckd, rb, perm, lcp, run_base=rb[:-1],
+                          stream=stream)
 
     def sort_only():
         P.ss_sort_ex(chars, offsets, None, fl, n, perm, lcp, stream=stream)
@@ -964,9 +981,10 @@ def main():
                        "equals_device_result": bool(same)}
 
     if rank == 0 and not args.no_extra:
-        line["merge_methods"] = dict(what="the step's merge of its runs by each method of ss_merge_ex",
+        line["merge_methods"] = dict(what="the step's merge of its runs by each method of ss_merge_ex, and from the "
+                                          "runs' sort caches (ss_merge_cached, the step's merge)",
                                      **compare_merge_methods(P, torch, dev, stream, chars, offsets, rperm, rlcp, rb,
-                                                             perm, lcp, fixed_len=fl))
+                                                             perm, lcp, fixed_len=fl, cache=(roff, rck, rckd)))
         line["classifiers"] = dict(what="the step's 4 runs sorted by one ss_sort_batch_tuned call per classifier",
                                    **compare_classifiers(P, torch, dev, stream, reqs))
         line["other_workloads"] = other_workloads(P, torch, dev, stream, peak)

@@ -215,6 +215,34 @@ int ss_sort_batch_async(const ss_request *reqs_host, const ss_tuning *tunings_ho
                         ss_stream_t stream);
 
 /*
+ * Distinguishing characters a sort hands to a later LCP merge (Section 5.4:
+ * the merge caches characters at each string's LCP; the sorter has already
+ * loaded them).  Device arrays of a request's n entries, written by the
+ * sort, per sorted position p:
+ *   off_out[p] = offsets[perm_out[p]];
+ *   ck_out[p]  = 8 characters of that string from depth ckd_out[p]
+ *                (big-endian, zero past its end), where
+ *                ckd_out[p] <= lcp_out[p] < ckd_out[p] + 8 or the string
+ *                ends before ckd_out[p] + 8 (position 0: depth 0).
+ * All three NULL: not written.
+ */
+typedef struct {
+    uint64_t *off_out;
+    uint64_t *ck_out;
+    uint32_t *ckd_out;
+} ss_sort_cache;
+
+/*
+ * ss_sort_batch_cached -- ss_sort_batch_tuned (tunings_host may be NULL)
+ * that also writes each request's caches (caches_host: `count` entries, or
+ * NULL for none) for ss_merge_cached.  Results and completion as
+ * ss_sort_batch_tuned.  SS_ERR_INVALID for a cache with only some of its
+ * arrays, or on a request with alphabet compression (caches hold bytes).
+ */
+int ss_sort_batch_cached(const ss_request *reqs_host, const ss_tuning *tunings_host,
+                         const ss_sort_cache *caches_host, uint32_t count, ss_stream_t stream);
+
+/*
  * ss_autotune -- picks a tuning for inputs like `req`'s: sorts its first
  * min(n, sample_n) strings (sample_n = 0: 2,000,000) with each of 22 or 23
  * candidate tunings, each step keeping the fastest so far: child_target
@@ -279,6 +307,20 @@ int ss_merge_ex(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uin
                 uint32_t fixed_len, const uint32_t *run_perm_dev, const uint32_t *run_lcp_dev,
                 const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K, uint32_t method,
                 uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
+
+/*
+ * ss_merge_cached -- ss_merge (pairwise rounds) of runs that a sort wrote
+ * with their caches (ss_sort_batch_cached, one request per run): run_off,
+ * run_ck, run_ckd are the runs' caches laid out as run_perm (run k at
+ * run_begin_host[k]).  The merge starts from them instead of loading every
+ * entry's string offset and characters itself.  Same results, completion
+ * and errors as ss_merge; NULL cache arrays return SS_ERR_INVALID.
+ */
+int ss_merge_cached(const uint8_t *chars_dev, const uint64_t *offsets_dev, const uint32_t *lengths_dev,
+                    uint32_t fixed_len, const uint32_t *run_perm_dev, const uint32_t *run_lcp_dev,
+                    const uint64_t *run_off_dev, const uint64_t *run_ck_dev, const uint32_t *run_ckd_dev,
+                    const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
+                    uint32_t *perm_out_dev, uint32_t *lcp_out_dev, ss_stream_t stream);
 
 /*
  * ss_merge_noalloc -- ss_merge that allocates nothing, for callers that

@@ -84,6 +84,8 @@ def lib():
     L.ss_server_submit_host.argtypes = [vp, vp, C.POINTER(u64)]
     L.ss_sort_batch_tuned.argtypes = [vp, vp, u32, vp]
     L.ss_sort_batch_async.argtypes = [vp, vp, u32, vp]
+    L.ss_sort_batch_cached.argtypes = [vp, vp, vp, u32, vp]
+    L.ss_merge_cached.argtypes = [vp, vp, vp, u32, vp, vp, vp, vp, vp, vp, vp, u32, vp, vp, vp]
     L.ss_autotune.argtypes = [vp, u32, C.POINTER(Tuning), C.POINTER(C.c_double), vp]
     L.ss_server_destroy.argtypes = [vp]
     L.ss_server_cancel.argtypes = [vp, u64, C.POINTER(i32)]
@@ -96,7 +98,8 @@ def lib():
                  "ss_gather_keys",
                  "ss_splitters", "ss_classify", "ss_classify_ex", "ss_profile_enable", "ss_profile_reset", "ss_profile_read",
                  "ss_server_create", "ss_server_submit", "ss_server_wait", "ss_server_destroy",
-                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_sort_batch_async", "ss_autotune",
+                 "ss_server_submit_host", "ss_sort_batch_tuned", "ss_sort_batch_async", "ss_sort_batch_cached",
+                 "ss_merge_cached", "ss_autotune",
                  "ss_server_cancel",
                  "ss_debug_fail_allocs", "ss_debug_copy_wait", "ss_device_error"):
         getattr(L, name).restype = i32
@@ -464,6 +467,38 @@ def ss_merge_ex(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin
     args, keep = _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
                              run_base)
     _check(lib().ss_merge_ex(*args[:9], int(method), *args[9:], _stream(stream)))
+    del keep
+
+
+class SortCache(C.Structure):
+    _fields_ = [("off_out", C.c_void_p), ("ck_out", C.c_void_p), ("ckd_out", C.c_void_p)]
+
+
+def ss_sort_batch_cached(requests, caches, tunings=None, stream=None):
+    """ss_sort_batch_tuned that also writes, per request, the caches a later
+    ss_merge_cached reads: caches[k] = (off_out int64[n], ck_out int64[n],
+    ckd_out int32[n]) device tensors, or None."""
+    arr, tarr = _tuned_args(requests, tunings)
+    carr = (SortCache * max(1, len(requests)))()
+    for k, q in enumerate(requests):
+        c = caches[k] if caches is not None else None
+        if c is not None:
+            n = int(q["n"])
+            carr[k] = SortCache(_dev(c[0], "int64", "off_out", n), _dev(c[1], "int64", "ck_out", n),
+                                _dev(c[2], "int32", "ckd_out", n))
+    _check(lib().ss_sort_batch_cached(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
+                                      C.cast(carr, C.c_void_p), len(requests), _stream(stream)))
+
+
+def ss_merge_cached(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_off, run_ck, run_ckd, run_begin,
+                    perm_out, lcp_out, run_base=None, stream=None):
+    """ss_merge of runs sorted by ss_sort_batch_cached, from their caches (laid out as run_perm)."""
+    args, keep = _merge_args(chars, offsets, lengths, fixed_len, run_perm, run_lcp, run_begin, perm_out, lcp_out,
+                             run_base)
+    total = int(np.asarray(run_begin, dtype=np.uint32)[-1])
+    cache = (_dev(run_off, "int64", "run_off", total), _dev(run_ck, "int64", "run_ck", total),
+             _dev(run_ckd, "int32", "run_ckd", total))
+    _check(lib().ss_merge_cached(*args[:6], *cache, *args[6:], _stream(stream)))
     del keep
 
 

@@ -229,7 +229,8 @@ int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *off
     const size_t A = 255;
     size_t cbytes = (chars_len + 15) & ~(size_t)15;   // aligned words past the end stay inside
     size_t nb4 = (4ull * n + A) & ~A, nb8 = (8ull * n + A) & ~A;
-    size_t bytes = ((cbytes + A) & ~A) + nb8 + (lengths_host ? nb4 : 0) + 2 * nb4 + (runs > 1 ? 2 * nb4 : 0) + 1024;
+    size_t bytes = ((cbytes + A) & ~A) + nb8 + (lengths_host ? nb4 : 0) + 2 * nb4 + (runs > 1 ? 3 * nb4 + 2 * nb8 : 0) +
+                   1024;
     void *block = nullptr;
     cudaError_t e = scratch_alloc(&block, bytes, st);
     if (e) {
@@ -253,6 +254,10 @@ int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *off
     p += nb4;
     uint32_t *d_rperm = runs > 1 ? (uint32_t *)p : nullptr;
     uint32_t *d_rlcp = runs > 1 ? (uint32_t *)(p + nb4) : nullptr;
+    // the runs' caches, written by their sort and read by the merge
+    uint64_t *d_roff = runs > 1 ? (uint64_t *)(p + 2 * nb4) : nullptr;
+    uint64_t *d_rck = runs > 1 ? (uint64_t *)(p + 2 * nb4 + nb8) : nullptr;
+    uint32_t *d_rckd = runs > 1 ? (uint32_t *)(p + 2 * nb4 + 2 * nb8) : nullptr;
     int rc = SS_OK;
     do {
         if (cbytes > chars_len && (e = cudaMemsetAsync(d_chars + chars_len, 0, cbytes - chars_len, st))) break;
@@ -267,13 +272,18 @@ int host_sort(const uint8_t *chars_host, uint64_t chars_len, const uint64_t *off
             std::vector<ReqDesc> rq(runs);
             std::vector<uint32_t> rb(runs + 1);
             for (uint32_t k = 0; k <= runs; k++) rb[k] = (uint32_t)((uint64_t)n * k / runs);
-            for (uint32_t k = 0; k < runs; k++)
+            for (uint32_t k = 0; k < runs; k++) {
                 rq[k] = make_req(d_chars, d_off + rb[k], d_len ? d_len + rb[k] : nullptr, fixed_len, rb[k + 1] - rb[k],
                                  d_rperm + rb[k], d_rlcp + rb[k], nullptr);
+                rq[k].off_out = d_roff + rb[k];
+                rq[k].ck_out = d_rck + rb[k];
+                rq[k].ckd_out = d_rckd + rb[k];
+            }
             rc = engine_sort(rq.data(), runs, st);
             if (rc == SS_OK) {
                 ReqDesc set = make_req(d_chars, d_off, d_len, fixed_len, 0, nullptr, nullptr, nullptr);
-                rc = merge_runs(set, d_rperm, d_rlcp, rb.data(), rb.data(), runs, d_perm, d_lcp, st);
+                rc = merge_runs(set, d_rperm, d_rlcp, rb.data(), rb.data(), runs, d_perm, d_lcp, st, MERGE_PAIRWISE,
+                                RunCache{d_roff, d_rck, d_rckd});
             }
         }
         if (rc != SS_OK) break;
@@ -406,6 +416,40 @@ int ss_sort_batch_async(const ss_request *reqs, const ss_tuning *tunings, uint32
     return engine_sort(v.data(), count, as_stream(stream), true);
 }
 
+int ss_sort_batch_cached(const ss_request *reqs, const ss_tuning *tunings, const ss_sort_cache *caches,
+                         uint32_t count, ss_stream_t stream) {
+    t_detail.clear();
+    if (count == 0) return SS_OK;
+    if (!reqs) {
+        set_error_detail("ss_sort_batch_cached: NULL request array");
+        return SS_ERR_INVALID;
+    }
+    std::vector<ReqDesc> v(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const ss_request &q = reqs[i];
+        v[i] = make_req(q.chars, q.offsets, q.lengths, q.fixed_len, q.n, q.perm_out, q.lcp_out, q.status_out);
+        int rc = check_req(v[i], "ss_sort_batch_cached");
+        if (rc == SS_OK && tunings) rc = pack_tuning(tunings[i], v[i], "ss_sort_batch_cached");
+        if (rc != SS_OK) return rc;
+        if (!caches) continue;
+        const ss_sort_cache &c = caches[i];
+        const int given = (c.off_out != nullptr) + (c.ck_out != nullptr) + (c.ckd_out != nullptr);
+        if (given == 0) continue;
+        if (given != 3) {
+            set_error_detail("ss_sort_batch_cached: request %u: give all of off_out, ck_out, ckd_out or none", i);
+            return SS_ERR_INVALID;
+        }
+        if (v[i].alpha) {
+            set_error_detail("ss_sort_batch_cached: request %u: caches hold bytes, not compressed characters", i);
+            return SS_ERR_INVALID;
+        }
+        v[i].off_out = c.off_out;
+        v[i].ck_out = c.ck_out;
+        v[i].ckd_out = c.ckd_out;
+    }
+    return engine_sort(v.data(), count, as_stream(stream));
+}
+
 int ss_sort_batch_tuned(const ss_request *reqs, const ss_tuning *tunings, uint32_t count, ss_stream_t stream) {
     t_detail.clear();
     if (count == 0) return SS_OK;
@@ -532,15 +576,12 @@ int ss_merge(const uint8_t *chars, const uint64_t *offsets, const uint32_t *leng
                        SS_MERGE_PAIRWISE, perm_out, lcp_out, stream);
 }
 
-int ss_merge_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
-                const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
-                const uint32_t *run_base_host, uint32_t K, uint32_t method, uint32_t *perm_out, uint32_t *lcp_out,
-                ss_stream_t stream) {
-    t_detail.clear();
-    if (method != SS_MERGE_PAIRWISE && method != SS_MERGE_LOSER_TREE) {
-        set_error_detail("ss_merge_ex: unknown merge method %u", method);
-        return SS_ERR_INVALID;
-    }
+// argument checks shared by the merge entry points: SS_OK with *total set
+// (0: nothing to merge), or the error
+static int check_merge(const uint8_t *chars, const uint64_t *offsets, const uint32_t *run_perm, const uint32_t *run_lcp,
+                       const uint32_t *run_begin_host, uint32_t K, const uint32_t *perm_out, const uint32_t *lcp_out,
+                       uint32_t *total) {
+    *total = 0;
     if (K == 0 || !run_begin_host) {
         set_error_detail("ss_merge: K must be >= 1 with run_begin_host[K+1]");
         return SS_ERR_INVALID;
@@ -554,16 +595,49 @@ int ss_merge_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *l
             set_error_detail("ss_merge: run_begin_host must be non-decreasing");
             return SS_ERR_INVALID;
         }
-    uint32_t total = run_begin_host[K];
-    if (total == 0) return SS_OK;
-    if (total == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
+    const uint32_t t = run_begin_host[K];
+    if (t == 0) return SS_OK;
+    if (t == 0xFFFFFFFFu) return SS_ERR_TOO_LARGE;
     if (!chars || !offsets || !run_perm || !run_lcp || !perm_out || !lcp_out) {
         set_error_detail("ss_merge: NULL pointer");
         return SS_ERR_INVALID;
     }
+    *total = t;
+    return SS_OK;
+}
+
+int ss_merge_ex(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
+                const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
+                const uint32_t *run_base_host, uint32_t K, uint32_t method, uint32_t *perm_out, uint32_t *lcp_out,
+                ss_stream_t stream) {
+    t_detail.clear();
+    if (method != SS_MERGE_PAIRWISE && method != SS_MERGE_LOSER_TREE) {
+        set_error_detail("ss_merge_ex: unknown merge method %u", method);
+        return SS_ERR_INVALID;
+    }
+    uint32_t total = 0;
+    int rc = check_merge(chars, offsets, run_perm, run_lcp, run_begin_host, K, perm_out, lcp_out, &total);
+    if (rc != SS_OK || total == 0) return rc;
     ReqDesc set = make_req(chars, offsets, lengths, fixed_len, 0, nullptr, nullptr, nullptr);
     return merge_runs(set, run_perm, run_lcp, run_begin_host, run_base_host, K, perm_out, lcp_out, as_stream(stream),
                       method);
+}
+
+int ss_merge_cached(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,
+                    const uint32_t *run_perm, const uint32_t *run_lcp, const uint64_t *run_off, const uint64_t *run_ck,
+                    const uint32_t *run_ckd, const uint32_t *run_begin_host, const uint32_t *run_base_host, uint32_t K,
+                    uint32_t *perm_out, uint32_t *lcp_out, ss_stream_t stream) {
+    t_detail.clear();
+    uint32_t total = 0;
+    int rc = check_merge(chars, offsets, run_perm, run_lcp, run_begin_host, K, perm_out, lcp_out, &total);
+    if (rc != SS_OK || total == 0) return rc;
+    if (!run_off || !run_ck || !run_ckd) {
+        set_error_detail("ss_merge_cached: NULL cache array");
+        return SS_ERR_INVALID;
+    }
+    ReqDesc set = make_req(chars, offsets, lengths, fixed_len, 0, nullptr, nullptr, nullptr);
+    return merge_runs(set, run_perm, run_lcp, run_begin_host, run_base_host, K, perm_out, lcp_out, as_stream(stream),
+                      MERGE_PAIRWISE, RunCache{run_off, run_ck, run_ckd});
 }
 
 int ss_gather_keys(const uint8_t *chars, const uint64_t *offsets, const uint32_t *lengths, uint32_t fixed_len,

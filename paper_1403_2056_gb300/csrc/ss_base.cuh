@@ -65,7 +65,8 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t W, uint32
     WElem e;
     if (ls < m) { e.g = 0; e.i = id; e.o = off; e.k0 = k0; e.k1 = k1; }
     else { e.g = 0xFFFFFFFFu; e.i = 0xFFFFFFFFu; e.o = 0; e.k0 = ~0ull; e.k1 = ~0ull; }
-    uint32_t lcp = 0;
+    uint32_t lcp = 0, ckd = 0;
+    uint64_t ck = 0;   // the key the LCP was decided in, and its depth
     for (;;) {
         // bitonic network inside each group's lanes (xor partners below W stay
         // in the group); after the stage of size k >= mmax the first k lanes of
@@ -86,11 +87,16 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t W, uint32
         uint64_t p1 = __shfl_up_sync(0xffffffffu, e.k1, 1, w);
         bool start = true;
         if (ls > 0 && ls < m && pg == e.g) {
-            if (p0 != e.k0) lcp = depth + key_lcp<A>(R, p0, e.k0);
-            else if (key_ends<A>(R, e.k0, depth)) lcp = depth + key_len<A>(R, e.k0, depth);
-            else if (p1 != e.k1) lcp = depth + kc + key_lcp<A>(R, p1, e.k1);
-            else if (key_ends<A>(R, e.k1, depth + kc)) lcp = depth + kc + key_len<A>(R, e.k1, depth + kc);
-            else start = false;
+            if (p0 != e.k0) { lcp = depth + key_lcp<A>(R, p0, e.k0); ck = e.k0; ckd = depth; }
+            else if (key_ends<A>(R, e.k0, depth)) { lcp = depth + key_len<A>(R, e.k0, depth); ck = e.k0; ckd = depth; }
+            else if (p1 != e.k1) { lcp = depth + kc + key_lcp<A>(R, p1, e.k1); ck = e.k1; ckd = depth + kc; }
+            else if (key_ends<A>(R, e.k1, depth + kc)) {
+                lcp = depth + kc + key_len<A>(R, e.k1, depth + kc);
+                ck = e.k1;
+                ckd = depth + kc;
+            } else {
+                start = false;
+            }
         }
         if (ls >= m) start = true;
         uint32_t sg = start ? ls : 0;
@@ -107,7 +113,11 @@ __device__ __forceinline__ void warp_finish(const ReqDesc &R, uint32_t W, uint32
     }
     if (ls < m) {
         R.perm_out[out + ls] = e.i;
-        if (ls > 0) R.lcp_out[out + ls] = lcp;
+        put_off(R, out + ls, e.o);
+        if (ls > 0) {
+            R.lcp_out[out + ls] = lcp;
+            put_ck(R, out + ls, ck, ckd);
+        }
     }
 }
 
@@ -547,9 +557,11 @@ __global__ void __launch_bounds__(NT, base_min_ctas(NT, sizeof(BaseSmem<NT, ITEM
             if (!__syncthreads_or(open)) {
                 for (uint32_t s = tid; s < m; s += NT) {
                     R.perm_out[lbase + s] = S.SI[S.SP[s]];
+                    put_off(R, lbase + s, soff[t.begin + S.SP[s]]);
                     if (s > 0) {
                         const uint64_t a = S.SK[s - 1], b = S.SK[s];
                         R.lcp_out[lbase + s] = a != b ? depth + key_lcp<A>(R, a, b) : depth + key_len<A>(R, b, depth);
+                        put_ck(R, lbase + s, b, depth);
                     }
                 }
                 finished = true;
@@ -636,7 +648,11 @@ __global__ void __launch_bounds__(NT, base_min_ctas(NT, sizeof(BaseSmem<NT, ITEM
                         const uint32_t s = tid * ITEMS + j;
                         if (s < M) {
                             R.perm_out[lbase + s] = S.SI[g[j] & 0xFFFu];
-                            if (s > 0) R.lcp_out[lbase + s] = lc[j];
+                            put_off(R, lbase + s, soff[t.begin + (g[j] & 0xFFFu)]);
+                            if (s > 0) {
+                                R.lcp_out[lbase + s] = lc[j];
+                                put_ck(R, lbase + s, k[j], depth);
+                            }
                         }
                     }
                     finished = true;
@@ -654,6 +670,7 @@ __global__ void __launch_bounds__(NT, base_min_ctas(NT, sizeof(BaseSmem<NT, ITEM
                     if (a != b) R.lcp_out[lbase + pos] = depth + key_lcp<A>(R, a, b);
                     else if (key_ends<A>(R, b, depth)) R.lcp_out[lbase + pos] = depth + key_len<A>(R, b, depth);
                     else st = 0;
+                    if (st) put_ck(R, lbase + pos, b, depth);
                 }
                 S.MG[s] = st ? pos : 0u;
             }
@@ -736,7 +753,10 @@ __global__ void __launch_bounds__(NT, base_min_ctas(NT, sizeof(BaseSmem<NT, ITEM
         // positions that ended as groups of one
         if (!finished)
             for (uint32_t i = tid; i < m; i += NT)
-                if (S.GS[S.SG[i]] == 1) R.perm_out[lbase + i] = S.SI[S.SP[i]];
+                if (S.GS[S.SG[i]] == 1) {
+                    R.perm_out[lbase + i] = S.SI[S.SP[i]];
+                    put_off(R, lbase + i, soff[t.begin + S.SP[i]]);
+                }
         __syncthreads();
         if (tid == 0) S.task = S.next;
         __syncthreads();

@@ -312,10 +312,12 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st, bool asy
     bool any_status = false;   // some request wants its status written on the device
     bool any_jump = false;     // some request classifies with jump tables
     bool any_alpha = false;    // some request uses alphabet compression
+    bool any_cache = false;    // some request wants the caches of its sorted positions
     for (const ReqDesc &q : reqs) {
         any_status = any_status || q.status_out;
         any_jump = any_jump || req_classifier(q) == CLS_JUMP;
         any_alpha = any_alpha || q.alpha;
+        any_cache = any_cache || q.ck_out;
     }
     // initial segments: one per request
     std::vector<BigSeg> big0;
@@ -435,6 +437,7 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st, bool asy
         P.cur = 0;
         P.any_jump = any_jump;
         P.any_status = any_status;
+        P.any_cache = any_cache;
         P.sms = (uint32_t)sm_count();
         if ((rc = sched_start(P, any_alpha, st)) != SS_OK) goto done;
         scratch_free(block, st);   // stream-ordered: after the last grid the scheduler launches
@@ -557,10 +560,11 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st, bool asy
             });
         }
         TRY(cudaGetLastError(), "base case launch");
-        if (nb) {
-            uint32_t grid = std::min<uint32_t>((nb + 255) / 256, sms * 8);
+        const uint32_t nfirst = any_cache ? nreq : 0u;
+        if (nb || nfirst) {
+            uint32_t grid = std::min<uint32_t>((std::max(nb, nfirst) + 255) / 256, sms * 8);
             with_alpha(any_alpha, [&](auto A) {
-                SS_LAUNCH_U("boundary", st, nb, k_boundary<decltype(A)::value><<<grid, 256, 0, st>>>(bounds, nb, dreqs));
+                SS_LAUNCH_U("boundary", st, nb, k_boundary<decltype(A)::value><<<grid, 256, 0, st>>>(bounds, nb, dreqs, nfirst));
             });
             TRY(cudaGetLastError(), "boundary launch");
         }

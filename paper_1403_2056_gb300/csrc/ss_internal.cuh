@@ -74,7 +74,25 @@ struct ReqDesc {
     int32_t *status_out;
     uint32_t alpha;            // 0: keys of 8 bytes; else the sorted alphabet a0..a3 (bytes 0..3, a0 >= 1) of a
                                // fixed-length request: keys of 32 characters, 2 bits each (alphabet compression)
+    uint64_t *off_out;         // NULL, or per sorted position: the string's offset,
+    uint64_t *ck_out;          // 8 of its characters (byte keys) from depth ckd_out,
+    uint32_t *ckd_out;         // where ckd_out <= its LCP < ckd_out + 8 (for a later LCP merge)
 };
+
+// The cache of R-local sorted position `local` (Section 5.4's distinguishing
+// characters, handed to a later merge), written in two parts: put_ck where
+// the position's LCP is decided (key = 8 characters from `depth`, depth <=
+// LCP < depth + 8, or the string ends there; every string that can still end
+// up at the position shares them), put_off where its string is (perm_out).
+__device__ __forceinline__ void put_ck(const ReqDesc &R, uint32_t local, uint64_t key, uint32_t depth) {
+    if (R.ck_out) {
+        R.ck_out[local] = key;
+        R.ckd_out[local] = depth;
+    }
+}
+__device__ __forceinline__ void put_off(const ReqDesc &R, uint32_t local, uint64_t off) {
+    if (R.off_out) R.off_out[local] = off;
+}
 
 // Per-request tuning: the segment size the tree depth aims at for children,
 // and the smallest depth step an even bucket takes (0 fields: the defaults).
@@ -205,6 +223,7 @@ struct SortPlan {               // everything the scheduler launches with, by va
     uint32_t cur;               // parity of the level to run
     uint32_t levels;            // levels run so far
     uint32_t any_jump, any_status, sms;
+    uint32_t any_cache;         // some request wants the caches of its sorted positions
     uint32_t base_grid[kClasses];
 };
 
@@ -573,9 +592,16 @@ int merge_kway(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
 size_t merge_kway_scratch(uint32_t total, uint32_t R, const uint32_t *rb);
 
 // merge (ss_merge.cu)
+// RunCache: the runs' string offsets and cached characters (run-aligned, as
+// a sort writes them; see put_ck and put_off), or all NULL: computed by the merge
+struct RunCache {
+    const uint64_t *off;
+    const uint64_t *ck;
+    const uint32_t *ckd;
+};
 int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
                const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t stream,
-               uint32_t method = 0);
+               uint32_t method = 0, RunCache cache = RunCache{nullptr, nullptr, nullptr});
 
 }  // namespace ss
 

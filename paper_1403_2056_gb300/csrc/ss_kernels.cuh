@@ -943,12 +943,21 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         if (threadIdx.x == 0) set_error(counters, E_COPY_TIMEOUT, tile);
         return;
     }
+    // a string of an all-equal complete bucket, not its first, has its LCP
+    // from this key (a bucket's first gets its cache with its boundary LCP)
+    auto done_not_first = [&](uint32_t info, uint32_t lo) {
+        return (info & BI_DONE) && (!(info & BI_FIRST) || lo > 0);
+    };
     for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
         const uint32_t b = S.slot_b[s];
         const uint32_t info = S.binfo[b];
-        if (info & (BI_FIN | BI_DELTA)) continue;   // final, or a new depth
         const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
         if (q < sg.begin || q >= seg_end) continue;
+        if (info & BI_FIN) {
+            if (done_not_first(info, s - S.lbase[b])) put_ck(R, q - R.base, S.u.buf[koff + S.src[s]], sg.depth);
+            continue;
+        }
+        if (info & BI_DELTA) continue;   // a new depth: gathered later
         key_out[q] = S.u.buf[koff + S.src[s]];
     }
     fence_proxy_async();
@@ -963,9 +972,13 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     }
     for (uint32_t s = threadIdx.x; s < tcount; s += kThreads) {
         const uint32_t b = S.slot_b[s];
-        if (S.binfo[b] & BI_FIN) continue;
+        const uint32_t info = S.binfo[b];
         const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
         if (q < sg.begin || q >= seg_end) continue;
+        if (info & BI_FIN) {   // placed now: its string's offset
+            put_off(R, q - R.base, S.u.buf[koff + S.src[s]]);
+            continue;
+        }
         soff_out[q] = S.u.buf[koff + S.src[s]];
     }
 }
@@ -1081,7 +1094,7 @@ __global__ void __launch_bounds__(256) k_gather_new(const GatherChunk *__restric
 // ------------------------------------------------------------ k_boundary
 
 template <bool A>
-__global__ void k_boundary(const Boundary *bounds, uint32_t nb, const ReqDesc *reqs) {
+__global__ void k_boundary(const Boundary *bounds, uint32_t nb, const ReqDesc *reqs, uint32_t nfirst) {
     for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nb; k += gridDim.x * blockDim.x) {
         Boundary b = bounds[k];
         const ReqDesc &R = reqs[b.req];
@@ -1089,6 +1102,16 @@ __global__ void k_boundary(const Boundary *bounds, uint32_t nb, const ReqDesc *r
         uint32_t sa = R.perm_out[lp - 1], sb = R.perm_out[lp];
         uint64_t ka = key_at<A>(R, sa, __ldg(R.offsets + sa), b.depth), kb = key_at<A>(R, sb, __ldg(R.offsets + sb), b.depth);
         R.lcp_out[lp] = b.depth + key_lcp<A>(R, ka, kb);
+        put_ck(R, lp, kb, b.depth);
+    }
+    // with caches: the first position of every request (LCP 0), keys at depth 0
+    for (uint32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < nfirst; k += gridDim.x * blockDim.x) {
+        const ReqDesc &R = reqs[k];
+        if (!R.ck_out || R.n == 0) continue;
+        const uint32_t s0 = R.perm_out[0];
+        const uint64_t o0 = __ldg(R.offsets + s0);
+        put_ck(R, 0, key_at<A>(R, s0, o0, 0), 0);
+        put_off(R, 0, o0);
     }
 }
 
@@ -1245,8 +1268,9 @@ __global__ void k_sched(SortPlan P) {
         // after all three (and the groups they hand over): the warp class, then boundaries
         k_small_warp<A><<<P.sms * 8, kThreads, 0, TL>>>(P.tl.l[0], c + C_NTASK + 0, P.reqs, P.eb);
         note_launch(c);
-        if (const uint32_t nbd = c[C_NBOUND]) {
-            k_boundary<A><<<min((nbd + 255) / 256, P.sms * 8), 256, 0, TL>>>(P.bounds, nbd, P.reqs);
+        const uint32_t nbd = c[C_NBOUND], nfirst = P.any_cache ? P.nreq : 0u;
+        if (nbd || nfirst) {
+            k_boundary<A><<<min((max(nbd, nfirst) + 255) / 256, P.sms * 8), 256, 0, TL>>>(P.bounds, nbd, P.reqs, nfirst);
             note_launch(c);
         }
     }

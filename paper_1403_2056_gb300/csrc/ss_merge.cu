@@ -413,6 +413,13 @@ __global__ void k_merge_round(ReqDesc S, const uint32_t *in_perm, const uint32_t
 #define SS_MERGE_TILE_THREADS 256
 #endif
 constexpr uint32_t kMergeTileThreads = SS_MERGE_TILE_THREADS;
+// CTAs per SM the merge tile must fit by registers: 6 (40 registers, a few
+// bytes spilled) measured faster than the 5 its 47 registers allow (its
+// lanes wait on dependent reads, more warps hide more); the chunk-start
+// search measured slower when held to fewer registers
+#ifndef SS_MERGE_TILE_MINB
+#define SS_MERGE_TILE_MINB 6
+#endif
 constexpr uint32_t kMergeTile = kMergeTileThreads * kMergeItems;   // outputs per CTA window
 static_assert(kMergeTile % kCoarse == 0, "a CTA window is a whole number of merge-path windows");
 static_assert(kMergeTile <= 65536, "tile-local sources are 16-bit");
@@ -523,7 +530,7 @@ struct MergeTileSmem {
 // (Algorithm 3) over kMergeItems outputs and records which entry each output
 // is and its LCP; the CTA then writes all outputs with coalesced stores.  Only
 // the case-1 comparisons that the cached characters leave open read strings.
-__global__ void __launch_bounds__(kMergeTileThreads) k_merge_tile(
+__global__ void __launch_bounds__(kMergeTileThreads, SS_MERGE_TILE_MINB) k_merge_tile(
     ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R, const uint32_t *rbase,
     const uint32_t *wbase, uint32_t npairs, uint32_t *out_perm, uint32_t *out_lcp, const Coarse *C,
     const uint32_t *cbase, const MergeStart *starts, const uint64_t *in_off, uint64_t *out_off, const uint64_t *ck,
@@ -637,7 +644,7 @@ __global__ void k_copy_run(const uint32_t *in_perm, const uint32_t *in_lcp, uint
 
 int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run_lcp, const uint32_t *run_begin_host,
                const uint32_t *run_base_host, uint32_t K, uint32_t *perm_out, uint32_t *lcp_out, cudaStream_t st,
-               uint32_t method) {
+               uint32_t method, RunCache cache) {
     uint32_t total = run_begin_host[K];
     // drop empty runs (they merge as nothing)
     std::vector<uint32_t> rb{0}, rbase;
@@ -722,13 +729,16 @@ int merge_runs(const ReqDesc &set, const uint32_t *run_perm, const uint32_t *run
             const uint32_t *bases = round == 1 ? d_rb + (R + 1) : nullptr;
             const uint32_t *d_cb = d_rb + (2 * R + 1);
             const uint32_t *d_wb = d_cb + npairs;
-            const uint64_t *src_o = off_buf[(round - 1) & 1];
+            // round 1 reads the runs' caches when the caller has them (a sort
+            // wrote them), else computes them
+            const bool given = round == 1 && cache.ck;
+            const uint64_t *src_o = given ? cache.off : off_buf[(round - 1) & 1];
             uint64_t *dst_o = last ? nullptr : off_buf[round & 1];
-            const uint64_t *src_ck = ck_buf[(round - 1) & 1];
-            const uint32_t *src_ckd = ckd_buf[(round - 1) & 1];
+            const uint64_t *src_ck = given ? cache.ck : ck_buf[(round - 1) & 1];
+            const uint32_t *src_ckd = given ? cache.ckd : ckd_buf[(round - 1) & 1];
             uint64_t *dst_ck = last ? nullptr : ck_buf[round & 1];
             uint32_t *dst_ckd = last ? nullptr : ckd_buf[round & 1];
-            if (round == 1) {
+            if (round == 1 && !given) {
                 uint32_t grid = std::min<uint32_t>((total + 255) / 256, 8192);
                 SS_LAUNCH_U("run_prep", st, total, k_run_prep<<<grid, 256, 0, st>>>(
                     set, src_p, src_l, d_rb, R, bases, total, 1, off_buf[0], ck_buf[0], ckd_buf[0]));

@@ -235,10 +235,11 @@ int ss_server_submit_host(ss_server *server, const ss_host_request *q, uint64_t 
     memset(&j.req, 0, sizeof(j.req));
     j.ha = HostArgs{q->chars, q->chars_len, q->offsets, q->lengths, q->lengths ? 0u : q->fixed_len, q->n,
                     q->runs ? q->runs : 1u, q->perm_out, q->lcp_out};
-    // device copies of the input, the output, the runs and the merge's buffers, and the sort's scratch
+    // device copies of the input, the output, the runs and their caches, the
+    // merge's buffers, and the sort's scratch
     const uint64_t n = q->n;
     j.bytes = q->n ? (size_t)(q->chars_len + 32 + 8 * n + (q->lengths ? 4 * n : 0) + 16 * n +
-                              (j.ha.runs > 1 ? 8 * n + 56 * n : 0) + engine_scratch_bytes(q->n, j.ha.runs))
+                              (j.ha.runs > 1 ? 8 * n + 20 * n + 56 * n : 0) + engine_scratch_bytes(q->n, j.ha.runs))
                    : 0;
     j.t_start = j.t_done = 0;
     j.status = SS_OK;

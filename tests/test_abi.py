@@ -150,3 +150,25 @@ def test_device_buffer_length_rule():
     P._need(torch.zeros(4), None, "x")
     with pytest.raises(ValueError):
         P._need(torch.zeros(3), 4, "x")
+
+
+def test_cache_arguments_checked_on_the_host():
+    """A sort cache with only some of its arrays, a cache on an alphabet-
+    compressed request, and ss_merge_cached without caches are refused before
+    any device work (the pointers are never dereferenced)."""
+    import ctypes as C
+    import paper_1403_2056_gb300 as P
+    q = P.Request(1, 1, None, 5, 5, 1, 1, None)   # fixed-length, 5 strings
+    arr = (P.Request * 1)(q)
+    for cache, tune in [((1, None, None), None), ((1, 1, None), None), ((None, None, 1), None),
+                        ((1, 1, 1), (0, 0, 0, P.alphabet(b"ACGT")))]:
+        carr = (P.SortCache * 1)(P.SortCache(*cache))
+        tarr = None if tune is None else (P.Tuning * 1)(P.Tuning(*tune))
+        rc = P.lib().ss_sort_batch_cached(C.cast(arr, C.c_void_p), None if tarr is None else C.cast(tarr, C.c_void_p),
+                                          C.cast(carr, C.c_void_p), 1, None)
+        assert rc == -1, cache
+        assert "ss_sort_batch_cached" in P._detail()
+    rb = (C.c_uint32 * 3)(0, 1, 2)
+    rc = P.lib().ss_merge_cached(1, 1, None, 0, 1, 1, None, 1, 1, C.cast(rb, C.c_void_p), None, 2, 1, 1, None)
+    assert rc == -1
+    assert "cache" in P._detail()

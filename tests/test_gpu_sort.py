@@ -636,3 +636,90 @@ def test_device_and_host_driven_levels_agree():
         assert np.array_equal(p0, p1) and np.array_equal(l0, l1), ss.name
         want_perm, want_lcp = oracle.sort(ss)
         assert np.array_equal(p0, want_perm) and np.array_equal(l0, want_lcp), ss.name
+
+
+# ------------------------------------------------------- sort caches
+def _check_caches(ss, perm, lcp, off, ck, ckd, base=0):
+    """off = the string's offset; ck = 8 bytes of the string from ckd
+    (big-endian, zero past its end); ckd <= lcp < ckd + 8 or the string ends
+    before ckd + 8; position 0 at depth 0 (the sort-cache contract)."""
+    assert ckd[0] == 0
+    for p in range(len(perm)):
+        i = int(perm[p]) + base
+        s = ss.string(i)
+        d = int(ckd[p])
+        assert int(off[p]) == int(ss.offsets[i]), p
+        want = int.from_bytes((s[d:d + 8] + bytes(8))[:8], "big")
+        assert int(ck[p]) == want, (p, d)
+        assert d <= int(lcp[p]), (p, d, int(lcp[p]))
+        assert int(lcp[p]) < d + 8 or len(s) < d + 8, (p, d, int(lcp[p]))
+
+
+@pytest.mark.parametrize("make", [lambda: W.url_like(40_000, seed=61), lambda: W.random_lower(30_000, seed=62),
+                                  lambda: W.dna_windows(30_000, 600_100, 100, seed=63),
+                                  lambda: W.sinha_dna_like(30_000, seed=64),
+                                  lambda: W.from_bytes_list([b"ab"[i % 2:i % 2 + 1] * (i % 7) for i in range(5000)]),
+                                  lambda: W.from_bytes_list([bytes([65 + i % 3]) * (i % 40) for i in range(3000)],
+                                                            terminated=False)])
+def test_sort_caches_and_cached_merge(make):
+    """ss_sort_batch_cached writes caches that satisfy their contract (checked
+    against the strings, every position), and ss_merge_cached of the runs from
+    them equals the oracle's sort of the whole set."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    ss = make()
+    n, K = ss.n, 3
+    rb = np.array([n * k // K for k in range(K + 1)], np.uint32)
+    chars, offsets, lengths = to_device(ss)
+    rperm = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    rlcp = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    off = torch.full((n,), -1, dtype=torch.int64, device="cuda:0")
+    ck = torch.full((n,), -1, dtype=torch.int64, device="cuda:0")
+    ckd = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    reqs, caches = [], []
+    for k in range(K):
+        b, e = int(rb[k]), int(rb[k + 1])
+        reqs.append(dict(chars=chars, offsets=offsets[b:e], lengths=None if lengths is None else lengths[b:e],
+                         fixed_len=ss.fixed_len, n=e - b, perm_out=rperm[b:e], lcp_out=rlcp[b:e]))
+        caches.append((off[b:e], ck[b:e], ckd[b:e]))
+    P.ss_sort_batch_cached(reqs, caches)
+    torch.cuda.synchronize()
+    hp, hl = rperm.cpu().numpy().view(np.uint32), rlcp.cpu().numpy().view(np.uint32)
+    ho, hk, hd = off.cpu().numpy().view(np.uint64), ck.cpu().numpy().view(np.uint64), ckd.cpu().numpy().view(np.uint32)
+    for k in range(K):
+        b, e = int(rb[k]), int(rb[k + 1])
+        want_p, want_l = oracle.sort(W.subset(ss, np.arange(b, e)))
+        assert np.array_equal(hp[b:e], want_p) and np.array_equal(hl[b:e], want_l), k
+        _check_caches(ss, hp[b:e], hl[b:e], ho[b:e], hk[b:e], hd[b:e], base=b)
+    perm = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    lcp = torch.full((n,), -1, dtype=torch.int32, device="cuda:0")
+    P.ss_merge_cached(chars, offsets, lengths, ss.fixed_len, rperm, rlcp, off, ck, ckd, rb, perm, lcp,
+                      run_base=rb[:-1])
+    torch.cuda.synchronize()
+    want_perm, want_lcp = oracle.sort(ss)
+    assert np.array_equal(perm.cpu().numpy().view(np.uint32), want_perm)
+    assert np.array_equal(lcp.cpu().numpy().view(np.uint32), want_lcp)
+
+
+def test_sort_caches_of_tiny_and_single_requests():
+    """Requests of 1, 2 and 33 strings (init, warp and CTA paths) write their caches."""
+    import torch
+    import paper_1403_2056_gb300 as P
+    sets = [W.random_lower(1, seed=65), W.random_lower(2, seed=66), W.url_like(33, seed=67), W.url_like(3000, seed=68)]
+    reqs, caches, outs = [], [], []
+    for ss in sets:
+        chars, offsets, lengths = to_device(ss)
+        t = [torch.full((ss.n,), -1, dtype=d, device="cuda:0") for d in (torch.int32, torch.int32, torch.int64,
+                                                                          torch.int64, torch.int32)]
+        reqs.append(dict(chars=chars, offsets=offsets, lengths=lengths, fixed_len=ss.fixed_len, n=ss.n,
+                         perm_out=t[0], lcp_out=t[1]))
+        caches.append((t[2], t[3], t[4]))
+        outs.append(t)
+    P.ss_sort_batch_cached(reqs, caches)
+    torch.cuda.synchronize()
+    for ss, t in zip(sets, outs):
+        p, l = t[0].cpu().numpy().view(np.uint32), t[1].cpu().numpy().view(np.uint32)
+        want_p, want_l = oracle.sort(ss)
+        assert np.array_equal(p, want_p) and np.array_equal(l, want_l)
+        _check_caches(ss, p, l, t[2].cpu().numpy().view(np.uint64), t[3].cpu().numpy().view(np.uint64),
+                      t[4].cpu().numpy().view(np.uint32))
