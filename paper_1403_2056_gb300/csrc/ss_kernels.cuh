@@ -1072,13 +1072,14 @@ __global__ void __launch_bounds__(256) k_gather_new(const GatherChunk *__restric
     for (uint32_t c = blockIdx.x; c < nch; c += gridDim.x) {
         const GatherChunk g = gchunks[c];
         const ReqDesc &R = reqs[g.req];
+        const bool by_index = R.lengths != nullptr;   // only explicit lengths need the string index
         constexpr int U = kGatherChunk / 256;
         uint32_t id[U];
         uint64_t so[U];
 #pragma unroll
         for (int u = 0; u < U; u++) {
             const uint32_t p = g.begin + u * 256 + threadIdx.x;
-            id[u] = p < g.end ? idx[p] : 0u;
+            id[u] = p < g.end && by_index ? idx[p] : 0u;
             so[u] = p < g.end ? soff[p] : 0ull;
         }
 #pragma unroll
