@@ -40,6 +40,31 @@ constexpr uint32_t kCoarse = SS_MERGE_COARSE;   // outputs per merge-path window
 
 // full comparison of strings a and b from depth h on (both share h characters),
 // 16 characters per round; returns -1/0/+1 and the lcp in *l
+// str_cmp_from that also hands back the 8 characters of both strings from
+// depth *kd where it decided (*kd <= *l < *kd + 8, or both end there): the
+// merge keeps them as the characters cached for the front that stays
+__device__ __forceinline__ int str_cmp_keys(const ReqDesc &S, uint32_t a, uint64_t oa, uint32_t b, uint64_t ob,
+                                            uint32_t h, uint32_t *l, uint64_t *ka, uint64_t *kb, uint32_t *kd) {
+    for (;;) {
+        uint64_t a0, a1, b0, b1;
+        load_key2_o(S, a, oa, h, a0, a1);
+        load_key2_o(S, b, ob, h, b0, b1);
+        if (a0 != b0 || has_zero(a0)) {
+            *ka = a0; *kb = b0; *kd = h;
+            if (a0 != b0) { *l = h + lcp8(a0, b0); return a0 < b0 ? -1 : 1; }
+            *l = h + nulpos(a0);
+            return 0;
+        }
+        if (a1 != b1 || has_zero(a1)) {
+            *ka = a1; *kb = b1; *kd = h + 8;
+            if (a1 != b1) { *l = h + 8 + lcp8(a1, b1); return a1 < b1 ? -1 : 1; }
+            *l = h + 8 + nulpos(a1);
+            return 0;
+        }
+        h += 16;
+    }
+}
+
 __device__ __forceinline__ int str_cmp_from(const ReqDesc &S, uint32_t a, uint64_t oa, uint32_t b, uint64_t ob,
                                             uint32_t h, uint32_t *l) {
     for (;;) {
@@ -593,7 +618,15 @@ __global__ void __launch_bounds__(kMergeTileThreads, SS_MERGE_TILE_MINB) k_merge
                         }
                     }
                 }
-                if (!decided) take_b = str_cmp_from(S, v.A(i), v.OA(i), v.B(j), v.OB(j), h, &hp) > 0;
+                if (!decided) {
+                    // the front that stays keeps the characters this comparison read
+                    // at its new LCP (the one that is output is replaced below)
+                    uint64_t ka, kb;
+                    uint32_t kd;
+                    take_b = str_cmp_keys(S, v.A(i), v.OA(i), v.B(j), v.OB(j), h, &hp, &ka, &kb, &kd) > 0;
+                    kA = ka; kdA = kd;
+                    kB = kb; kdB = kd;
+                }
             } else if (ha < hb) {    // case 2: B is smaller
                 take_b = true;
                 hp = ha;
