@@ -40,6 +40,8 @@
  *   - Reads of string bytes are aligned 8-byte words in a 4 KiB page that
  *     holds at least one byte of the string being read (or of its
  *     terminator), so no read touches a page the strings do not touch.
+ *     A 16-byte aligned offsets array may be read in whole 16-byte blocks
+ *     (at most 8 bytes past its last entry, in the same block).
  */
 #ifndef SS_GB300_H
 #define SS_GB300_H

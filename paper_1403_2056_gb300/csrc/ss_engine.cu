@@ -325,11 +325,14 @@ int engine_sort(const ReqDesc *reqs_in, uint32_t nreq, cudaStream_t st, bool asy
     std::vector<uint4> pchunk_host;
     uint32_t tiles0 = 0, counts0 = 0, pairs0 = 0;
     for (uint32_t r = 0; r < nreq; r++) {
-        const ReqDesc &q = reqs[r];
+        ReqDesc &q = reqs[r];
         if (q.n < 2) continue;
         if (q.n > req_small_max(q)) {
+            // a 16-byte aligned offsets array is copied straight into the first
+            // level's scatter: k_init writes no index or offset for the request
+            q.lvl1 = ((uintptr_t)q.offsets & 15u) == 0 ? 1u : 0u;
             BigSeg s{};
-            s.begin = q.base; s.size = q.n; s.depth = 0; s.req = r;
+            s.begin = q.base; s.size = q.n; s.depth = 0; s.req = r; s.lvl1 = q.lvl1;
             big0.push_back(s);
             uint32_t d = req_choose_d(q.n, q), t = tiles_of(q.n), B = buckets_of(d);
             tiles0 += t; counts0 += B * t; pairs0 += B;

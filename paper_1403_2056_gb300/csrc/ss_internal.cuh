@@ -77,6 +77,8 @@ struct ReqDesc {
     uint64_t *off_out;         // NULL, or per sorted position: the string's offset,
     uint64_t *ck_out;          // 8 of its characters (byte keys) from depth ckd_out,
     uint32_t *ckd_out;         // where ckd_out <= its LCP < ckd_out + 8 (for a later LCP merge)
+    uint32_t lvl1;             // set by the engine: the request's first level takes its string
+                               // indices from the positions and its offsets from `offsets` itself
 };
 
 // The cache of R-local sorted position `local` (Section 5.4's distinguishing
@@ -139,7 +141,9 @@ struct BigSeg {                 // a segment sorted by one multi-CTA S5 step
     uint32_t begin, size, depth, req;
     uint32_t d, tiles;
     uint32_t tile_base, cnt_base, bkt_base, scan_base;
-    uint32_t pad0, pad1;
+    uint32_t lvl1;              // 1: a request's first segment, positions are string indices and the
+                                // string offsets are the request's own array (ReqDesc::lvl1)
+    uint32_t pad1;
 };
 
 struct SmallTask {              // a base-case segment

@@ -80,8 +80,10 @@ __global__ void k_init(const ReqDesc *reqs, uint32_t nreq, uint32_t N, uint32_t 
         const ReqDesc &R = reqs[r];
         uint32_t i = g - R.base;
         uint64_t off = __ldg(R.offsets + i);
-        idx0[g] = i;
-        soff0[g] = off;
+        if (!R.lvl1) {   // else the first level's scatter takes both from the request
+            idx0[g] = i;
+            soff0[g] = off;
+        }
         // characters 0..15: the second word serves the shared-prefix step below
         // (it lives in the other parity's key buffer until the first scatter)
         uint64_t k0, k1 = 0;
@@ -808,13 +810,17 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     const uint32_t ibytes = 4u * (((tbeg + tcount + 3u) & ~3u) - i0);
     const uint32_t k0 = tbeg & ~1u, koff = tbeg - k0;
     const uint32_t kbytes = 8u * (((tbeg + tcount + 1u) & ~1u) - k0);
+    // a request's first level: string index = position - base, offsets copied
+    // from the request's 16-byte aligned array (tiles start at multiples of
+    // kTile from its first string; the last 16-byte block is read whole)
+    const bool lvl1 = MODE == MODE_SORT && sg.lvl1;
 
     const long long budget = g_copy_wait_cycles;
     const bool withheld = MODE == MODE_SORT && g_copy_withheld;   // test only: no copy is issued, the waits run out
     if (MODE == MODE_SORT && threadIdx.x == 0) {
         for (int k = 0; k < 3; k++) mbar_init(&S.bar[k], 1);
         fence_mbar_init();
-        if (!withheld) {
+        if (!withheld && !lvl1) {
             mbar_expect_tx(&S.bar[0], ibytes);
             bulk_to_smem(S.sidx(), idx_in + i0, ibytes, &S.bar[0]);
         }
@@ -946,7 +952,7 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         bulk_to_smem(S.u.buf, key_in + k0, kbytes, &S.bar[1]);
     }
     // string indices; strings whose bucket is final go straight to the output
-    if (!__syncthreads_and(mbar_wait(&S.bar[0], 0, budget))) {
+    if (!lvl1 && !__syncthreads_and(mbar_wait(&S.bar[0], 0, budget))) {
         if (threadIdx.x == 0) set_error(counters, E_COPY_TIMEOUT, tile);
         // the key copy in flight lands before the CTA leaves
         if (!SS_SCATTER_COMPACT && !withheld) mbar_wait(&S.bar[1], 0, budget);
@@ -958,7 +964,7 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         const uint32_t lo = s - S.lbase[b];
         const uint32_t q = S.tbase[b] + lo;
         if (q < sg.begin || q >= seg_end) { set_error(counters, E_BAD_POS, q); continue; }
-        const uint32_t id = S.sidx()[ioff + S.src[s]];
+        const uint32_t id = lvl1 ? tbeg - R.base + S.src[s] : S.sidx()[ioff + S.src[s]];
         const uint32_t info = S.binfo[b];
         if (info & BI_FIN) {
             const uint32_t local = q - R.base;
@@ -1001,9 +1007,16 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
     }
     fence_proxy_async();
     __syncthreads();   // every key read from the buffer: it takes the offsets next
+    const uint32_t ooff = lvl1 ? 0u : koff;   // the offsets' place of the tile's first string in buf
     if (threadIdx.x == 0) {
-        mbar_expect_tx(&S.bar[2], kbytes);
-        bulk_to_smem(S.u.buf, soff_in + k0, kbytes, &S.bar[2]);
+        if (lvl1) {
+            const uint32_t obytes = 8u * ((tcount + 1u) & ~1u);
+            mbar_expect_tx(&S.bar[2], obytes);
+            bulk_to_smem(S.u.buf, R.offsets + (tbeg - R.base), obytes, &S.bar[2]);
+        } else {
+            mbar_expect_tx(&S.bar[2], kbytes);
+            bulk_to_smem(S.u.buf, soff_in + k0, kbytes, &S.bar[2]);
+        }
     }
     if (!__syncthreads_and(mbar_wait(&S.bar[2], 0, budget))) {
         if (threadIdx.x == 0) set_error(counters, E_COPY_TIMEOUT, tile);
@@ -1015,10 +1028,10 @@ __global__ void __launch_bounds__(kThreads, SS_SCATTER_MINB) k_scatter(const Big
         const uint32_t q = S.tbase[b] + (s - S.lbase[b]);
         if (q < sg.begin || q >= seg_end) continue;
         if (info & BI_FIN) {   // placed now: its string's offset
-            put_off(R, q - R.base, S.u.buf[koff + S.src[s]]);
+            put_off(R, q - R.base, S.u.buf[ooff + S.src[s]]);
             continue;
         }
-        soff_out[q] = S.u.buf[koff + S.src[s]];
+        soff_out[q] = S.u.buf[ooff + S.src[s]];
     }
 }
 
