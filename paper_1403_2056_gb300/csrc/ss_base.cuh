@@ -3,19 +3,23 @@
 // (or one warp), and their LCPs are written (the role LCP insertion sort,
 // Algorithm 5, plays in the paper's pS5).
 //
-// A segment is sorted by its 8-character keys once, with a CTA merge sort
-// (8 keys per thread sorted in registers, then merge-path passes through
-// padded, bank-conflict-free shared memory).  Sorting is skipped when every
-// group's keys are already equal.  Neighbours with different keys are split
-// (LCP = depth +
-// lcp of the keys); neighbours with equal keys that hold the end of the
-// string are equal strings (LCP = their length); runs of equal keys without
-// the end form groups that continue 8 characters deeper.  Groups of at most
-// 32 strings are finished by one warp in registers; larger groups are
-// re-sorted by the CTA, compacted, by (group, next key, position).  Equal
-// strings keep their input order (input order inside a segment is index
-// order).  An LCP belongs to a position: once two neighbouring positions are
-// split, every later re-sort stays on one side of that boundary.
+// A segment is sorted by its 8-character keys once: by one counting pass on
+// a digit of the keys when no digit gets more than a few strings (then
+// insertion sort inside each digit), else with a CTA merge sort (8 keys per
+// thread sorted in registers, then merge-path passes through padded,
+// bank-conflict-free shared memory).  Sorting is skipped when every group's
+// keys are already equal.  Neighbours with different keys are split (LCP =
+// depth + lcp of the keys); neighbours with equal keys that hold the end of
+// the string are equal strings (LCP = their length); runs of equal keys
+// without the end form groups that continue 8 characters deeper.  Groups of
+// at most 32 strings are finished by the warp class (several groups packed
+// into one warp); larger groups are re-sorted by the CTA, compacted, by
+// (group, next key, position).  Equal strings keep their input order (input
+// order inside a segment is index order).  An LCP belongs to a position:
+// once two neighbouring positions are split, every later re-sort stays on one
+// side of that boundary.  With sort caches requested, each position's 8
+// characters are written where its LCP is decided and its string offset where
+// its permutation entry is.
 #pragma once
 
 #include "ss_internal.cuh"

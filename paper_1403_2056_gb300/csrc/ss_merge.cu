@@ -9,14 +9,18 @@
 // characters each window's strings share; then every chunk of kMergeItems
 // outputs gets its start (the search inside its window, from the shared
 // prefix, and the LCPs of both fronts with the string before the chunk: one
-// side's is the run's own LCP entry, the other is one string comparison).
-// The merge proper runs per CTA window of kMergeTile outputs: the window's
-// LCPs and cached characters are staged in shared memory, each thread runs
-// the binary LCP-merge over its chunk there, and the CTA writes the outputs
-// with coalesced stores.
+// side's is the run's own LCP entry, the other comes from the search's last
+// probes where unequal LCPs decide, else from one string comparison).  The
+// merge proper runs per CTA window of kMergeTile outputs: each thread runs
+// the binary LCP-merge over its chunk, reading the window's LCPs and cached
+// characters through L1, and the CTA writes the outputs with coalesced
+// stores staged in shared memory.
 // Comparisons whose LCPs differ cost no string access at all (cases 2 and 3
 // of LCP-Compare); equal LCPs first try the cached characters, and only then
-// read characters, 8 at a time from the known common prefix on.
+// read characters, 16 at a time from the known common prefix on; the front
+// that stays keeps the characters read last as its cache.  Round 1 takes the
+// runs' offsets and cached characters from the sort when the caller has them
+// (ss_merge_cached), else loads them itself (k_run_prep).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -474,8 +478,8 @@ __device__ __forceinline__ MergeWindow merge_window(const uint32_t *wbase, uint3
 // window (same grid shape as k_merge_tile): the merge-path search inside the
 // kCoarse window of its diagonal, from the window's shared prefix, and the
 // LCPs of both fronts with the string output just before the chunk.  These are
-// the string accesses of a round; they run here at full occupancy, apart from
-// the staged merge.
+// most of the string accesses of a round; they run here, apart from the merge
+// tile, at the occupancy the registers allow.
 __global__ void __launch_bounds__(kMergeTileThreads) k_merge_starts(
     ReqDesc S, const uint32_t *in_perm, const uint32_t *in_lcp, const uint32_t *rb, uint32_t R, const uint32_t *rbase,
     const uint32_t *wbase, uint32_t npairs, const Coarse *C, const uint32_t *cbase, const uint64_t *in_off,
